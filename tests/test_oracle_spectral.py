@@ -1,0 +1,158 @@
+"""Pins for oracle.spectral, oracle.general, oracle.shybrid and oracle.rank."""
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import synth
+from oracle import diffusion as D
+from oracle import general, graph, rank, shybrid
+from oracle import spectral as S
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden_rows(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append([float(t) for t in line.split()])
+    return rows
+
+
+def test_spectrum_facts(small_graph):
+    # Sec. 3: eigenvalues in [-1, 1]; Sec. 4.4: lambda_1 = 1 and lambda_n <= -1/(n-1).
+    W, A = small_graph["W"], small_graph["A"]
+    lam, U = S.eigh_desc(W)
+    n = lam.size
+    assert lam[0] == pytest.approx(1.0, abs=1e-12)
+    assert lam[-1] >= -1 - 1e-12 and lam[0] <= 1 + 1e-12
+    assert lam[-1] <= -1.0 / (n - 1) + 1e-12
+    ncomp, _ = S.components(A)
+    assert np.sum(lam > 1 - 1e-9) == ncomp
+    if ncomp == 1:
+        sd = np.sqrt(np.asarray(A.sum(1)).ravel())
+        u = U[:, 0] * np.sign(U[:, 0].sum())
+        assert np.allclose(u, sd / np.linalg.norm(sd), atol=1e-10)
+
+
+def test_multiplicity_equals_components():
+    X1, _ = synth.database(21, 20, 4, 1, 40.0, 40.0)
+    X2, _ = synth.database(22, 20, 4, 1, 40.0, 40.0)
+    A = sp.block_diag([graph.adjacency(X1, 4), graph.adjacency(X2, 4)]).tocsr()
+    W, _ = graph.normalize(A)
+    lam, _ = S.eigh_desc(W)
+    ncomp, _ = S.components(A)
+    assert ncomp >= 2
+    assert np.sum(lam > 1 - 1e-9) == ncomp
+
+
+def test_orthogonality_eq5(small_graph):
+    lam, U = S.eigh_desc(small_graph["W"])
+    r = 7
+    U1, U2 = U[:, :r], U[:, r:]
+    assert np.allclose(U1.T @ U1, np.eye(r), atol=1e-12)
+    assert np.allclose(U2.T @ U2, np.eye(60 - r), atol=1e-12)
+    assert np.allclose(U1.T @ U2, 0, atol=1e-12)
+    assert np.allclose(U1 @ U1.T + U2 @ U2.T, np.eye(60), atol=1e-12)
+
+
+def test_theorem1_matrix_identity(small_graph):
+    # Eq. 15: h(W) = U1 g(Lambda1) U1^T + h(W - U1 Lambda1 U1^T), dense, several r.
+    W = small_graph["W"].toarray()
+    hW = D.closed_form(W, np.eye(60), 0.99)
+    for r in (0, 1, 6, 33, 60):
+        lam, U = S.eigenpairs(W, r)
+        rhs = (U * D.g_alpha(lam, 0.99)) @ U.T + D.closed_form(S.deflated(W, U, lam), np.eye(60), 0.99)
+        assert np.allclose(hW, rhs, atol=1e-10)
+
+
+def test_theorem2_polynomial(small_graph):
+    # Appendix A, Eq. 32, for h(x) = 0.3 + 0.5x - 0.2x^2 + 0.1x^5.
+    W = small_graph["W"]
+    coeffs = [0.3, 0.5, -0.2, 0.0, 0.0, 0.1]
+    y = np.random.default_rng(1).standard_normal(60)
+    lam, U = S.eigenpairs(W, 9)
+    direct = general.poly_apply(lambda z: W @ z, coeffs, y)
+    assert np.allclose(general.hybrid_poly(W, U, lam, coeffs, y), direct, atol=1e-12)
+
+
+def test_kappa_formulas(small_graph):
+    # Eq. 22 and Eq. 23 against condition numbers of the dense matrices.
+    W = small_graph["W"].toarray()
+    lam, U = S.eigh_desc(W)
+    a = 0.99
+    L = (np.eye(60) - a * W) / (1 - a)
+    assert S.kappa_of(L) == pytest.approx(S.kappa_laplacian(a, 1.0, lam[-1]), rel=1e-9)
+    for r in (1, 3, 8):
+        if lam[r] <= 0:
+            continue
+        Wr = S.deflated(W, U[:, :r], lam[:r])
+        Lr = (np.eye(60) - a * Wr) / (1 - a)
+        assert S.kappa_of(Lr) == pytest.approx(S.kappa_laplacian(a, lam[r], lam[-1]), rel=1e-9)
+
+
+def test_worked_kappa_ratio_golden():
+    # Sec. 4.4: alpha = 0.99, lambda_{r+1} = 0.7 gives the ratio 0.0326.
+    (alpha, lam, ratio, digits), = _golden_rows("kappa_ratio.txt")
+    got = S.kappa_laplacian(alpha, lam, -0.5) / S.kappa_laplacian(alpha, 1.0, -0.5)
+    assert float(f"{got:.{int(digits)}g}") == ratio
+
+
+def test_cg_error_within_bound(small_graph):
+    # Eq. 21: ||e_i||_A / ||e_0||_A <= phi_i(A) at every iteration.
+    W = small_graph["W"]
+    a = 0.99
+    y = np.zeros(60)
+    y[[3, 17, 40]] = [1.0, 0.5, 0.25]
+    for r in (0, 5):
+        lam, U = S.eigenpairs(W, r)
+        Wr = S.deflated(W, U, lam)
+        Lr = (np.eye(60) - a * Wr) / (1 - a)
+        xstar = np.linalg.solve(Lr, y)
+        kap = S.kappa_of(Lr)
+        errs = []
+        D.cg(lambda z: Lr @ z, y, 1e-14, 200, callback=lambda i, x: errs.append(S.a_norm(Lr, xstar - x)))
+        e0 = errs[0]
+        for i, e in enumerate(errs):
+            assert e / e0 <= S.phi(kap, i) + 1e-12
+
+
+def test_table1_memory_golden():
+    # Table 1: an n x r FP64 embedding of the 933,412-node component with r = 5k
+    # takes 35,606 MB, i.e. MiB (2^20 bytes), truncated (35,606.5 exactly).
+    (n, r, b, mb), = _golden_rows("table1_memory.txt")
+    assert int(n * r * b // 2 ** 20) == mb
+
+
+def test_sparsify_keeps_largest_magnitudes():
+    U = np.array([[0.1, -0.5, 0.02], [0.3, -0.02, 0.9]])
+    out = shybrid.sparsify(U, 0.5)
+    assert np.count_nonzero(out) == 3
+    assert set(np.abs(out[out != 0])) == {0.5, 0.3, 0.9}
+    # equal magnitudes: the later (row-major) entry goes first
+    out2 = shybrid.sparsify(U, 4 / 6)
+    assert np.count_nonzero(out2) == 2 and out2[0, 1] == -0.5 and out2[1, 2] == 0.9
+    out3 = shybrid.sparsify(np.array([[0.2, -0.2, 0.2]]), 1 / 3)
+    assert list(out3[0]) == [0.2, -0.2, 0.0]
+
+
+def test_topk_matches_python_sort():
+    rng = np.random.default_rng(3)
+    x = rng.integers(0, 6, 50).astype(float) / 7  # many ties
+    for K in (1, 5, 50):
+        ids, sc = rank.topk(x, K)
+        want = sorted(range(50), key=lambda i: (-x[i], i))[:K]
+        assert list(ids) == want
+        assert np.array_equal(sc, x[want])
+
+
+def test_pooled_and_rank_match():
+    x = np.arange(12, dtype=float)
+    assert list(rank.pooled(x, 3)) == [3, 12, 21, 30]
+    ref = np.array([1.0, 1.0 + 1e-9, 0.5])
+    assert rank.ranks_match([1, 0, 2], [0, 1, 2], ref, 1e-6)
+    assert not rank.ranks_match([2, 0, 1], [0, 1, 2], ref, 1e-6)
