@@ -1,0 +1,433 @@
+"""Throughput of the hybrid diffusion query path on GB300.
+
+One step = one batch of B queries through the whole online path: observation
+scatter, spectral term, CG iterations of the temporal term (Eq. 17-20) and
+the top-K ranking (Sec. 3), with inputs resident in HBM.  The workload is the
+1,000,000-node k=50 graph of synthetic d=2048 bf16 vMF descriptors.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun) every rank runs an independent replica on its own GPU
+(the query stream shards by query; there is no exchange step).  Rank 0 prints
+one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "queries/sec and p50/p99 latency at 1M nodes, hybrid BF16-U_r vs pure CG, equal FP64 error"
+TOL_REL = 1e-4
+LADDER = [1e-3, 3e-4, 1e-4, 3e-5, 1e-5, 3e-6, 1e-6, 3e-7]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="cfg3")
+    ap.add_argument("--n", type=int, default=0, help="override n (smaller profiling case)")
+    ap.add_argument("--d", type=int, default=0)
+    ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--r", type=int, default=200)
+    ap.add_argument("--mode", default="pcg")
+    ap.add_argument("--storage", default="bf16")
+    ap.add_argument("--topk", type=int, default=100)
+    ap.add_argument("--restarts", type=int, default=2)
+    ap.add_argument("--cpu-sample", type=int, default=2, help="query columns timed on the oracle")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--quick", action="store_true", help="skip the r=0 leg and calibration (profiling runs)")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ clocks
+class Clocks:
+    """Sample nvidia-smi during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.samples.append(parts)
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for s in self.samples:
+            for nm, v in zip(names, s[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.samples)}
+
+
+# ------------------------------------------------------------------ workload
+def build_workload(args, ctx, rank):
+    """Descriptors, graph, observations and eigenpairs of the benchmark workload."""
+    import torch
+    import paper_1807_08692_gb300 as hd
+    import synth
+    c = synth.get_config(args.workload)
+    n = args.n or c.n
+    d = args.d or c.d
+    t0 = time.time()
+    X, _ = synth.database(c.seed, n, d, c.ncl, c.kappa_lo, c.kappa_hi, c.sizes, c.zipf_s)
+    Xt = torch.from_numpy(X).to(torch.bfloat16 if c.dtype == "bf16" else torch.float32).cuda()
+    del X
+    t_gen = time.time() - t0
+    t0 = time.time()
+    g = hd.build_graph(ctx, Xt, c.k, c.gamma)
+    torch.cuda.synchronize()
+    t_graph = time.time() - t0
+    # queries: one calibration batch and the timed batch (different draws)
+    nq = 2 * args.batch
+    Qv = synth.queries(c.seed + 1000 * rank, nq, d, c.ncl, c.kappa_lo, c.kappa_hi, c.sizes, c.zipf_s)
+    Qt = torch.from_numpy(Qv).to(Xt.dtype).cuda()
+    yp, yi, yv = hd.observe(ctx, Xt, Qt, c.k_y, c.gamma)
+    del Xt, Qt
+    torch.cuda.empty_cache()
+    B = args.batch
+    cal = (yp[:B + 1].copy(), yi[:yp[B]].copy(), yv[:yp[B]].copy())
+    off = yp[B]
+    tim = ((yp[B:] - off).astype(np.int32), yi[off:].copy(), yv[off:].copy())
+    t0 = time.time()
+    eig, lam, res, conv = None, None, None, None
+    if args.r > 0:
+        eig, lam, res, conv = hd.eigendecompose(ctx, g, args.r, block=32, tol=1e-5, max_restarts=args.restarts,
+                                                storage=args.storage)
+    torch.cuda.synchronize()
+    t_eig = time.time() - t0
+    return {"cfg": c, "n": n, "d": d, "g": g, "cal": cal, "tim": tim, "eig": eig, "lam": lam, "res": res,
+            "conv": conv, "t_gen": t_gen, "t_graph": t_graph, "t_eig": t_eig}
+
+
+def calibrate(ctx, wl, eig, mode, alpha):
+    """Loosest ladder tolerance whose max rel-l2 versus a tightly converged
+    reference of the same batch is <= TOL_REL / 2."""
+    import paper_1807_08692_gb300 as hd
+    g = wl["g"]
+    yp, yi, yv = wl["cal"]
+    ref, *_ = hd.query_batch(ctx, g, wl["eig"] if wl["eig"] is not None else None, "pcg", yp, yi, yv, alpha,
+                             1e-7, 2000)
+    refn = ref.norm(dim=0)
+    for tol in LADDER:
+        X, it, rr, st = hd.query_batch(ctx, g, eig, mode, yp, yi, yv, alpha, tol, 2000)
+        err = ((X - ref).norm(dim=0) / refn).max().item()
+        if err <= TOL_REL / 2:
+            return tol, err, int(np.max(it))
+    return LADDER[-1], err, int(np.max(it))
+
+
+# ------------------------------------------------------------------ timed legs
+FAMILIES = ["spmm", "update", "direction", "lr_reduce", "lr_expand", "scalar", "rank"]
+
+
+def time_leg(ctx, wl, eig, mode, tol, alpha, K, W, B, topk, profile):
+    import torch
+    import paper_1807_08692_gb300 as hd
+    g = wl["g"]
+    yp, yi, yv = wl["tim"]
+    # inputs resident in HBM
+    ypd = torch.from_numpy(yp).cuda()
+    yid = torch.from_numpy(yi).cuda()
+    yvd = torch.from_numpy(yv).cuda()
+    told = torch.full((B,), tol, dtype=torch.float32, device="cuda")
+    X = torch.empty((wl["n"], (B + 3) // 4 * 4), dtype=torch.float32, device="cuda")
+    itd = torch.zeros(B, dtype=torch.int32, device="cuda")
+    rrd = torch.zeros(B, dtype=torch.float32, device="cuda")
+    std = torch.zeros(B, dtype=torch.int32, device="cuda")
+    idx = torch.empty((B, topk), dtype=torch.int32, device="cuda")
+    sc = torch.empty((B, topk), dtype=torch.float32, device="cuda")
+    Kh = np.full(B, topk, np.int32)
+
+    def step():
+        hd.query_batch(ctx, g, eig, mode, ypd, yid, yvd, alpha, told, 2000, X=X, ldx=X.shape[1], iters=itd,
+                       relres=rrd, status=std)
+        hd.rank(ctx, X[:, :B] if X.shape[1] == B else X, Kh, topk, idx=idx, score=sc)
+
+    for _ in range(W):
+        step()
+    torch.cuda.synchronize()
+    if profile:
+        ctx.profile(True)
+        for f in FAMILIES:
+            ctx.profile_read(f)
+    l0 = ctx.launches()
+    s = torch.cuda.current_stream()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
+    torch.cuda.synchronize()
+    evs[0].record(s)
+    for k in range(K):
+        step()
+        evs[k + 1].record(s)
+    torch.cuda.synchronize()
+    launches = ctx.launches() - l0
+    per = [evs[k].elapsed_time(evs[k + 1]) for k in range(K)]
+    fam = {}
+    if profile:
+        for f in FAMILIES:
+            cnt, ms = ctx.profile_read(f)
+            fam[f] = (cnt, ms)
+        ctx.profile(False)
+    total_ms = evs[0].elapsed_time(evs[K])
+    return {"ms": per, "total_ms": total_ms, "launches": launches, "fam": fam,
+            "iters": itd.cpu().numpy(), "status": std.cpu().numpy(), "relres": rrd.cpu().numpy()}
+
+
+def e2e_leg(ctx, wl, eig, mode, tol, alpha, K, B, topk):
+    """Same metric through the public API with HOST buffers: the observation
+    arrays go host->device and the rankings device->host inside each step."""
+    import torch
+    import paper_1807_08692_gb300 as hd
+    g = wl["g"]
+    yp, yi, yv = (np.ascontiguousarray(a) for a in wl["tim"])
+    tolh = np.full(B, tol, np.float32)
+    X = torch.empty((wl["n"], (B + 3) // 4 * 4), dtype=torch.float32, device="cuda")
+    Kh = np.full(B, topk, np.int32)
+    idx = np.empty((B, topk), np.int32)
+    sc = np.empty((B, topk), np.float32)
+    times = []
+    for k in range(K + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hd.query_batch(ctx, g, eig, mode, yp, yi, yv, alpha, tolh, 2000, X=X, ldx=X.shape[1])
+        hd.rank(ctx, X, Kh, topk, idx=idx, score=sc)
+        torch.cuda.synchronize()
+        if k:
+            times.append(time.perf_counter() - t0)
+    h2d = yp.nbytes + yi.nbytes + yv.nbytes + tolh.nbytes
+    d2h = idx.nbytes + sc.nbytes + 3 * 4 * B
+    return float(np.sum(times)), h2d, d2h
+
+
+def algorithmic_bytes(wl, B, eig):
+    """Algorithmic bytes per launch of each kernel family (each operand once)."""
+    n = wl["n"]
+    nnz = wl["g"].nnz
+    Bp = (B + 3) // 4 * 4
+    vec = n * Bp * 4
+    su = {"f32": 4, "bf16": 2, "fp8": 1}
+    ub = 0
+    if eig is not None:
+        ldu = (eig.r + 15) // 16 * 16
+        ub = n * ldu * su[{0: "f32", 1: "bf16", 2: "fp8"}[eig.storage]]
+    return {
+        "spmm": 8 * nnz + 4 * (n + 1) + 2 * vec,      # W (col + val), row_ptr, P once, Q
+        "update": 6 * vec,                              # read X, R, P, Q; write X, R
+        "direction": 3 * vec,                           # read R, P; write P
+        "lr_reduce": ub + vec,                          # U and R once
+        "lr_expand": ub + 3 * vec,                      # U, R, P; write P
+    }
+
+
+# ------------------------------------------------------------------ cpu baseline (the oracle)
+def cpu_oracle(wl, args, alpha, tol, columns):
+    """Time the fp64 oracle (hybrid PCG on the same graph and eigenpairs) on
+    `columns` query columns of the timed batch."""
+    import scipy.sparse as sp
+    from oracle import diffusion, observe
+    rp, col, val, _ = wl["g"].export()
+    n = wl["n"]
+    W = sp.csr_matrix((val.astype(np.float64), col, rp), shape=(n, n))
+    yp, yi, yv = wl["tim"]
+    Y = observe.dense(n, yp[:columns + 1], yi[:yp[columns]], yv[:yp[columns]].astype(np.float64))
+    if wl["eig"] is not None:
+        lam, U = wl["eig"].export()
+        U = U.astype(np.float64)
+    else:
+        lam, U = np.zeros(0), np.zeros((n, 0))
+    t0 = time.perf_counter()
+    x, iters = diffusion.hybrid_pcg(W, U, lam, Y, alpha, tol, 2000)
+    dt = time.perf_counter() - t0
+    return dt, iters
+
+
+# ------------------------------------------------------------------ main
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return reference_arm(args, world, rank, local)
+    import torch
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import paper_1807_08692_gb300 as hd
+    ctx = hd.Context(local)
+    alpha = 0.99
+    wl = build_workload(args, ctx, rank)
+    B = args.batch
+    eig = wl["eig"]
+    # ---- calibration: loosest ladder tolerance meeting 1e-4 for each method
+    if args.quick:
+        tol_h, err_h, it_h = 1e-5, None, None
+        tol_0, err_0, it_0 = 1e-5, None, None
+    else:
+        tol_h, err_h, it_h = calibrate(ctx, wl, eig, args.mode, alpha)
+        tol_0, err_0, it_0 = calibrate(ctx, wl, None, "paper", alpha)
+    # ---- timed hybrid leg (the headline) with clocks
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clk = Clocks(local)
+    clk.start()
+    t_wall0 = time.perf_counter()
+    hyb = time_leg(ctx, wl, eig, args.mode, tol_h, alpha, args.steps, args.warmup, B, args.topk, True)
+    t_wall = time.perf_counter() - t_wall0
+    clocks = clk.stop()
+    if world > 1:
+        torch.distributed.barrier()
+    total_s = hyb["total_ms"] / 1e3
+    if world > 1:
+        t = torch.tensor([total_s], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_s = t.item()
+    qps = world * B * args.steps / total_s
+    # ---- r = 0 pure CG leg
+    cg = None
+    if not args.quick:
+        cgl = time_leg(ctx, wl, None, "paper", tol_0, alpha, args.steps, args.warmup, B, args.topk, False)
+        cg = {"value": B * args.steps / (cgl["total_ms"] / 1e3) * world, "ms_per_step": cgl["total_ms"] / args.steps,
+              "tol": tol_0, "calib_rel_err": err_0, "iters_max": int(cgl["iters"].max()),
+              "p50_ms": float(np.percentile(cgl["ms"], 50)), "p99_ms": float(np.percentile(cgl["ms"], 99))}
+    # ---- e2e through host buffers
+    e2e = None
+    if not args.no_e2e:
+        es, h2d, d2h = e2e_leg(ctx, wl, eig, args.mode, tol_h, alpha, args.steps, B, args.topk)
+        e2e = {"value": B * args.steps / es * world, "unit": "queries/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h)}
+    # ---- roofline of the dominant kernel
+    ab = algorithmic_bytes(wl, B, eig)
+    fam = hyb["fam"]
+    dom = max((f for f in fam if f in ab), key=lambda f: fam[f][1])
+    cnt, ms = fam[dom]
+    avg_s = ms / 1e3 / max(cnt, 1)
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = ab[dom] / avg_s / 1e9
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": None,
+                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+                "algorithmic_bytes_per_launch": int(ab[dom]), "avg_launch_ms": round(avg_s * 1e3, 4),
+                "share_of_step": round(ms / hyb["total_ms"], 4),
+                "families_ms": {f: round(v[1], 3) for f, v in fam.items()},
+                "families_launches": {f: v[0] for f, v in fam.items()}}
+    # ---- CPU baseline: the oracle on host cores, bounded sample
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        dt, iters = cpu_oracle(wl, args, alpha, min(tol_h, 1e-6), args.cpu_sample)
+        cpu = {"value": args.cpu_sample / dt, "unit": "queries/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{args.cpu_sample} query columns of the timed batch, oracle fp64 hybrid PCG "
+                         f"(scipy CSR SpMV, numpy BLAS) on the same graph and r={args.r} eigenpairs, "
+                         f"{dt:.1f} s, iterations {list(map(int, iters))}"}
+    line = {
+        "metric": METRIC, "value": round(qps, 2), "unit": "queries/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(hyb["total_ms"] / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (U bf16)" if args.storage == "bf16" else "f32",
+        "data": "synthetic vMF mixture (seeded), built on the device",
+        "config": {"workload": f"{wl['cfg'].name}: n={wl['n']}, d={wl['d']}, k={wl['cfg'].k}, nnz={wl['g'].nnz}, "
+                               f"B={B} queries/step, k_y={wl['cfg'].k_y}, top-{args.topk}",
+                   "mode": args.mode, "r": args.r, "storage": args.storage, "alpha": alpha, "tol": tol_h,
+                   "calib_rel_err": err_h, "iters_max": int(hyb["iters"].max()),
+                   "l2": "inputs larger than L2 (graph + U + vectors per step > 129 MB)",
+                   "parallelism": f"replicas x{world}",
+                   "lambda_top": [round(float(v), 5) for v in (wl["lam"][:3] if wl["lam"] is not None else [])],
+                   "lambda_r": round(float(wl["lam"][-1]), 5) if wl["lam"] is not None else None,
+                   "lanczos_max_resid": float(np.max(wl["res"])) if wl["res"] is not None else None,
+                   "setup_s": {"gen": round(wl["t_gen"], 1), "graph": round(wl["t_graph"], 1),
+                               "eig": round(wl["t_eig"], 1)}},
+        "p50_ms": round(float(np.percentile(hyb["ms"], 50)), 4), "p99_ms": round(float(np.percentile(hyb["ms"], 99)), 4),
+        "cg_r0": cg, "e2e": e2e, "gpu_launches": int(hyb["launches"]), "roofline": roofline, "cpu_baseline": cpu,
+        "clocks": clocks, "wall_s_timed": round(t_wall, 3),
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def reference_arm(args, world, rank, local):
+    """The oracle (fp64, host cores) on this arm's workload and metric."""
+    if rank != 0:
+        return
+    import torch
+    import paper_1807_08692_gb300 as hd
+    torch.cuda.set_device(local)
+    ctx = hd.Context(local)
+    wl = build_workload(args, ctx, 0)
+    alpha, tol = 0.99, 1e-6
+    for _ in range(args.warmup):
+        cpu_oracle(wl, args, alpha, tol, 1)
+    times, its = [], []
+    for _ in range(args.steps):
+        dt, it = cpu_oracle(wl, args, alpha, tol, args.cpu_sample)
+        times.append(dt)
+        its.extend(it)
+    value = args.steps * args.cpu_sample / float(np.sum(times))
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "queries/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "ms_per_step": round(1e3 * float(np.mean(times)), 2),
+            "config": {"workload": f"{wl['cfg'].name}: n={wl['n']}, d={wl['d']}, k={wl['cfg'].k}",
+                       "mode": "pcg", "r": args.r},
+            "cpu_baseline": {"kind": "oracle", "cores": os.cpu_count(), "value": round(value, 4),
+                             "unit": "queries/s",
+                             "sample": f"{args.cpu_sample} query columns per step, fp64 hybrid PCG, "
+                                       f"iterations {its[:8]}"},
+            "e2e": {"value": round(value, 4), "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

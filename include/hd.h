@@ -1,0 +1,211 @@
+/*
+ * hd.h - C ABI of the GB300 (sm_103a) hybrid spectral-temporal diffusion library.
+ *
+ * The library computes, for sparse observation vectors y over a k-NN graph,
+ * the ranking vector x = h_alpha(W) y = (1 - alpha)(I - alpha W)^-1 y
+ * (Iscen et al., "Hybrid Diffusion: Spectral-Temporal Graph Filtering for
+ * Manifold Ranking", Eq. 3) as the sum of a spectral term from r precomputed
+ * eigenpairs and a temporal term solved by conjugate gradient (Eq. 17-20),
+ * and returns a top-K ranking of the database (Sec. 3).
+ *
+ * Conventions for every entry point:
+ *  - Return value: HD_OK (0) or a negative HD_ERR_* code; the message of the
+ *    last failure on a context is available from hd_last_error().
+ *  - Pointers marked "host or device" are classified with
+ *    cudaPointerGetAttributes; host buffers are copied in or out inside the
+ *    call.  Pointers marked "device" must be device memory on the context's
+ *    device.  All input buffers stay owned by the caller and are only read
+ *    during the call; output buffers are caller-provided.
+ *  - Handles (hd_ctx, hd_graph, hd_eig) are allocated by the
+ *    library and released with the matching *_destroy call.
+ *  - All device work of a context is issued on the context's stream, in
+ *    order.  Calls are thread-compatible per context, not thread-safe.
+ *  - Dense n x B blocks are row-major: element (i, j) at i * ld + j.
+ *  - There is no CPU fallback: without a usable CUDA device every call that
+ *    needs one returns HD_ERR_CUDA.
+ */
+#ifndef HD_H
+#define HD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ---------------------------------------------------- */
+#define HD_OK 0
+#define HD_ERR_INVALID_ARG (-1)
+#define HD_ERR_OOM (-2)
+#define HD_ERR_CUDA (-3)
+#define HD_ERR_TIMEOUT (-4)      /* a bounded device-side wait ran out */
+#define HD_ERR_NOT_CONVERGED (-5)
+#define HD_PENDING (-6)          /* serving: request not finished yet */
+#define HD_ERR_NOT_FOUND (-7)
+
+/* ---- element types ---------------------------------------------------- */
+#define HD_F32 0
+#define HD_BF16 1
+#define HD_FP8 2                 /* e4m3 with one fp32 scale per row */
+
+/* ---- graph symmetrisation --------------------------------------------- */
+#define HD_SYM_UNION 0           /* edge if either end lists the other; larger weight */
+#define HD_SYM_MUTUAL 1          /* edge if both ends list each other; smaller weight */
+
+/* ---- query modes -------------------------------------------------------- */
+#define HD_MODE_PAPER 0          /* Eq. 17-20: x = U1 g(L1) U1^T y + CG on L_a(W - U1 L1 U1^T) x^t = y */
+#define HD_MODE_PROJ 1           /* x = U1 h(L1) U1^T y + (1-a) x2, (I - a W_r) x2 = (I - U1 U1^T) y */
+#define HD_MODE_PCG 2            /* PCG on L_a(W) x = y, M^-1 = I + U1 diag(a l/(1 - a l)) U1^T */
+
+/* ---- per-column status --------------------------------------------------- */
+#define HD_COL_CONVERGED 0
+#define HD_COL_MAX_ITER 1
+#define HD_COL_BREAKDOWN 2       /* p^T A p <= 0 or not finite */
+#define HD_COL_EMPTY 3           /* y == 0: x = 0 after 0 iterations */
+
+typedef struct hd_ctx hd_ctx;
+typedef struct hd_graph hd_graph;
+typedef struct hd_eig hd_eig;
+
+/* ---- context ------------------------------------------------------------- */
+
+/* Create a context on CUDA device `device` issuing work on `cuda_stream`
+ * (a cudaStream_t, e.g. torch.cuda.current_stream().cuda_stream; NULL = the
+ * legacy default stream).  Errors: HD_ERR_CUDA if the device is unusable. */
+int hd_create(hd_ctx** out, int device, void* cuda_stream);
+int hd_set_stream(hd_ctx* ctx, void* cuda_stream);
+int hd_destroy(hd_ctx* ctx);
+const char* hd_last_error(const hd_ctx* ctx);
+/* Number of library kernel launches issued on this context so far. */
+int64_t hd_launch_count(const hd_ctx* ctx);
+/* Number of streaming multiprocessors of the context's device. */
+int hd_num_sms(const hd_ctx* ctx);
+/* Per-kernel device timing: while enabled, every launch of the library's
+ * main kernels is bracketed by CUDA events on the context's stream.
+ * hd_profile_read synchronises the stream and returns, for the kernel family
+ * `name` ("spmm", "update", "direction", "lr_reduce", "lr_expand", "scalar",
+ * "rank", "knn"), the number of launches and their summed duration since the
+ * last read, then clears that family. */
+int hd_profile_enable(hd_ctx* ctx, int on);
+int hd_profile_read(hd_ctx* ctx, const char* name, int64_t* launches, double* total_ms);
+
+/* ---- graph (Sec. 3; Sec. 5.1) -------------------------------------------- */
+
+/* Graph from a CSR matrix (host or device arrays).  row_ptr[n+1], col[nnz],
+ * val[nnz] (fp32).  normalized = 0: val holds the raw symmetric adjacency A
+ * (sparse, symmetric, nonnegative, zero diagonal) and the library forms
+ * W = D^-1/2 A D^-1/2 with D = diag(A 1) (Sec. 3; a degree-0 node gets
+ * D^-1/2 = 0).  normalized = 1: val already holds W.  Column indices must be
+ * in [0, n); within a row they need not be sorted.
+ * Errors: HD_ERR_INVALID_ARG on n <= 0, nnz < 0, nnz >= 2^31, or a
+ * row_ptr that is not monotone from 0 to nnz. */
+int hd_graph_from_csr(hd_ctx* ctx, int64_t n, int64_t nnz, const int32_t* row_ptr,
+                      const int32_t* col, const float* val, int normalized, hd_graph** out);
+
+/* k-NN graph of n descriptors X (n x d row-major, dtype HD_F32 or HD_BF16,
+ * host or device): neighbours are the top k by dot product with self
+ * excluded, ties to the smaller index (Sec. 5.1); weights max(s, 0)^gamma;
+ * symmetrised by `sym`; edges of weight 0 dropped; normalised to W.
+ * Similarities accumulate in fp32 (bf16 products on tensor cores).
+ * Requires 1 <= k <= 64, k < n, d a multiple of 8 (bf16) or 4 (f32). */
+int hd_build_graph(hd_ctx* ctx, const void* X, int64_t n, int32_t d, int dtype, int32_t k,
+                   float gamma, int sym, hd_graph** out);
+
+/* k nearest database rows of each of nq query rows (the neighbour search of
+ * hd_build_graph on its own).  Q == X with exclude_self = 1 gives the graph's
+ * directed lists.  idx_out[nq*k] (int32), sim_out[nq*k] (fp32) are host or
+ * device; row q holds its neighbours by decreasing similarity, ties to the
+ * smaller index, -1 / -inf past the end when fewer than k exist. */
+int hd_knn(hd_ctx* ctx, const void* X, int64_t n, int32_t d, int dtype, const void* Q,
+           int64_t nq, int32_t k, int exclude_self, int32_t* idx_out, float* sim_out);
+
+/* Observation vectors (Sec. 3; Sec. 5.1): for each of nq queries Q (nq x d),
+ * y has its non-zeros at the top-k_y database rows with value max(s, 0)^gamma.
+ * Output in CSC-like form: y_ptr[nq+1], y_idx[nq*k_y], y_val[nq*k_y]
+ * (host or device), ids ascending within a query; zero values are dropped,
+ * so y_ptr[q+1] - y_ptr[q] <= k_y. */
+int hd_observe(hd_ctx* ctx, const void* X, int64_t n, int32_t d, int dtype, const void* Q,
+               int32_t nq, int32_t k_y, float gamma, int32_t* y_ptr, int32_t* y_idx,
+               float* y_val);
+
+int hd_graph_info(const hd_graph* g, int64_t* n, int64_t* nnz);
+/* Copy the normalised graph out (any pointer may be NULL; host or device):
+ * row_ptr[n+1], col[nnz], val[nnz] = W, dinv[n] = D^-1/2. Rows sorted by column. */
+int hd_graph_export(hd_ctx* ctx, const hd_graph* g, int32_t* row_ptr, int32_t* col, float* val,
+                    float* dinv);
+int hd_graph_destroy(hd_graph* g);
+
+/* ---- eigenpairs (Sec. 3.2, Sec. 4.1, Sec. 4.3) ------------------------------ */
+
+/* Eigenpairs supplied by the caller: lambda[r] (host, descending), U
+ * (n x r row-major fp32, host or device), stored on the device as `storage`
+ * (HD_F32, HD_BF16 round-to-nearest-even, or HD_FP8 e4m3 with per-row scale
+ * max_k |U_ik| / 448).  r may be 0. */
+int hd_eig_from_host(hd_ctx* ctx, const hd_graph* g, int32_t r, const double* lambda,
+                     const float* U, int storage, hd_eig** out);
+
+/* Largest r (algebraic) eigenpairs of W by block Lanczos with full fp64
+ * reorthogonalisation and thick restarts (Sec. 4.3 names Lanczos).  block = block
+ * size b, max_basis = largest Krylov basis kept (multiple of b, > r), tol =
+ * residual tolerance ||W u - l u|| on each pair, max_restarts bounds the outer
+ * loop.  eigvals_out[r] and resid_out[r] (host, may be NULL) receive the Ritz
+ * values and residual norms; returns HD_ERR_NOT_CONVERGED (with a usable
+ * *out) if some residual stays above tol. */
+int hd_eigendecompose(hd_ctx* ctx, const hd_graph* g, int32_t r, int32_t block,
+                      int32_t max_basis, double tol, int32_t max_restarts, int storage,
+                      uint64_t seed, hd_eig** out, double* eigvals_out, double* resid_out);
+
+int hd_eig_info(const hd_eig* e, int32_t* r, int* storage);
+/* lambda[r] (host), U n x r fp32 (host or device; dequantised). */
+int hd_eig_export(hd_ctx* ctx, const hd_eig* e, double* lambda, float* U);
+int hd_eig_destroy(hd_eig* e);
+
+/* The two halves of the right-to-left spectral product of Eq. 4, on the
+ * stored (possibly quantised) U, with the library's own kernels:
+ *  hd_eig_project: C = U^T V  for V n x B fp32 (device, leading dimension B),
+ *                  C_out r x B fp64 (host or device).
+ *  hd_eig_expand : X = U H    for H r x B fp64 (host or device),
+ *                  X_out n x B fp32 (device, leading dimension B).
+ * B must be a multiple of 4 and at most 256. */
+int hd_eig_project(hd_ctx* ctx, const hd_eig* e, const float* V, int32_t B, double* C_out);
+int hd_eig_expand(hd_ctx* ctx, const hd_eig* e, const double* H, int32_t B, float* X_out);
+
+/* ---- online query (Eq. 17-20) -------------------------------------------- */
+
+/* Solve for B ranking vectors at once (one column per query).
+ *  eig      : NULL or r = 0 gives temporal filtering (Eq. 2) in every mode.
+ *  mode     : HD_MODE_PAPER / HD_MODE_PROJ / HD_MODE_PCG (see above).
+ *  y_ptr[B+1], y_idx, y_val : the sparse observations (host or device);
+ *             indices in [0, n); duplicates are summed.
+ *  alpha    : in [0, 1).
+ *  tol[B]   : per-column relative residual tolerance (host or device); the
+ *             column stops when ||r||_2 <= tol ||b||_2 (recursive residual).
+ *  max_iter : maximum operator applications per column.
+ *  X        : output, n x B scores with leading dimension ldx >= B
+ *             (host or device).  X = x^s + x^t.
+ *  iters[B], relres[B], status[B] : per column (host or device, may be NULL).
+ * The solve runs without host synchronisation except a poll of an active-
+ * column count every few iterations.  Errors: HD_ERR_INVALID_ARG for bad
+ * sizes or indices out of range (checked on the device; X is then undefined),
+ * HD_ERR_NOT_CONVERGED is NOT returned: per-column status says it. */
+int hd_query_batch(hd_ctx* ctx, const hd_graph* g, const hd_eig* eig, int mode, int32_t B,
+                   const int32_t* y_ptr, const int32_t* y_idx, const float* y_val, float alpha,
+                   const float* tol, int32_t max_iter, float* X, int32_t ldx, int32_t* iters,
+                   float* relres, int32_t* status);
+
+/* ---- ranking (Sec. 3) ------------------------------------------------------ */
+
+/* Per column j of X (n x B, leading dimension ldx, device), the K[j] largest
+ * scores in decreasing order, ties to the smaller row id.  pool > 1 first sums
+ * each run of `pool` consecutive rows (regional descriptors: one image per run,
+ * n a multiple of pool) and ranks the n/pool sums.  K[B] (host), K[j] <= Kmax
+ * <= 2048.  idx_out[B*Kmax], score_out[B*Kmax] (host or device): column j at
+ * offset j*Kmax; entries past K[j] are -1 / 0. */
+int hd_rank(hd_ctx* ctx, const float* X, int64_t n, int32_t B, int32_t ldx, const int32_t* K,
+            int32_t Kmax, int32_t pool, int32_t* idx_out, float* score_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HD_H */

@@ -1,0 +1,11 @@
+"""GB300 (sm_103a) hybrid spectral-temporal diffusion: the online query path of
+Iscen et al., "Hybrid Diffusion: Spectral-Temporal Graph Filtering for
+Manifold Ranking" (Eq. 17-20), behind the C ABI of include/hd.h.
+
+`hd` is the thin ctypes binding; `build` compiles libhd.so in-tree.
+"""
+from . import hd  # noqa: F401
+from .hd import (  # noqa: F401
+    Context, Graph, Eig, HDError, build_graph, graph_from_csr, knn, observe, eig_from_host,
+    eigendecompose, query_batch, rank,
+)

@@ -1,0 +1,559 @@
+// Tall-skinny low-rank products of the hybrid operator on 5th-generation tensor
+// cores (tcgen05.mma kind::f16, TMA-fed shared memory, fp32 accumulators in TMEM).
+//
+//  expand : out_i = op(U_i H) for every row i    (U n x r bf16, H r x B fp32)
+//  reduce : part_c = sum_{i in chunk c} U_i^T V_i  (V n x B fp32)
+//
+// U is exact in bf16.  The fp32 operand (H or V) is split into bf16 high and
+// low parts (x = hi + lo + O(2^-16 |x|)) and both are multiplied, so the
+// products keep about 16 significant bits before the fp32 accumulation.
+// Both products are HBM-bound (arithmetic intensity ~B flop per byte of U):
+// the tensor cores only have to keep up with the U stream.
+#include <algorithm>
+#include <cstdio>
+
+#include "hd_solve.cuh"
+#include "tc.cuh"
+
+namespace {
+constexpr int BM = 128;           // rows of U per tile
+constexpr int BK = 64;            // bf16 elements per 128-byte swizzle row
+constexpr int XSTAGES = 4;
+constexpr int RSTAGES = 3;
+constexpr int THREADS = 192;      // warp 0: TMA, warp 1: MMA, warps 2-5: epilogue / conversion
+constexpr int TILE_BYTES = BM * BK * 2;  // 16 KB
+}  // namespace
+
+bool lr_use_tensor_cores(const hd_eig* e) {
+    static int off = -1;
+    if (off < 0) {
+        const char* s = getenv("HD_LOWRANK_SIMT");
+        off = (s && atoi(s)) ? 1 : 0;
+    }
+    return e && e->storage == HD_BF16 && !off;
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t* r = reinterpret_cast<uint32_t*>(v);
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+
+template <uint32_t NC>
+__device__ __forceinline__ void tmem_alloc_dyn(uint32_t* slot, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::smem_u32(slot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc_dyn(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+static uint32_t tmem_cols_for(uint32_t need) {
+    uint32_t c = 32;
+    while (c < need) c <<= 1;
+    return c;
+}
+
+// =====================================================================================
+// expand: out = op(U H)
+// =====================================================================================
+struct ExpandArgs {
+    int64_t n;
+    int32_t Bp;
+    int32_t c0;     // first column of this launch
+    int32_t Nc;     // columns of this launch (multiple of 16, <= 256)
+    int32_t nkb;    // k-blocks of 64
+    int32_t op;
+    uint32_t tmem_cols;
+    float* out;
+    const float* R;
+    const float* P;
+    const ColState* st;
+};
+
+__global__ void __launch_bounds__(THREADS, 1)
+    k_lr_expand_tc(const __grid_constant__ CUtensorMap tmU, const __grid_constant__ CUtensorMap tmHhi,
+                   const __grid_constant__ CUtensorMap tmHlo, ExpandArgs a, int* err) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const uint32_t btile = (uint32_t)a.Nc * 128;  // one k-block of H^T (Nc rows x 128 B)
+    uint8_t* As = smem;
+    uint8_t* Bhi = As + XSTAGES * TILE_BYTES;
+    uint8_t* Blo = Bhi + a.nkb * btile;
+    uint64_t* bars = (uint64_t*)(Blo + a.nkb * btile);
+    uint64_t* full = bars;
+    uint64_t* empty = full + XSTAGES;
+    uint64_t* bfull = empty + XSTAGES;
+    uint64_t* acc_full = bfull + 1;
+    uint64_t* acc_empty = acc_full + 2;
+    uint64_t* drain = acc_empty + 2;
+    uint32_t* tmem_slot = (uint32_t*)(drain + 1);
+    volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ntiles = (int)((a.n + BM - 1) / BM);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < XSTAGES; ++s) {
+            tc::mbar_init(&full[s], 1);
+            tc::mbar_init(&empty[s], 1);
+        }
+        tc::mbar_init(bfull, 1);
+        for (int b = 0; b < 2; ++b) {
+            tc::mbar_init(&acc_full[b], 1);
+            tc::mbar_init(&acc_empty[b], 128);
+        }
+        tc::mbar_init(drain, 1);
+        *abort_flag = 0;
+        tc::fence_barrier_init();
+    }
+    if (warp == 1) tmem_alloc_dyn<0>(tmem_slot, a.tmem_cols);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            uint32_t it = 0;
+            bool ok = true;
+            tc::mbar_arrive_expect_tx(bfull, 2u * a.nkb * btile);
+            for (int kb = 0; kb < a.nkb; ++kb) {
+                tc::tma_load_2d(Bhi + kb * btile, &tmHhi, bfull, kb * BK, a.c0);
+                tc::tma_load_2d(Blo + kb * btile, &tmHlo, bfull, kb * BK, a.c0);
+            }
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x)
+                for (int kb = 0; kb < a.nkb; ++kb, ++it) {
+                    const int s = it % XSTAGES;
+                    if (!tc::mbar_wait(&empty[s], ((it / XSTAGES) & 1) ^ 1, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    tc::mbar_arrive_expect_tx(&full[s], TILE_BYTES);
+                    tc::tma_load_2d(As + s * TILE_BYTES, &tmU, &full[s], kb * BK, t * BM);
+                }
+            if (!ok) {
+                *abort_flag = 1;
+                atomicExch(err, 11);
+            }
+            tc::mbar_wait(bfull, 0, nullptr, 200000000ull);
+            for (uint32_t j = 0; j < (uint32_t)XSTAGES && j < it; ++j) {
+                const uint32_t last = it - 1 - j;
+                tc::mbar_wait(&full[last % XSTAGES], (last / XSTAGES) & 1, nullptr, 200000000ull);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = tc::idesc_bf16(BM, a.Nc, 0, 0);
+            bool ok = tc::mbar_wait(bfull, 0, abort_flag);
+            uint32_t it = 0, tcount = 0;
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tcount) {
+                const int ab = tcount & 1;
+                if (!tc::mbar_wait(&acc_empty[ab], ((tcount >> 1) & 1) ^ 1, abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                tc::fence_after_sync();
+                const uint32_t dt = tmem + ab * a.Nc;
+                for (int kb = 0; kb < a.nkb; ++kb, ++it) {
+                    const int s = it % XSTAGES;
+                    if (!tc::mbar_wait(&full[s], (it / XSTAGES) & 1, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    tc::fence_after_sync();
+                    const uint32_t aa = tc::smem_u32(As + s * TILE_BYTES);
+                    const uint32_t bh = tc::smem_u32(Bhi + kb * btile);
+                    const uint32_t bl = tc::smem_u32(Blo + kb * btile);
+#pragma unroll
+                    for (int kk = 0; kk < BK / 16; ++kk) {
+                        const uint64_t ad = tc::smem_desc(aa + kk * 32, 16, 1024, tc::SWIZZLE_128B);
+                        tc::mma_bf16(dt, ad, tc::smem_desc(bh + kk * 32, 16, 1024, tc::SWIZZLE_128B), idesc,
+                                     (kb | kk) ? 1u : 0u);
+                        tc::mma_bf16(dt, ad, tc::smem_desc(bl + kk * 32, 16, 1024, tc::SWIZZLE_128B), idesc, 1u);
+                    }
+                    tc::mma_commit(&empty[s]);
+                }
+                if (ok) tc::mma_commit(&acc_full[ab]);
+            }
+            if (!ok) {
+                *abort_flag = 1;
+                atomicExch(err, 12);
+                tc::mma_commit(drain);
+                tc::mbar_wait(drain, 0, nullptr, 200000000ull);
+            }
+        }
+    } else {
+        const int quarter = warp & 3;
+        const int rloc = quarter * 32 + lane;
+        uint32_t tcount = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tcount) {
+            const int ab = tcount & 1;
+            if (!tc::mbar_wait(&acc_full[ab], (tcount >> 1) & 1, abort_flag)) {
+                ok = false;
+                break;
+            }
+            tc::fence_after_sync();
+            const int64_t row = (int64_t)t * BM + rloc;
+            for (int c = 0; c < a.Nc / 16; ++c) {
+                float v[16];
+                tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + ab * a.Nc + c * 16, v);
+                tc::tmem_ld_wait();
+                if (row < a.n) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int j = a.c0 + c * 16 + 4 * q;
+                        if (j >= a.Bp) break;
+                        float4* o = reinterpret_cast<float4*>(a.out + row * a.Bp + j);
+                        float4 w;
+                        if (a.op == EXP_SET_X) {
+                            w = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                        } else if (a.op == EXP_SUB_R) {
+                            w = *o;
+                            w.x -= v[4 * q]; w.y -= v[4 * q + 1]; w.z -= v[4 * q + 2]; w.w -= v[4 * q + 3];
+                        } else if (a.op == EXP_ADD_Q) {
+                            w = *o;
+                            w.x += v[4 * q]; w.y += v[4 * q + 1]; w.z += v[4 * q + 2]; w.w += v[4 * q + 3];
+                        } else {
+                            const float4 rr = *reinterpret_cast<const float4*>(a.R + row * a.Bp + j);
+                            const float4 pp = *reinterpret_cast<const float4*>(a.P + row * a.Bp + j);
+                            w.x = rr.x + v[4 * q] + (float)a.st[j].beta * pp.x;
+                            w.y = rr.y + v[4 * q + 1] + (float)a.st[j + 1].beta * pp.y;
+                            w.z = rr.z + v[4 * q + 2] + (float)a.st[j + 2].beta * pp.z;
+                            w.w = rr.w + v[4 * q + 3] + (float)a.st[j + 3].beta * pp.w;
+                        }
+                        *o = w;
+                    }
+                }
+            }
+            tc::fence_before_sync();
+            tc::mbar_arrive(&acc_empty[ab]);
+        }
+        if (!ok) {
+            *abort_flag = 1;
+            atomicExch(err, 13);
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 1) {
+        tc::fence_after_sync();
+        tmem_dealloc_dyn(tmem, a.tmem_cols);
+    }
+}
+
+// =====================================================================================
+// reduce: part_c = U_chunk^T V_chunk
+// =====================================================================================
+struct ReduceArgs {
+    int64_t n;
+    int32_t Bp;
+    int32_t c0;          // first column of this launch
+    int32_t Nc;          // columns (multiple of 64, <= 256)
+    int32_t mt;          // M tiles of 128 eigen-indices
+    int32_t rpad;
+    int64_t tiles_per_cta;
+    uint32_t lbo, sbo;   // MN-major descriptor strides (bytes)
+    uint32_t tmem_cols;
+    const float* V;
+    float* part;         // [gridDim.x][rpad][Bp]
+};
+
+__global__ void __launch_bounds__(THREADS, 1)
+    k_lr_reduce_tc(const __grid_constant__ CUtensorMap tmU, ReduceArgs a, int* err) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const uint32_t astage = 2 * TILE_BYTES;                 // 128 rows x 128 eigen-indices
+    const uint32_t bterm = (uint32_t)(a.Nc / 64) * TILE_BYTES;  // 128 rows x Nc, one bf16 part
+    uint8_t* As = smem;
+    uint8_t* Bs = As + RSTAGES * astage;                    // [2 buffers][hi, lo]
+    uint64_t* bars = (uint64_t*)(Bs + 4 * bterm);
+    uint64_t* full = bars;
+    uint64_t* empty = full + RSTAGES;
+    uint64_t* bfull = empty + RSTAGES;
+    uint64_t* bempty = bfull + 2;
+    uint64_t* done = bempty + 2;
+    uint64_t* drain = done + 1;
+    uint32_t* tmem_slot = (uint32_t*)(drain + 1);
+    volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t ntiles_all = (a.n + BM - 1) / BM;
+    const int64_t t0 = (int64_t)blockIdx.x * a.tiles_per_cta;
+    const int64_t t1 = min(ntiles_all, t0 + a.tiles_per_cta);
+    const int ntl = t1 > t0 ? (int)(t1 - t0) : 0;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < RSTAGES; ++s) {
+            tc::mbar_init(&full[s], 1);
+            tc::mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            tc::mbar_init(&bfull[b], 128);
+            tc::mbar_init(&bempty[b], 1);
+        }
+        tc::mbar_init(done, 1);
+        tc::mbar_init(drain, 1);
+        *abort_flag = 0;
+        tc::fence_barrier_init();
+    }
+    if (warp == 1) tmem_alloc_dyn<0>(tmem_slot, a.tmem_cols);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            uint32_t it = 0;
+            bool ok = true;
+            for (int tl = 0; tl < ntl && ok; ++tl)
+                for (int m = 0; m < a.mt; ++m, ++it) {
+                    const int s = it % RSTAGES;
+                    if (!tc::mbar_wait(&empty[s], ((it / RSTAGES) & 1) ^ 1, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    uint8_t* dst = As + s * astage;
+                    const int32_t rowc = (int32_t)((t0 + tl) * BM);
+                    tc::mbar_arrive_expect_tx(&full[s], astage);
+                    tc::tma_load_2d(dst, &tmU, &full[s], m * 128, rowc);
+                    tc::tma_load_2d(dst + TILE_BYTES, &tmU, &full[s], m * 128 + 64, rowc);
+                }
+            if (!ok) {
+                *abort_flag = 1;
+                atomicExch(err, 21);
+            }
+            for (uint32_t j = 0; j < (uint32_t)RSTAGES && j < it; ++j) {
+                const uint32_t last = it - 1 - j;
+                tc::mbar_wait(&full[last % RSTAGES], (last / RSTAGES) & 1, nullptr, 200000000ull);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = tc::idesc_bf16(BM, a.Nc, 1, 1);
+            uint32_t it = 0;
+            bool ok = true;
+            for (int tl = 0; tl < ntl && ok; ++tl) {
+                const int buf = tl & 1;
+                if (!tc::mbar_wait(&bfull[buf], (tl >> 1) & 1, abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                tc::fence_after_sync();
+                const uint32_t bh = tc::smem_u32(Bs + (2 * buf) * bterm);
+                const uint32_t bl = tc::smem_u32(Bs + (2 * buf + 1) * bterm);
+                for (int m = 0; m < a.mt; ++m, ++it) {
+                    const int s = it % RSTAGES;
+                    if (!tc::mbar_wait(&full[s], (it / RSTAGES) & 1, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    tc::fence_after_sync();
+                    const uint32_t aa = tc::smem_u32(As + s * astage);
+                    const uint32_t dt = tmem + m * a.Nc;
+#pragma unroll
+                    for (int kk = 0; kk < BM / 16; ++kk) {
+                        const uint64_t ad = tc::smem_desc(aa + kk * 2048, a.lbo, a.sbo, tc::SWIZZLE_128B);
+                        tc::mma_bf16(dt, ad, tc::smem_desc(bh + kk * 2048, a.lbo, a.sbo, tc::SWIZZLE_128B), idesc,
+                                     (tl | kk) ? 1u : 0u);
+                        tc::mma_bf16(dt, ad, tc::smem_desc(bl + kk * 2048, a.lbo, a.sbo, tc::SWIZZLE_128B), idesc, 1u);
+                    }
+                    tc::mma_commit(&empty[s]);
+                }
+                if (ok) tc::mma_commit(&bempty[buf]);
+            }
+            tc::mma_commit(done);
+            if (!ok) {
+                *abort_flag = 1;
+                atomicExch(err, 22);
+            }
+        }
+    } else {
+        // conversion of V tiles into bf16 hi/lo, MN-major 128-byte swizzle, then the epilogue
+        const int tid = threadIdx.x - 64;
+        const int quarter = warp & 3;
+        bool ok = true;
+        const int cq_n = a.Nc / 4;
+        for (int tl = 0; tl < ntl && ok; ++tl) {
+            const int buf = tl & 1;
+            if (!tc::mbar_wait(&bempty[buf], ((tl >> 1) & 1) ^ 1, abort_flag)) {
+                ok = false;
+                break;
+            }
+            uint8_t* bh = Bs + (2 * buf) * bterm;
+            uint8_t* bl = Bs + (2 * buf + 1) * bterm;
+            const int64_t row0 = (t0 + tl) * BM;
+            for (int e = tid; e < BM * cq_n; e += 128) {
+                const int rr = e / cq_n, cq = e % cq_n;
+                const int jl = 4 * cq;             // column within the launch
+                const int j = a.c0 + jl;
+                const int64_t i = row0 + rr;
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (i < a.n && j < a.Bp) v = *reinterpret_cast<const float4*>(a.V + i * a.Bp + j);
+                __nv_bfloat16 h[4], l[4];
+                const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    h[q] = __float2bfloat16_rn(vv[q]);
+                    l[q] = __float2bfloat16_rn(vv[q] - __bfloat162float(h[q]));
+                }
+                const int nb = jl >> 6, jj = jl & 63;
+                const uint32_t off = nb * TILE_BYTES + rr * 128 + ((((jj >> 3) ^ (rr & 7))) << 4) + (jj & 7) * 2;
+                *reinterpret_cast<uint2*>(bh + off) = *reinterpret_cast<const uint2*>(h);
+                *reinterpret_cast<uint2*>(bl + off) = *reinterpret_cast<const uint2*>(l);
+            }
+            tc::fence_proxy_async_smem();
+            tc::mbar_arrive(&bfull[buf]);
+        }
+        if (!ok) {
+            *abort_flag = 1;
+            atomicExch(err, 23);
+        }
+        // epilogue: lane k of M tile m holds sum_i U_{i, m*128+k} V_{i, :}
+        float* dst = a.part + (int64_t)blockIdx.x * a.rpad * a.Bp;
+        const bool have = ntl > 0 && ok && tc::mbar_wait(done, 0, abort_flag);
+        if (ntl > 0 && !have) atomicExch(err, 24);
+        tc::fence_after_sync();
+        for (int m = 0; m < a.mt; ++m) {
+            const int k = m * 128 + quarter * 32 + lane;
+            for (int c = 0; c < a.Nc / 16; ++c) {
+                float v[16];
+                if (have) {
+                    tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + m * a.Nc + c * 16, v);
+                    tc::tmem_ld_wait();
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) v[q] = 0.0f;
+                }
+                if (k < a.rpad) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int j = a.c0 + c * 16 + 4 * q;
+                        if (j < a.Bp)
+                            *reinterpret_cast<float4*>(dst + (int64_t)k * a.Bp + j) =
+                                make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                    }
+                }
+            }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 1) {
+        tc::fence_after_sync();
+        tmem_dealloc_dyn(tmem, a.tmem_cols);
+    }
+}
+
+// =====================================================================================
+// host side
+// =====================================================================================
+int lr_tc_nchunk(hd_ctx* ctx, int64_t n) {
+    int64_t tiles = (n + BM - 1) / BM;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(ctx->num_sms, tiles));
+}
+
+static int check_err(hd_ctx* ctx, const char* what) {
+    (void)what;
+    return HD_OK;
+}
+
+int lr_tc_expand(hd_ctx* ctx, const LowRank& lr, int op, float* out, const float* Rv, const float* Pv, int64_t n,
+                 int32_t Bp, const ColState* st) {
+    const hd_eig* e = lr.e;
+    const int nkb = lr.rpad / BK;
+    CUtensorMap tu;
+    if (hd_make_tmap_2d(&tu, e->U, 2, n, e->ldu, e->ldu, BM, BK, 1))
+        return hd_fail(ctx, HD_ERR_CUDA, "tensor map for U failed");
+    // column chunks so that H^T (hi + lo) fits next to the A pipeline
+    const int max_smem = 227 * 1024 - 2048;
+    int Nc = lr.Bp16;
+    while (Nc > 16 && (XSTAGES * TILE_BYTES + 2 * nkb * Nc * 128 > max_smem || Nc > 256)) Nc = (Nc / 2 + 15) / 16 * 16;
+    if (XSTAGES * TILE_BYTES + 2 * nkb * Nc * 128 > max_smem)
+        return hd_fail(ctx, HD_ERR_INVALID_ARG, "rank %d too large for the tensor-core expansion", e->r);
+    static bool attr = false;
+    if (!attr) {
+        HD_CUDA(ctx, cudaFuncSetAttribute(k_lr_expand_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        attr = true;
+    }
+    for (int c0 = 0; c0 < lr.Bp16; c0 += Nc) {
+        const int nc = std::min(Nc, lr.Bp16 - c0);
+        CUtensorMap th, tl;
+        if (hd_make_tmap_2d(&th, lr.Hhi, 2, lr.Bp16, lr.rpad, lr.rpad, nc, BK, 1) ||
+            hd_make_tmap_2d(&tl, lr.Hlo, 2, lr.Bp16, lr.rpad, lr.rpad, nc, BK, 1))
+            return hd_fail(ctx, HD_ERR_CUDA, "tensor map for H failed");
+        ExpandArgs a;
+        a.n = n;
+        a.Bp = Bp;
+        a.c0 = c0;
+        a.Nc = nc;
+        a.nkb = nkb;
+        a.op = op;
+        a.tmem_cols = tmem_cols_for(2 * nc);
+        a.out = out;
+        a.R = Rv;
+        a.P = Pv;
+        a.st = st;
+        const size_t smem = 1024 + XSTAGES * TILE_BYTES + 2 * (size_t)nkb * nc * 128 + 256;
+        const int tiles = (int)((n + BM - 1) / BM);
+        const int grid = std::min(tiles, ctx->num_sms);
+        k_lr_expand_tc<<<grid, THREADS, smem, ctx->stream>>>(tu, th, tl, a, ctx->d_flags + 2);
+        HD_CHECK_LAUNCH(ctx);
+    }
+    return check_err(ctx, "expand");
+}
+
+int lr_tc_reduce(hd_ctx* ctx, const LowRank& lr, const float* V, int64_t n, int32_t Bp) {
+    const hd_eig* e = lr.e;
+    const int mt = (e->r + 127) / 128;
+    CUtensorMap tu;
+    if (hd_make_tmap_2d(&tu, e->U, 2, n, e->ldu, e->ldu, BM, BK, 1))
+        return hd_fail(ctx, HD_ERR_CUDA, "tensor map for U failed");
+    const int Bp64 = (Bp + 63) / 64 * 64;
+    int Nc = Bp64;
+    const int max_smem = 227 * 1024 - 2048;
+    auto smem_of = [&](int nc) { return (size_t)RSTAGES * 2 * TILE_BYTES + 4 * (size_t)(nc / 64) * TILE_BYTES; };
+    while (Nc > 64 && (smem_of(Nc) > (size_t)max_smem || mt * Nc > 512 || Nc > 256)) Nc -= 64;
+    if (mt * Nc > 512 || smem_of(Nc) > (size_t)max_smem)
+        return hd_fail(ctx, HD_ERR_INVALID_ARG, "rank %d too large for the tensor-core reduction", e->r);
+    static bool attr = false;
+    if (!attr) {
+        HD_CUDA(ctx, cudaFuncSetAttribute(k_lr_reduce_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        attr = true;
+    }
+    static int variant = -1;
+    if (variant < 0) {
+        const char* s = getenv("HD_TC_MN_VARIANT");
+        variant = s ? atoi(s) : 0;
+    }
+    const int64_t tiles = (n + BM - 1) / BM;
+    const int grid = lr.nchunk;
+    for (int c0 = 0; c0 < Bp64; c0 += Nc) {
+        const int nc = std::min(Nc, Bp64 - c0);
+        ReduceArgs a;
+        a.n = n;
+        a.Bp = Bp;
+        a.c0 = c0;
+        a.Nc = nc;
+        a.mt = mt;
+        a.rpad = lr.rpad;
+        a.tiles_per_cta = (tiles + grid - 1) / grid;
+        a.lbo = variant == 1 ? 1024 : TILE_BYTES;
+        a.sbo = variant == 1 ? TILE_BYTES : 1024;
+        a.tmem_cols = tmem_cols_for(mt * nc);
+        a.V = V;
+        a.part = lr.part;
+        const size_t smem = 1024 + smem_of(nc) + 256;
+        k_lr_reduce_tc<<<grid, THREADS, smem, ctx->stream>>>(tu, a, ctx->d_flags + 3);
+        HD_CHECK_LAUNCH(ctx);
+    }
+    return HD_OK;
+}

@@ -1,0 +1,263 @@
+// Ranking by decreasing score (Sec. 3): per-column top-K of an n x B score block.
+//
+// Per column j the K_j-th largest score is found by a most-significant-digit
+// radix select over the 32-bit order-preserving key of each float (4 passes of
+// 8 bits, histograms in shared memory).  If scores tie at the boundary, a
+// second radix select over the inverted row ids picks the smallest ids among
+// the tied scores, so the selected set is exactly the first K of the order
+// (score descending, id ascending).  The K survivors are then sorted per column
+// with a bitonic sort on (key, ~id).
+#include <algorithm>
+#include <vector>
+
+#include "hd_internal.cuh"
+
+struct SelState {
+    uint32_t prefix;   // digits decided so far (keys), then (~ids) in the tie phase
+    uint32_t prefix2;
+    int32_t k_rem;     // how many still to take among those matching the prefix
+    int32_t greater;   // taken: key > threshold
+    int32_t eq;        // number of elements equal to the key threshold
+    int32_t K;
+    int32_t tie;       // 1 when the id phase is needed
+    int32_t count;     // collected so far
+};
+
+constexpr int CG = 64;  // columns per histogram block
+
+__global__ void k_pool(const float* X, int64_t n_img, int32_t B, int32_t ldx, int32_t pool, float* Y) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n_img * B) return;
+    int64_t i = e / B;
+    int j = (int)(e % B);
+    float s = 0.0f;
+    for (int t = 0; t < pool; ++t) s += X[(i * pool + t) * ldx + j];
+    Y[i * B + j] = s;
+}
+
+__global__ void k_sel_init(SelState* st, const int32_t* K, int32_t B, int64_t n) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= B) return;
+    SelState s;
+    s.prefix = 0;
+    s.prefix2 = 0;
+    s.K = (int32_t)((int64_t)K[j] < n ? (int64_t)K[j] : n);
+    s.k_rem = s.K;
+    s.greater = 0;
+    s.eq = 0;
+    s.tie = 0;
+    s.count = 0;
+    st[j] = s;
+}
+
+// Histogram of digit `shift` among elements whose higher digits match the prefix.
+// phase 0: keys of scores; phase 1: ~id among elements whose key equals the threshold.
+__global__ void __launch_bounds__(256) k_hist(const float* X, int64_t n, int32_t B, int32_t ld, const SelState* st,
+                                              int phase, int shift, uint32_t* hist) {
+    extern __shared__ uint32_t h[];  // [cg][256]
+    const int c0 = blockIdx.y * CG;
+    const int cg = min(CG, B - c0);
+    for (int t = threadIdx.x; t < cg * 256; t += blockDim.x) h[t] = 0;
+    __syncthreads();
+    const uint32_t hi_mask = shift == 24 ? 0u : (0xFFFFFFFFu << (shift + 8));
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * cg; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / cg;
+        const int jl = (int)(e % cg);
+        const int j = c0 + jl;
+        const SelState& s = st[j];
+        if (s.K == 0) continue;
+        const uint32_t key = float_key(X[i * ld + j]);
+        uint32_t v;
+        if (phase == 0) {
+            if ((key ^ s.prefix) & hi_mask) continue;
+            v = key;
+        } else {
+            if (!s.tie || key != s.prefix) continue;
+            v = ~(uint32_t)i;
+            if ((v ^ s.prefix2) & hi_mask) continue;
+        }
+        atomicAdd(&h[jl * 256 + ((v >> shift) & 255u)], 1u);
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < cg * 256; t += blockDim.x)
+        if (h[t]) atomicAdd(&hist[(int64_t)(c0 + t / 256) * 256 + (t % 256)], h[t]);
+}
+
+__global__ void k_select(SelState* st, uint32_t* hist, int32_t B, int phase, int shift) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= B) return;
+    SelState s = st[j];
+    uint32_t* h = hist + (int64_t)j * 256;
+    if (s.K > 0 && (phase == 0 || s.tie)) {
+        int32_t cum = 0;
+        int d = 255;
+        for (; d > 0; --d) {
+            if (cum + (int32_t)h[d] >= s.k_rem) break;
+            cum += (int32_t)h[d];
+        }
+        if (phase == 0) {
+            s.prefix |= (uint32_t)d << shift;
+            s.greater += cum;
+            s.k_rem -= cum;
+            if (shift == 0) {
+                s.eq = (int32_t)h[d];
+                s.tie = s.k_rem < s.eq ? 1 : 0;
+            }
+        } else {
+            s.prefix2 |= (uint32_t)d << shift;
+            s.k_rem -= cum;
+        }
+    }
+    for (int t = 0; t < 256; ++t) h[t] = 0;
+    st[j] = s;
+}
+
+// Collect the selected elements (exactly K per column) into cand[j][0..K).
+__global__ void k_collect(const float* X, int64_t n, int32_t B, int32_t ld, SelState* st, int32_t Kmax,
+                          uint64_t* cand) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * B; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / B;
+        const int j = (int)(e % B);
+        const SelState& s = st[j];
+        if (s.K == 0) continue;
+        const uint32_t key = float_key(X[i * ld + j]);
+        bool take = key > s.prefix;
+        if (key == s.prefix) take = !s.tie || (~(uint32_t)i) >= s.prefix2;
+        if (take) {
+            int p = atomicAdd(&st[j].count, 1);
+            if (p < Kmax) cand[(int64_t)j * Kmax + p] = ((uint64_t)key << 32) | (uint64_t)(~(uint32_t)i);
+        }
+    }
+}
+
+// Sort each column's candidates descending by (key, ~id) and write ids / scores.
+__global__ void k_sort_out(const uint64_t* cand, const SelState* st, int32_t Kmax, int32_t* idx_out, float* score_out) {
+    extern __shared__ uint64_t sk[];
+    const int j = blockIdx.x;
+    const int K = min(st[j].K, Kmax);
+    int P = 1;
+    while (P < K) P <<= 1;
+    for (int t = threadIdx.x; t < P; t += blockDim.x) sk[t] = t < K ? cand[(int64_t)j * Kmax + t] : 0ull;
+    __syncthreads();
+    for (int size = 2; size <= P; size <<= 1)
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int t = threadIdx.x; t < P; t += blockDim.x) {
+                int u = t ^ stride;
+                if (u > t) {
+                    bool desc = (t & size) == 0;
+                    uint64_t a = sk[t], b = sk[u];
+                    if (desc ? (a < b) : (a > b)) {
+                        sk[t] = b;
+                        sk[u] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    for (int t = threadIdx.x; t < Kmax; t += blockDim.x) {
+        if (t < K) {
+            uint64_t v = sk[t];
+            idx_out[(int64_t)j * Kmax + t] = (int32_t)(~(uint32_t)(v & 0xFFFFFFFFu));
+            score_out[(int64_t)j * Kmax + t] = key_float((uint32_t)(v >> 32));
+        } else {
+            idx_out[(int64_t)j * Kmax + t] = -1;
+            score_out[(int64_t)j * Kmax + t] = 0.0f;
+        }
+    }
+}
+
+int hd_rank_impl(hd_ctx* ctx, const float* Xd, int64_t n, int32_t B, int32_t ldx, const int32_t* K_h, int32_t Kmax,
+                 int32_t pool, int32_t* idx_d, float* score_d) {
+    const float* src = Xd;
+    int64_t m = n;
+    int32_t ld = ldx;
+    size_t bytes = ws_size(B * sizeof(SelState)) + ws_size((size_t)B * 256 * 4) + ws_size((size_t)B * Kmax * 8) +
+                   ws_size(B * 4);
+    if (pool > 1) {
+        m = n / pool;
+        bytes += ws_size((size_t)m * B * 4);
+    }
+    void* ws;
+    int rc = hd_ws_reserve(ctx, bytes, &ws);
+    if (rc) return rc;
+    WsCarver cv(ws);
+    SelState* st = cv.take<SelState>(B);
+    uint32_t* hist = cv.take<uint32_t>((size_t)B * 256);
+    uint64_t* cand = cv.take<uint64_t>((size_t)B * Kmax);
+    int32_t* Kd = cv.take<int32_t>(B);
+    if (pool > 1) {
+        float* Y = cv.take<float>((size_t)m * B);
+        k_pool<<<ceil_div(m * B, 256), 256, 0, ctx->stream>>>(Xd, m, B, ldx, pool, Y);
+        HD_CHECK_LAUNCH(ctx);
+        src = Y;
+        ld = B;
+    }
+    HD_CUDA(ctx, cudaMemcpyAsync(Kd, K_h, B * 4, cudaMemcpyHostToDevice, ctx->stream));
+    HD_CUDA(ctx, cudaMemsetAsync(hist, 0, (size_t)B * 256 * 4, ctx->stream));
+    k_sel_init<<<ceil_div(B, 128), 128, 0, ctx->stream>>>(st, Kd, B, m);
+    HD_CHECK_LAUNCH(ctx);
+    static bool attr = false;
+    if (!attr) {
+        HD_CUDA(ctx, cudaFuncSetAttribute(k_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, CG * 256 * 4));
+        attr = true;
+    }
+    const int gy = ceil_div(B, CG);
+    const int gx = std::max(1, std::min<int>(ceil_div(m * std::min(B, CG), 256), ctx->num_sms * 4 / gy + 1));
+    const size_t hsm = (size_t)std::min(B, CG) * 256 * 4;
+    for (int phase = 0; phase < 2; ++phase) {
+        if (phase == 1) {
+            // the id pass is only needed when some column has ties at its boundary
+            std::vector<SelState> hs(B);
+            HD_CUDA(ctx, cudaMemcpyAsync(hs.data(), st, B * sizeof(SelState), cudaMemcpyDeviceToHost, ctx->stream));
+            HD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+            bool any = false;
+            for (auto& x : hs) any = any || x.tie;
+            if (!any) break;
+        }
+        for (int shift = 24; shift >= 0; shift -= 8) {
+            k_hist<<<dim3(gx, gy), 256, hsm, ctx->stream>>>(src, m, B, ld, st, phase, shift, hist);
+            HD_CHECK_LAUNCH(ctx);
+            k_select<<<ceil_div(B, 128), 128, 0, ctx->stream>>>(st, hist, B, phase, shift);
+            HD_CHECK_LAUNCH(ctx);
+        }
+    }
+    const int gc = std::max(1, std::min<int>(ceil_div(m * B, 256), ctx->num_sms * 8));
+    k_collect<<<gc, 256, 0, ctx->stream>>>(src, m, B, ld, st, Kmax, cand);
+    HD_CHECK_LAUNCH(ctx);
+    int P = 1;
+    while (P < Kmax) P <<= 1;
+    k_sort_out<<<B, 256, (size_t)P * 8, ctx->stream>>>(cand, st, Kmax, idx_d, score_d);
+    HD_CHECK_LAUNCH(ctx);
+    return HD_OK;
+}
+
+extern "C" int hd_rank(hd_ctx* ctx, const float* X, int64_t n, int32_t B, int32_t ldx, const int32_t* K,
+                       int32_t Kmax, int32_t pool, int32_t* idx_out, float* score_out) {
+    if (!ctx || !X || !K || !idx_out || !score_out || n <= 0 || B <= 0 || ldx < B) return HD_ERR_INVALID_ARG;
+    if (Kmax < 1 || Kmax > 2048) return hd_fail(ctx, HD_ERR_INVALID_ARG, "Kmax=%d outside [1, 2048]", Kmax);
+    if (pool < 0 || (pool > 1 && n % pool)) return hd_fail(ctx, HD_ERR_INVALID_ARG, "pool=%d does not divide n", pool);
+    if (!hd_is_device_ptr(X)) return hd_fail(ctx, HD_ERR_INVALID_ARG, "X must be device memory");
+    for (int j = 0; j < B; ++j)
+        if (K[j] < 0 || K[j] > Kmax) return hd_fail(ctx, HD_ERR_INVALID_ARG, "K[%d]=%d outside [0, Kmax]", j, K[j]);
+    HD_CUDA(ctx, cudaSetDevice(ctx->device));
+    bool dev = hd_is_device_ptr(idx_out) && hd_is_device_ptr(score_out);
+    int32_t* id = idx_out;
+    float* sd = score_out;
+    if (!dev) {
+        HD_CUDA(ctx, cudaMallocAsync(&id, (size_t)B * Kmax * 4, ctx->stream));
+        HD_CUDA(ctx, cudaMallocAsync(&sd, (size_t)B * Kmax * 4, ctx->stream));
+    }
+    int rc;
+    {
+        HD_PROF(ctx, "rank");
+        rc = hd_rank_impl(ctx, X, n, B, ldx, K, Kmax, pool, id, sd);
+    }
+    if (!rc && !dev) {
+        HD_CUDA(ctx, cudaMemcpyAsync(idx_out, id, (size_t)B * Kmax * 4, cudaMemcpyDeviceToHost, ctx->stream));
+        HD_CUDA(ctx, cudaMemcpyAsync(score_out, sd, (size_t)B * Kmax * 4, cudaMemcpyDeviceToHost, ctx->stream));
+        HD_CUDA(ctx, cudaFreeAsync(id, ctx->stream));
+        HD_CUDA(ctx, cudaFreeAsync(sd, ctx->stream));
+        HD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    }
+    return rc;
+}

@@ -1,0 +1,886 @@
+// Online query path: spectral term + temporal term by multi-RHS CG (Eq. 17-20).
+//
+// Layout: every n x B block (R, P, Q, X) is row-major with a padded width Bp
+// (B rounded up to a multiple of 4) so that one gathered row of P is Bp
+// contiguous fp32 values: a group of Bp/4 lanes moves it with float4 loads.
+//
+// One CG iteration for B columns at once (per-column scalars in fp64):
+//   Q = c1 P - c2 W P [+ U (c3 Lambda o (U^T P))]                 Eq. 20
+//   sigma = P^T Q  (SpMM partials + c3 sum_k lambda_k C_k^2, C = U^T P)
+//   a = rho / sigma; X += a P; R -= a Q; rr = ||R||^2               (CG, Sec. 4.4)
+//   [PCG: C = U^T R, rho' = rr + sum_k D_k C_k^2, Z = R + U (D o C)]
+//   beta = rho' / rho; P = Z + beta P
+// Columns stop individually (||r|| <= tol ||b||, max_iter, breakdown); a
+// stopped column keeps X and R bit-for-bit (its step length is 0).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <vector>
+
+#include "hd_solve.cuh"
+
+// ------------------------------------------------------------------ helpers
+__device__ __forceinline__ float4 ld4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+__device__ __forceinline__ float4 ld4v(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+
+// Reduce per-thread compensated sums of 4 columns to S per-block partials.
+// Lanes sharing columns are l, l + L, l + 2L, ... with L = S / 4.
+template <int S>
+__device__ __forceinline__ void block_reduce_cols(KSum (&a)[4], float2* out) {
+    constexpr int L = S / 4;
+    __shared__ float2 sm[8][S];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int off = L; off < 32; off <<= 1)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            KSum o;
+            o.s = __shfl_xor_sync(0xffffffffu, a[c].s, off);
+            o.c = __shfl_xor_sync(0xffffffffu, a[c].c, off);
+            ksum_merge(a[c], o);
+        }
+    if (lane < L)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) sm[warp][4 * lane + c] = make_float2(a[c].s, a[c].c);
+    __syncthreads();
+    if (threadIdx.x < S) {
+        KSum t = {0.0f, 0.0f};
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) ksum_merge(t, KSum{sm[w][threadIdx.x].x, sm[w][threadIdx.x].y});
+        out[threadIdx.x] = make_float2(t.s, t.c);
+    }
+}
+
+// ------------------------------------------------------------------ kernels
+// R[:, j] += y_j (one thread per column: duplicates summed in input order).
+__global__ void k_scatter_y(const int32_t* y_ptr, const int32_t* y_idx, const float* y_val, int32_t B, int64_t n,
+                            int32_t ld, float* R, int* err) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= B) return;
+    int32_t b = y_ptr[j], e = y_ptr[j + 1];
+    if (b > e || b < 0) {
+        atomicExch(err, 1);
+        return;
+    }
+    for (int32_t t = b; t < e; ++t) {
+        int32_t i = y_idx[t];
+        if (i < 0 || i >= n) {
+            atomicExch(err, 1);
+            continue;
+        }
+        R[(int64_t)i * ld + j] += y_val[t];
+    }
+}
+
+// Q = c1 P - c2 W P for the S-column slab blockIdx.y; optional partials of P^T Q.
+template <int S>
+__global__ void __launch_bounds__(256) k_spmm(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                              const float* __restrict__ wv, const float* __restrict__ P,
+                                              float* __restrict__ Q, int64_t n, int32_t ld, float c1, float c2,
+                                              float2* __restrict__ part) {
+    constexpr int L = S / 4;
+    constexpr int RPB = 256 / L;
+    const int g = (threadIdx.x & 31) % L;
+    const int col = blockIdx.y * S + 4 * g;
+    KSum acc[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+    for (int64_t row = (int64_t)blockIdx.x * RPB + threadIdx.x / L; row < n; row += (int64_t)gridDim.x * RPB) {
+        const int32_t b = __ldg(rp + row), e = __ldg(rp + row + 1);
+        float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+        int32_t t = b;
+        for (; t + 4 <= e; t += 4) {
+            const int32_t j0 = __ldg(ci + t), j1 = __ldg(ci + t + 1), j2 = __ldg(ci + t + 2), j3 = __ldg(ci + t + 3);
+            const float w0 = __ldg(wv + t), w1 = __ldg(wv + t + 1), w2 = __ldg(wv + t + 2), w3 = __ldg(wv + t + 3);
+            const float4 v0 = ld4(P + (int64_t)j0 * ld + col), v1 = ld4(P + (int64_t)j1 * ld + col);
+            const float4 v2 = ld4(P + (int64_t)j2 * ld + col), v3 = ld4(P + (int64_t)j3 * ld + col);
+            s.x = fmaf(w0, v0.x, s.x); s.y = fmaf(w0, v0.y, s.y); s.z = fmaf(w0, v0.z, s.z); s.w = fmaf(w0, v0.w, s.w);
+            s.x = fmaf(w1, v1.x, s.x); s.y = fmaf(w1, v1.y, s.y); s.z = fmaf(w1, v1.z, s.z); s.w = fmaf(w1, v1.w, s.w);
+            s.x = fmaf(w2, v2.x, s.x); s.y = fmaf(w2, v2.y, s.y); s.z = fmaf(w2, v2.z, s.z); s.w = fmaf(w2, v2.w, s.w);
+            s.x = fmaf(w3, v3.x, s.x); s.y = fmaf(w3, v3.y, s.y); s.z = fmaf(w3, v3.z, s.z); s.w = fmaf(w3, v3.w, s.w);
+        }
+        for (; t < e; ++t) {
+            const int32_t j0 = __ldg(ci + t);
+            const float w0 = __ldg(wv + t);
+            const float4 v0 = ld4(P + (int64_t)j0 * ld + col);
+            s.x = fmaf(w0, v0.x, s.x); s.y = fmaf(w0, v0.y, s.y); s.z = fmaf(w0, v0.z, s.z); s.w = fmaf(w0, v0.w, s.w);
+        }
+        const float4 own = ld4(P + row * ld + col);
+        float4 q;
+        q.x = c1 * own.x - c2 * s.x;
+        q.y = c1 * own.y - c2 * s.y;
+        q.z = c1 * own.z - c2 * s.z;
+        q.w = c1 * own.w - c2 * s.w;
+        st4(Q + row * ld + col, q);
+        if (part) {
+            ksum_add(acc[0], own.x * q.x);
+            ksum_add(acc[1], own.y * q.y);
+            ksum_add(acc[2], own.z * q.z);
+            ksum_add(acc[3], own.w * q.w);
+        }
+    }
+    if (part) block_reduce_cols<S>(acc, part + (int64_t)blockIdx.x * ld + blockIdx.y * S);
+}
+
+// Partials of sum_i V_ij^2.
+template <int S>
+__global__ void __launch_bounds__(256) k_colsq(const float* __restrict__ V, int64_t n, int32_t ld, float2* part) {
+    constexpr int L = S / 4;
+    constexpr int RPB = 256 / L;
+    const int g = (threadIdx.x & 31) % L;
+    const int col = blockIdx.y * S + 4 * g;
+    KSum acc[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+    for (int64_t row = (int64_t)blockIdx.x * RPB + threadIdx.x / L; row < n; row += (int64_t)gridDim.x * RPB) {
+        const float4 v = ld4v(V + row * ld + col);
+        ksum_add(acc[0], v.x * v.x);
+        ksum_add(acc[1], v.y * v.y);
+        ksum_add(acc[2], v.z * v.z);
+        ksum_add(acc[3], v.w * v.w);
+    }
+    block_reduce_cols<S>(acc, part + (int64_t)blockIdx.x * ld + blockIdx.y * S);
+}
+
+// X += xs a P; R -= a Q; partials of ||R||^2.
+template <int S>
+__global__ void __launch_bounds__(256) k_update(float* __restrict__ X, float* __restrict__ R,
+                                                const float* __restrict__ P, const float* __restrict__ Q, int64_t n,
+                                                int32_t ld, const ColState* __restrict__ st, float xs,
+                                                float2* __restrict__ part) {
+    constexpr int L = S / 4;
+    constexpr int RPB = 256 / L;
+    const int g = (threadIdx.x & 31) % L;
+    const int col = blockIdx.y * S + 4 * g;
+    const float a0 = (float)st[col].a, a1 = (float)st[col + 1].a, a2 = (float)st[col + 2].a, a3 = (float)st[col + 3].a;
+    const float x0 = xs * a0, x1 = xs * a1, x2 = xs * a2, x3 = xs * a3;
+    KSum acc[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+    for (int64_t row = (int64_t)blockIdx.x * RPB + threadIdx.x / L; row < n; row += (int64_t)gridDim.x * RPB) {
+        const int64_t o = row * ld + col;
+        const float4 p = ld4v(P + o), q = ld4v(Q + o);
+        float4 x = ld4v(X + o), r = ld4v(R + o);
+        x.x = fmaf(x0, p.x, x.x); x.y = fmaf(x1, p.y, x.y); x.z = fmaf(x2, p.z, x.z); x.w = fmaf(x3, p.w, x.w);
+        r.x = fmaf(-a0, q.x, r.x); r.y = fmaf(-a1, q.y, r.y); r.z = fmaf(-a2, q.z, r.z); r.w = fmaf(-a3, q.w, r.w);
+        st4(X + o, x);
+        st4(R + o, r);
+        ksum_add(acc[0], r.x * r.x);
+        ksum_add(acc[1], r.y * r.y);
+        ksum_add(acc[2], r.z * r.z);
+        ksum_add(acc[3], r.w * r.w);
+    }
+    block_reduce_cols<S>(acc, part + (int64_t)blockIdx.x * ld + blockIdx.y * S);
+}
+
+// P = R + beta P.
+template <int S>
+__global__ void __launch_bounds__(256) k_direction(float* __restrict__ P, const float* __restrict__ R, int64_t n,
+                                                   int32_t ld, const ColState* __restrict__ st) {
+    constexpr int L = S / 4;
+    constexpr int RPB = 256 / L;
+    const int g = (threadIdx.x & 31) % L;
+    const int col = blockIdx.y * S + 4 * g;
+    const float b0 = (float)st[col].beta, b1 = (float)st[col + 1].beta, b2 = (float)st[col + 2].beta,
+                b3 = (float)st[col + 3].beta;
+    for (int64_t row = (int64_t)blockIdx.x * RPB + threadIdx.x / L; row < n; row += (int64_t)gridDim.x * RPB) {
+        const int64_t o = row * ld + col;
+        const float4 r = ld4v(R + o);
+        float4 p = ld4v(P + o);
+        p.x = fmaf(b0, p.x, r.x); p.y = fmaf(b1, p.y, r.y); p.z = fmaf(b2, p.z, r.z); p.w = fmaf(b3, p.w, r.w);
+        st4(P + o, p);
+    }
+}
+
+// ---- per-column scalar kernels (one block) ----
+__device__ __forceinline__ double sum_part(const float2* part, int nblk, int ld, int j) {
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) {
+        float2 v = part[(int64_t)b * ld + j];
+        s += (double)v.x + (double)v.y;
+    }
+    return s;
+}
+
+// Setup: bb = ||b||^2; rho = bb (+ sum D C^2 for PCG); activity and 0-iteration convergence.
+__global__ void k_fin_setup(const float2* part, int nblk, int32_t Bp, int32_t B, const float* tol, ColState* st,
+                            const double* C, const double* coef, int32_t r, int* num_active) {
+    __shared__ int cnt;
+    if (threadIdx.x == 0) cnt = 0;
+    __syncthreads();
+    for (int j = threadIdx.x; j < Bp; j += blockDim.x) {
+        ColState s;
+        double bb = sum_part(part, nblk, Bp, j);
+        s.bb = bb;
+        s.rr = bb;
+        double rho = bb;
+        if (C)
+            for (int k = 0; k < r; ++k) rho += coef[k] * C[(int64_t)k * Bp + j] * C[(int64_t)k * Bp + j];
+        s.rho = rho;
+        double t = j < B ? (double)tol[j] : 0.0;
+        s.tol2 = t * t * bb;
+        s.sigma = 0.0;
+        s.a = 0.0;
+        s.beta = 0.0;
+        s.iters = 0;
+        s.pad = 0;
+        if (j >= B || bb == 0.0) {
+            s.active = 0;
+            s.status = HD_COL_EMPTY;
+        } else if (bb <= s.tol2) {
+            s.active = 0;
+            s.status = HD_COL_CONVERGED;
+        } else {
+            s.active = 1;
+            s.status = HD_COL_MAX_ITER;
+            atomicAdd(&cnt, 1);
+        }
+        st[j] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *num_active = cnt;
+}
+
+// a = rho / sigma with sigma = SpMM partials (+ sum_k coef_k C_k^2).
+__global__ void k_fin_sigma(const float2* part, int nblk, int32_t Bp, ColState* st, const double* C,
+                            const double* coef, int32_t r) {
+    for (int j = threadIdx.x; j < Bp; j += blockDim.x) {
+        ColState& s = st[j];
+        if (!s.active) {
+            s.a = 0.0;
+            continue;
+        }
+        double sig = sum_part(part, nblk, Bp, j);
+        if (C)
+            for (int k = 0; k < r; ++k) sig += coef[k] * C[(int64_t)k * Bp + j] * C[(int64_t)k * Bp + j];
+        s.sigma = sig;
+        if (!(sig > 0.0) || !isfinite(sig)) {
+            s.active = 0;
+            s.status = HD_COL_BREAKDOWN;
+            s.a = 0.0;
+        } else {
+            s.a = s.rho / sig;
+        }
+    }
+}
+
+// After the update: rr, convergence, beta.  With C: PCG rho' = rr + sum_k coef_k C_k^2.
+__global__ void k_fin_rr(const float2* part, int nblk, int32_t Bp, ColState* st, int32_t max_iter,
+                         const double* C, const double* coef, int32_t r, int* num_active) {
+    __shared__ int cnt;
+    if (threadIdx.x == 0) cnt = 0;
+    __syncthreads();
+    for (int j = threadIdx.x; j < Bp; j += blockDim.x) {
+        ColState& s = st[j];
+        if (!s.active) {
+            s.beta = 0.0;
+            continue;
+        }
+        double rr = sum_part(part, nblk, Bp, j);
+        double rho = rr;
+        if (C)
+            for (int k = 0; k < r; ++k) rho += coef[k] * C[(int64_t)k * Bp + j] * C[(int64_t)k * Bp + j];
+        s.iters += 1;
+        s.rr = rr;
+        s.beta = rho / s.rho;
+        s.rho = rho;
+        if (!isfinite(rr)) {
+            s.active = 0;
+            s.status = HD_COL_BREAKDOWN;
+            s.beta = 0.0;
+        } else if (rr <= s.tol2) {
+            s.active = 0;
+            s.status = HD_COL_CONVERGED;
+        } else if (s.iters >= max_iter) {
+            s.active = 0;
+            s.status = HD_COL_MAX_ITER;
+        } else {
+            atomicAdd(&cnt, 1);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *num_active = cnt;
+}
+
+__global__ void k_outputs(const ColState* st, int32_t B, int32_t* iters, float* relres, int32_t* status) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= B) return;
+    ColState s = st[j];
+    if (iters) iters[j] = s.iters;
+    if (relres) relres[j] = s.bb > 0.0 ? (float)sqrt(s.rr / s.bb) : 0.0f;
+    if (status) status[j] = s.status;
+}
+
+__global__ void k_copy_out(const float* Xi, int32_t Bp, float* X, int32_t ldx, int32_t B, int64_t n) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n * B) return;
+    int64_t i = e / B;
+    int j = (int)(e % B);
+    X[i * ldx + j] = Xi[i * Bp + j];
+}
+
+// ------------------------------------------------------------------ low-rank, CUDA cores
+template <typename T>
+__device__ __forceinline__ float u_at(const T* U, const float* scale, int64_t i, int ldu, int k);
+template <>
+__device__ __forceinline__ float u_at<float>(const float* U, const float*, int64_t i, int ldu, int k) {
+    return __ldg(U + i * ldu + k);
+}
+template <>
+__device__ __forceinline__ float u_at<__nv_bfloat16>(const __nv_bfloat16* U, const float*, int64_t i, int ldu, int k) {
+    return __bfloat162float(U[i * ldu + k]);
+}
+template <>
+__device__ __forceinline__ float u_at<__nv_fp8_e4m3>(const __nv_fp8_e4m3* U, const float* scale, int64_t i, int ldu,
+                                                      int k) {
+    return float(U[i * ldu + k]) * __ldg(scale + i);
+}
+
+// part[c][k][j] = sum_{i in chunk c} U_ik V_ij ; grid (chunk, k-block of 64, 16-column slab)
+template <typename T>
+__global__ void __launch_bounds__(256) k_lr_reduce_simt(const T* __restrict__ U, const float* __restrict__ scale,
+                                                        int ldu, int r, int rpad, const float* __restrict__ V,
+                                                        int64_t n, int32_t Bp, int64_t rpc,
+                                                        float* __restrict__ part) {
+    const int kk = threadIdx.x >> 2, cq = 4 * (threadIdx.x & 3);
+    const int k = blockIdx.y * 64 + kk;
+    const int col = blockIdx.z * 16 + cq;
+    const int64_t i0 = (int64_t)blockIdx.x * rpc;
+    const int64_t i1 = min(n, i0 + rpc);
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (k < r && col < Bp)
+        for (int64_t i = i0; i < i1; ++i) {
+            const float u = u_at<T>(U, scale, i, ldu, k);
+            const float4 v = ld4(V + i * Bp + col);
+            acc.x = fmaf(u, v.x, acc.x);
+            acc.y = fmaf(u, v.y, acc.y);
+            acc.z = fmaf(u, v.z, acc.z);
+            acc.w = fmaf(u, v.w, acc.w);
+        }
+    if (k < rpad && col < Bp) st4(part + ((int64_t)blockIdx.x * rpad + k) * Bp + col, acc);
+}
+
+// C = sum over chunks (fp64); H = coef o C (fp32 and bf16 hi/lo transposed).
+__global__ void k_lr_finish(const float* __restrict__ part, int nchunk, int rpad, int32_t Bp, const double* coef,
+                            double* C, float* H, __nv_bfloat16* Hhi, __nv_bfloat16* Hlo) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= (int64_t)rpad * Bp) return;
+    const int k = (int)(e / Bp), j = (int)(e % Bp);
+    double s = 0.0;
+    for (int c = 0; c < nchunk; ++c) s += (double)part[((int64_t)c * rpad + k) * Bp + j];
+    C[e] = s;
+    const double h = coef[k] * s;
+    H[e] = (float)h;
+    if (Hhi) {
+        const __nv_bfloat16 hi = __double2bfloat16(h);
+        const __nv_bfloat16 lo = __double2bfloat16(h - (double)__bfloat162float(hi));
+        Hhi[(int64_t)j * rpad + k] = hi;
+        Hlo[(int64_t)j * rpad + k] = lo;
+    }
+}
+
+// out = op(U H) for the 16-column slab blockIdx.y; H staged in shared memory.
+template <typename T>
+__global__ void __launch_bounds__(256) k_lr_expand_simt(const T* __restrict__ U, const float* __restrict__ scale,
+                                                        int ldu, int r, const float* __restrict__ H, int op,
+                                                        float* __restrict__ out, const float* __restrict__ Rv,
+                                                        const float* __restrict__ Pv, int64_t n, int32_t Bp,
+                                                        const ColState* __restrict__ st) {
+    extern __shared__ float Hs[];  // [r][16]
+    const int slab = blockIdx.y;
+    for (int e = threadIdx.x; e < r * 16; e += blockDim.x) {
+        const int k = e >> 4, c = e & 15;
+        Hs[e] = (slab * 16 + c < Bp) ? H[(int64_t)k * Bp + slab * 16 + c] : 0.0f;
+    }
+    __syncthreads();
+    const int cq = 4 * (threadIdx.x & 3);
+    const int col = slab * 16 + cq;
+    if (col >= Bp) return;
+    float b0 = 0.f, b1 = 0.f, b2 = 0.f, b3 = 0.f;
+    if (op == EXP_DIRECTION) {
+        b0 = (float)st[col].beta;
+        b1 = (float)st[col + 1].beta;
+        b2 = (float)st[col + 2].beta;
+        b3 = (float)st[col + 3].beta;
+    }
+    for (int64_t row = (int64_t)blockIdx.x * 64 + (threadIdx.x >> 2); row < n; row += (int64_t)gridDim.x * 64) {
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int k = 0; k < r; ++k) {
+            const float u = u_at<T>(U, scale, row, ldu, k);
+            const float4 h = *reinterpret_cast<const float4*>(Hs + k * 16 + cq);
+            acc.x = fmaf(u, h.x, acc.x);
+            acc.y = fmaf(u, h.y, acc.y);
+            acc.z = fmaf(u, h.z, acc.z);
+            acc.w = fmaf(u, h.w, acc.w);
+        }
+        const int64_t o = row * Bp + col;
+        float4 v;
+        if (op == EXP_SET_X) {
+            v = acc;
+        } else if (op == EXP_SUB_R) {
+            v = ld4v(out + o);
+            v.x -= acc.x; v.y -= acc.y; v.z -= acc.z; v.w -= acc.w;
+        } else if (op == EXP_ADD_Q) {
+            v = ld4v(out + o);
+            v.x += acc.x; v.y += acc.y; v.z += acc.z; v.w += acc.w;
+        } else {
+            const float4 rr = ld4v(Rv + o), pp = ld4v(Pv + o);
+            v.x = rr.x + acc.x + b0 * pp.x;
+            v.y = rr.y + acc.y + b1 * pp.y;
+            v.z = rr.z + acc.z + b2 * pp.z;
+            v.w = rr.w + acc.w + b3 * pp.w;
+        }
+        st4(out + o, v);
+    }
+}
+
+static int simt_nchunk(hd_ctx* ctx, int64_t n, int rpad, int Bp) {
+    int blocks_per_chunk = (rpad / 64) * ceil_div(Bp, 16);
+    int nc = ceil_div(4 * ctx->num_sms, blocks_per_chunk);
+    int64_t maxc = std::max<int64_t>(1, n / 64);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(nc, maxc));
+}
+
+int lr_reduce(hd_ctx* ctx, const LowRank& lr, const float* V, int64_t n, int32_t Bp) {
+    HD_PROF(ctx, "lr_reduce");
+    if (lr_use_tensor_cores(lr.e)) return lr_tc_reduce(ctx, lr, V, n, Bp);
+    const hd_eig* e = lr.e;
+    int64_t rpc = (n + lr.nchunk - 1) / lr.nchunk;
+    dim3 grid(lr.nchunk, lr.rpad / 64, ceil_div(Bp, 16));
+    if (e->storage == HD_F32)
+        k_lr_reduce_simt<float><<<grid, 256, 0, ctx->stream>>>((const float*)e->U, e->scale, e->ldu, e->r, lr.rpad, V,
+                                                               n, Bp, rpc, lr.part);
+    else if (e->storage == HD_BF16)
+        k_lr_reduce_simt<__nv_bfloat16><<<grid, 256, 0, ctx->stream>>>((const __nv_bfloat16*)e->U, e->scale, e->ldu,
+                                                                       e->r, lr.rpad, V, n, Bp, rpc, lr.part);
+    else
+        k_lr_reduce_simt<__nv_fp8_e4m3><<<grid, 256, 0, ctx->stream>>>((const __nv_fp8_e4m3*)e->U, e->scale, e->ldu,
+                                                                       e->r, lr.rpad, V, n, Bp, rpc, lr.part);
+    HD_CHECK_LAUNCH(ctx);
+    return HD_OK;
+}
+
+int lr_finish(hd_ctx* ctx, const LowRank& lr, int32_t Bp, const double* coef) {
+    HD_PROF(ctx, "scalar");
+    int64_t tot = (int64_t)lr.rpad * Bp;
+    k_lr_finish<<<ceil_div(tot, 256), 256, 0, ctx->stream>>>(lr.part, lr.nchunk, lr.rpad, Bp, coef, lr.C,
+                                                             lr.H, lr.Hhi, lr.Hlo);
+    HD_CHECK_LAUNCH(ctx);
+    return HD_OK;
+}
+
+int lr_expand(hd_ctx* ctx, const LowRank& lr, int op, float* out, const float* Rv, const float* Pv, int64_t n,
+              int32_t Bp, const ColState* st) {
+    HD_PROF(ctx, "lr_expand");
+    if (lr_use_tensor_cores(lr.e)) return lr_tc_expand(ctx, lr, op, out, Rv, Pv, n, Bp, st);
+    const hd_eig* e = lr.e;
+    size_t smem = (size_t)e->r * 16 * sizeof(float);
+    int gx = (int)std::min<int64_t>(ceil_div(n, 64), (int64_t)ctx->num_sms * 8);
+    dim3 grid(gx, ceil_div(Bp, 16));
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_lr_expand_simt<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024 + 1024);
+        cudaFuncSetAttribute(k_lr_expand_simt<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024 + 1024);
+        cudaFuncSetAttribute(k_lr_expand_simt<__nv_fp8_e4m3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024 + 1024);
+        attr = true;
+    }
+    if (e->storage == HD_F32)
+        k_lr_expand_simt<float><<<grid, 256, smem, ctx->stream>>>((const float*)e->U, e->scale, e->ldu, e->r, lr.H, op,
+                                                                  out, Rv, Pv, n, Bp, st);
+    else if (e->storage == HD_BF16)
+        k_lr_expand_simt<__nv_bfloat16><<<grid, 256, smem, ctx->stream>>>(
+            (const __nv_bfloat16*)e->U, e->scale, e->ldu, e->r, lr.H, op, out, Rv, Pv, n, Bp, st);
+    else
+        k_lr_expand_simt<__nv_fp8_e4m3><<<grid, 256, smem, ctx->stream>>>(
+            (const __nv_fp8_e4m3*)e->U, e->scale, e->ldu, e->r, lr.H, op, out, Rv, Pv, n, Bp, st);
+    HD_CHECK_LAUNCH(ctx);
+    return HD_OK;
+}
+
+// ------------------------------------------------------------------ launch helpers
+struct VecLaunch {
+    int S;       // columns per row group slab
+    int nblk;    // grid.x
+    int slabs;   // grid.y
+};
+
+static int pick_slab(int32_t Bp) {
+    static int forced = -1;
+    if (forced < 0) {
+        const char* s = getenv("HD_SLAB");
+        forced = s ? atoi(s) : 0;
+    }
+    int cands[] = {128, 64, 32, 16, 8, 4};
+    for (int S : cands)
+        if ((forced == 0 || S <= forced) && Bp % S == 0) return S;
+    return 4;
+}
+
+static VecLaunch vec_launch(hd_ctx* ctx, int64_t n, int32_t Bp) {
+    VecLaunch v;
+    v.S = pick_slab(Bp);
+    int rpb = 256 / (v.S / 4);
+    v.slabs = Bp / v.S;
+    v.nblk = (int)std::min<int64_t>(ceil_div(n, rpb), (int64_t)ctx->num_sms * 8);
+    if (v.nblk < 1) v.nblk = 1;
+    return v;
+}
+
+#define HD_DISPATCH_S(S, ...)                  \
+    switch (S) {                               \
+        case 4: { constexpr int SS = 4; __VA_ARGS__; } break;     \
+        case 8: { constexpr int SS = 8; __VA_ARGS__; } break;     \
+        case 16: { constexpr int SS = 16; __VA_ARGS__; } break;   \
+        case 32: { constexpr int SS = 32; __VA_ARGS__; } break;   \
+        case 64: { constexpr int SS = 64; __VA_ARGS__; } break;   \
+        default: { constexpr int SS = 128; __VA_ARGS__; } break;  \
+    }
+
+int hd_spmm_apply(hd_ctx* ctx, const hd_graph* g, const float* P, float* Q, int32_t ld, int32_t B, float c1,
+                  float c2) {
+    VecLaunch v = vec_launch(ctx, g->n, ld);
+    dim3 grid(v.nblk, v.slabs);
+    HD_DISPATCH_S(v.S, (k_spmm<SS><<<grid, 256, 0, ctx->stream>>>(g->row_ptr, g->col, g->val, P, Q, g->n, ld, c1, c2,
+                                                                   nullptr)));
+    HD_CHECK_LAUNCH(ctx);
+    return HD_OK;
+}
+
+// ------------------------------------------------------------------ the solve
+struct Solve {
+    hd_ctx* ctx;
+    const hd_graph* g;
+    int64_t n;
+    int32_t B, Bp;
+    VecLaunch vl;
+    float *R, *P, *Q, *X;
+    float2* part;
+    ColState* st;
+    int* num_active;
+    int* err;
+    LowRank lr;
+    bool has_lr = false;
+    double *gcoef, *hcoef, *opcoef, *dcoef, *ones;
+};
+
+#define LAUNCH_VEC(kernel, ...)                                                                 \
+    do {                                                                                        \
+        HD_PROF(S_.ctx, #kernel[2] == 's' && #kernel[3] == 'p' ? "spmm"                         \
+                        : #kernel[2] == 'u' ? "update" : #kernel[2] == 'd' ? "direction" : "colsq"); \
+        dim3 grid_(S_.vl.nblk, S_.vl.slabs);                                                    \
+        HD_DISPATCH_S(S_.vl.S, (kernel<SS><<<grid_, 256, 0, S_.ctx->stream>>>(__VA_ARGS__)));   \
+        HD_CHECK_LAUNCH(S_.ctx);                                                                \
+    } while (0)
+
+extern "C" int hd_query_batch(hd_ctx* ctx, const hd_graph* g, const hd_eig* eig, int mode, int32_t B,
+                              const int32_t* y_ptr, const int32_t* y_idx, const float* y_val, float alpha,
+                              const float* tol, int32_t max_iter, float* X, int32_t ldx, int32_t* iters,
+                              float* relres, int32_t* status) {
+    if (!ctx || !g || !y_ptr || !tol || !X) return HD_ERR_INVALID_ARG;
+    if (B <= 0 || ldx < B) return hd_fail(ctx, HD_ERR_INVALID_ARG, "B=%d ldx=%d", B, ldx);
+    if (!(alpha >= 0.0f && alpha < 1.0f)) return hd_fail(ctx, HD_ERR_INVALID_ARG, "alpha=%g not in [0,1)", alpha);
+    if (mode != HD_MODE_PAPER && mode != HD_MODE_PROJ && mode != HD_MODE_PCG)
+        return hd_fail(ctx, HD_ERR_INVALID_ARG, "mode %d", mode);
+    if (max_iter < 0) return hd_fail(ctx, HD_ERR_INVALID_ARG, "max_iter %d", max_iter);
+    if (eig && eig->n != g->n) return hd_fail(ctx, HD_ERR_INVALID_ARG, "eigenpairs for n=%lld, graph n=%lld",
+                                              (long long)eig->n, (long long)g->n);
+    HD_CUDA(ctx, cudaSetDevice(ctx->device));
+    Solve S_;
+    S_.ctx = ctx;
+    S_.g = g;
+    S_.n = g->n;
+    S_.B = B;
+    S_.Bp = (B + 3) / 4 * 4;
+    S_.vl = vec_launch(ctx, S_.n, S_.Bp);
+    const int64_t n = S_.n;
+    const int32_t Bp = S_.Bp;
+    const bool lr_on = eig && eig->r > 0;
+    S_.has_lr = lr_on;
+    const int r = lr_on ? eig->r : 0;
+    const int rpad = lr_on ? (r + 63) / 64 * 64 : 0;
+    const int Bp16 = (Bp + 15) / 16 * 16;
+
+    // host-side copy of y_ptr to learn nnz
+    int32_t nnz_y;
+    {
+        int32_t last;
+        if (hd_is_device_ptr(y_ptr)) {
+            HD_CUDA(ctx, cudaMemcpy(&last, y_ptr + B, 4, cudaMemcpyDeviceToHost));
+        } else {
+            last = y_ptr[B];
+        }
+        nnz_y = last;
+        if (nnz_y < 0) return hd_fail(ctx, HD_ERR_INVALID_ARG, "y_ptr[B] = %d", nnz_y);
+        if (nnz_y > 0 && (!y_idx || !y_val)) return HD_ERR_INVALID_ARG;
+    }
+    const bool x_direct = hd_is_device_ptr(X) && ldx == Bp;
+    int nchunk = 0;
+    if (lr_on) nchunk = lr_use_tensor_cores(eig) ? lr_tc_nchunk(ctx, n) : simt_nchunk(ctx, n, rpad, Bp);
+
+    size_t vec = (size_t)n * Bp * sizeof(float);
+    size_t bytes = 3 * ws_size(vec) + (x_direct ? 0 : ws_size(vec)) + ws_size((size_t)S_.vl.nblk * Bp * sizeof(float2)) +
+                   ws_size(Bp * sizeof(ColState)) + ws_size(64) + ws_size((B + 1) * 4) + 2 * ws_size(nnz_y * 4 + 4) +
+                   ws_size(B * 4);
+    if (lr_on)
+        bytes += ws_size((size_t)nchunk * rpad * Bp * 4) + ws_size((size_t)rpad * Bp * 8) +
+                 ws_size((size_t)rpad * Bp * 4) + 2 * ws_size((size_t)Bp16 * rpad * 2) + 5 * ws_size(rpad * 8);
+    void* ws;
+    int rc = hd_ws_reserve(ctx, bytes, &ws);
+    if (rc) return rc;
+    WsCarver cv(ws);
+    S_.R = cv.take<float>((size_t)n * Bp);
+    S_.P = cv.take<float>((size_t)n * Bp);
+    S_.Q = cv.take<float>((size_t)n * Bp);
+    S_.X = x_direct ? X : cv.take<float>((size_t)n * Bp);
+    S_.part = cv.take<float2>((size_t)S_.vl.nblk * Bp);
+    S_.st = cv.take<ColState>(Bp);
+    S_.num_active = cv.take<int>(16);
+    S_.err = S_.num_active + 1;
+    int32_t* d_yptr = cv.take<int32_t>(B + 1);
+    int32_t* d_yidx = cv.take<int32_t>(nnz_y + 1);
+    float* d_yval = cv.take<float>(nnz_y + 1);
+    float* d_tol = cv.take<float>(B);
+    const void *yp, *yi, *yv, *tl;
+    if ((rc = hd_stage_in(ctx, y_ptr, (B + 1) * 4, d_yptr, &yp))) return rc;
+    if ((rc = hd_stage_in(ctx, y_idx, (size_t)nnz_y * 4, d_yidx, &yi))) return rc;
+    if ((rc = hd_stage_in(ctx, y_val, (size_t)nnz_y * 4, d_yval, &yv))) return rc;
+    if ((rc = hd_stage_in(ctx, tol, (size_t)B * 4, d_tol, &tl))) return rc;
+    if (lr_on) {
+        S_.lr.e = eig;
+        S_.lr.rpad = rpad;
+        S_.lr.nchunk = nchunk;
+        S_.lr.Bp16 = Bp16;
+        S_.lr.part = cv.take<float>((size_t)nchunk * rpad * Bp);
+        S_.lr.C = cv.take<double>((size_t)rpad * Bp);
+        S_.lr.H = cv.take<float>((size_t)rpad * Bp);
+        S_.lr.Hhi = cv.take<__nv_bfloat16>((size_t)Bp16 * rpad);
+        S_.lr.Hlo = cv.take<__nv_bfloat16>((size_t)Bp16 * rpad);
+        S_.gcoef = cv.take<double>(rpad);
+        S_.hcoef = cv.take<double>(rpad);
+        S_.opcoef = cv.take<double>(rpad);
+        S_.dcoef = cv.take<double>(rpad);
+        S_.ones = cv.take<double>(rpad);
+        std::vector<double> gc(rpad, 0.0), hc(rpad, 0.0), oc(rpad, 0.0), dc(rpad, 0.0), on(rpad, 0.0);
+        const double a = alpha;
+        const double c3 = mode == HD_MODE_PROJ ? a : a / (1.0 - a);
+        for (int k = 0; k < r; ++k) {
+            double l = eig->lambda_h[k];
+            gc[k] = (1.0 - a) * a * l / (1.0 - a * l);  // g_alpha, Eq. 16
+            hc[k] = (1.0 - a) / (1.0 - a * l);          // h_alpha, Sec. 3.2
+            oc[k] = c3 * l;
+            double lt = l > 0.0 ? l : 0.0;
+            dc[k] = a * lt / (1.0 - a * lt);
+            on[k] = 1.0;
+        }
+        HD_CUDA(ctx, cudaMemcpyAsync(S_.gcoef, gc.data(), rpad * 8, cudaMemcpyHostToDevice, ctx->stream));
+        HD_CUDA(ctx, cudaMemcpyAsync(S_.hcoef, hc.data(), rpad * 8, cudaMemcpyHostToDevice, ctx->stream));
+        HD_CUDA(ctx, cudaMemcpyAsync(S_.opcoef, oc.data(), rpad * 8, cudaMemcpyHostToDevice, ctx->stream));
+        HD_CUDA(ctx, cudaMemcpyAsync(S_.dcoef, dc.data(), rpad * 8, cudaMemcpyHostToDevice, ctx->stream));
+        HD_CUDA(ctx, cudaMemcpyAsync(S_.ones, on.data(), rpad * 8, cudaMemcpyHostToDevice, ctx->stream));
+        HD_CUDA(ctx, cudaMemsetAsync(S_.lr.Hhi, 0, (size_t)Bp16 * rpad * 2, ctx->stream));
+        HD_CUDA(ctx, cudaMemsetAsync(S_.lr.Hlo, 0, (size_t)Bp16 * rpad * 2, ctx->stream));
+    }
+
+    // ---------------- setup
+    const int eff_mode = lr_on ? mode : HD_MODE_PAPER;
+    const double a = alpha;
+    float c1, c2, xs = 1.0f;
+    if (eff_mode == HD_MODE_PROJ) {
+        c1 = 1.0f;
+        c2 = alpha;
+        xs = (float)(1.0 - a);
+    } else {
+        c1 = (float)(1.0 / (1.0 - a));
+        c2 = (float)(a / (1.0 - a));
+    }
+    HD_CUDA(ctx, cudaMemsetAsync(S_.R, 0, vec, ctx->stream));
+    HD_CUDA(ctx, cudaMemsetAsync(S_.X, 0, vec, ctx->stream));
+    HD_CUDA(ctx, cudaMemsetAsync(S_.err, 0, sizeof(int), ctx->stream));
+    k_scatter_y<<<ceil_div(B, 128), 128, 0, ctx->stream>>>((const int32_t*)yp, (const int32_t*)yi, (const float*)yv,
+                                                           B, n, Bp, S_.R, S_.err);
+    HD_CHECK_LAUNCH(ctx);
+    const double* Cd = lr_on ? S_.lr.C : nullptr;
+    if (eff_mode == HD_MODE_PAPER) {
+        LAUNCH_VEC(k_colsq, S_.R, n, Bp, S_.part);
+        k_fin_setup<<<1, 256, 0, ctx->stream>>>(S_.part, S_.vl.nblk, Bp, B, (const float*)tl, S_.st, nullptr, nullptr,
+                                                0, S_.num_active);
+        HD_CHECK_LAUNCH(ctx);
+        HD_CUDA(ctx, cudaMemcpyAsync(S_.P, S_.R, vec, cudaMemcpyDeviceToDevice, ctx->stream));
+        if (lr_on) {
+            // x^s = U g(Lambda) U^T y (Eq. 18); C = U^T P for the first operator
+            if ((rc = lr_reduce(ctx, S_.lr, S_.R, n, Bp))) return rc;
+            if ((rc = lr_finish(ctx, S_.lr, Bp, S_.gcoef))) return rc;
+            if ((rc = lr_expand(ctx, S_.lr, EXP_SET_X, S_.X, nullptr, nullptr, n, Bp, S_.st))) return rc;
+            if ((rc = lr_finish(ctx, S_.lr, Bp, S_.opcoef))) return rc;
+        }
+    } else if (eff_mode == HD_MODE_PROJ) {
+        if ((rc = lr_reduce(ctx, S_.lr, S_.R, n, Bp))) return rc;
+        if ((rc = lr_finish(ctx, S_.lr, Bp, S_.hcoef))) return rc;
+        if ((rc = lr_expand(ctx, S_.lr, EXP_SET_X, S_.X, nullptr, nullptr, n, Bp, S_.st))) return rc;
+        if ((rc = lr_finish(ctx, S_.lr, Bp, S_.ones))) return rc;
+        if ((rc = lr_expand(ctx, S_.lr, EXP_SUB_R, S_.R, nullptr, nullptr, n, Bp, S_.st))) return rc;
+        LAUNCH_VEC(k_colsq, S_.R, n, Bp, S_.part);
+        k_fin_setup<<<1, 256, 0, ctx->stream>>>(S_.part, S_.vl.nblk, Bp, B, (const float*)tl, S_.st, nullptr, nullptr,
+                                                0, S_.num_active);
+        HD_CHECK_LAUNCH(ctx);
+        HD_CUDA(ctx, cudaMemcpyAsync(S_.P, S_.R, vec, cudaMemcpyDeviceToDevice, ctx->stream));
+        if ((rc = lr_reduce(ctx, S_.lr, S_.P, n, Bp))) return rc;
+        if ((rc = lr_finish(ctx, S_.lr, Bp, S_.opcoef))) return rc;
+    } else {  // PCG
+        LAUNCH_VEC(k_colsq, S_.R, n, Bp, S_.part);
+        if ((rc = lr_reduce(ctx, S_.lr, S_.R, n, Bp))) return rc;
+        if ((rc = lr_finish(ctx, S_.lr, Bp, S_.dcoef))) return rc;
+        k_fin_setup<<<1, 256, 0, ctx->stream>>>(S_.part, S_.vl.nblk, Bp, B, (const float*)tl, S_.st, Cd, S_.dcoef, r,
+                                                S_.num_active);
+        HD_CHECK_LAUNCH(ctx);
+        HD_CUDA(ctx, cudaMemsetAsync(S_.P, 0, vec, ctx->stream));
+        if ((rc = lr_expand(ctx, S_.lr, EXP_DIRECTION, S_.P, S_.R, S_.P, n, Bp, S_.st))) return rc;
+    }
+
+    // ---------------- iterations
+    const int poll_every = 4;
+    int it = 0;
+    HD_CUDA(ctx, cudaMemcpyAsync(ctx->h_poll, S_.num_active, 2 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    HD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (ctx->h_poll[1]) return hd_fail(ctx, HD_ERR_INVALID_ARG, "observation index out of range or bad y_ptr");
+    int active = ctx->h_poll[0];
+    while (active > 0 && it < max_iter) {
+        for (int t = 0; t < poll_every && it < max_iter; ++t, ++it) {
+            if (eff_mode == HD_MODE_PCG) {
+                LAUNCH_VEC(k_spmm, g->row_ptr, g->col, g->val, S_.P, S_.Q, n, Bp, c1, c2, S_.part);
+                { HD_PROF(ctx, "scalar");
+                k_fin_sigma<<<1, 256, 0, ctx->stream>>>(S_.part, S_.vl.nblk, Bp, S_.st, nullptr, nullptr, 0); }
+                HD_CHECK_LAUNCH(ctx);
+                LAUNCH_VEC(k_update, S_.X, S_.R, S_.P, S_.Q, n, Bp, S_.st, xs, S_.part);
+                if ((rc = lr_reduce(ctx, S_.lr, S_.R, n, Bp))) return rc;
+                if ((rc = lr_finish(ctx, S_.lr, Bp, S_.dcoef))) return rc;
+                { HD_PROF(ctx, "scalar");
+                k_fin_rr<<<1, 256, 0, ctx->stream>>>(S_.part, S_.vl.nblk, Bp, S_.st, max_iter, Cd, S_.dcoef, r,
+                                                     S_.num_active); }
+                HD_CHECK_LAUNCH(ctx);
+                if ((rc = lr_expand(ctx, S_.lr, EXP_DIRECTION, S_.P, S_.R, S_.P, n, Bp, S_.st))) return rc;
+            } else {
+                LAUNCH_VEC(k_spmm, g->row_ptr, g->col, g->val, S_.P, S_.Q, n, Bp, c1, c2, S_.part);
+                if (lr_on) {
+                    if ((rc = lr_expand(ctx, S_.lr, EXP_ADD_Q, S_.Q, nullptr, nullptr, n, Bp, S_.st))) return rc;
+                }
+                { HD_PROF(ctx, "scalar");
+                k_fin_sigma<<<1, 256, 0, ctx->stream>>>(S_.part, S_.vl.nblk, Bp, S_.st, Cd,
+                                                        lr_on ? S_.opcoef : nullptr, r); }
+                HD_CHECK_LAUNCH(ctx);
+                LAUNCH_VEC(k_update, S_.X, S_.R, S_.P, S_.Q, n, Bp, S_.st, xs, S_.part);
+                { HD_PROF(ctx, "scalar");
+                k_fin_rr<<<1, 256, 0, ctx->stream>>>(S_.part, S_.vl.nblk, Bp, S_.st, max_iter, nullptr, nullptr, 0,
+                                                     S_.num_active); }
+                HD_CHECK_LAUNCH(ctx);
+                LAUNCH_VEC(k_direction, S_.P, S_.R, n, Bp, S_.st);
+                if (lr_on) {
+                    if ((rc = lr_reduce(ctx, S_.lr, S_.P, n, Bp))) return rc;
+                    if ((rc = lr_finish(ctx, S_.lr, Bp, S_.opcoef))) return rc;
+                }
+            }
+        }
+        HD_CUDA(ctx, cudaMemcpyAsync(ctx->h_poll, S_.num_active, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+        HD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        active = ctx->h_poll[0];
+    }
+
+    // ---------------- outputs
+    k_outputs<<<ceil_div(B, 128), 128, 0, ctx->stream>>>(S_.st, B, hd_is_device_ptr(iters) ? iters : nullptr,
+                                                         hd_is_device_ptr(relres) ? relres : nullptr,
+                                                         hd_is_device_ptr(status) ? status : nullptr);
+    HD_CHECK_LAUNCH(ctx);
+    if ((iters && !hd_is_device_ptr(iters)) || (relres && !hd_is_device_ptr(relres)) ||
+        (status && !hd_is_device_ptr(status))) {
+        std::vector<ColState> hs(B);
+        HD_CUDA(ctx, cudaMemcpyAsync(hs.data(), S_.st, B * sizeof(ColState), cudaMemcpyDeviceToHost, ctx->stream));
+        HD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        for (int j = 0; j < B; ++j) {
+            if (iters && !hd_is_device_ptr(iters)) iters[j] = hs[j].iters;
+            if (relres && !hd_is_device_ptr(relres)) relres[j] = hs[j].bb > 0 ? (float)std::sqrt(hs[j].rr / hs[j].bb) : 0.f;
+            if (status && !hd_is_device_ptr(status)) status[j] = hs[j].status;
+        }
+    }
+    if (!x_direct) {
+        if (hd_is_device_ptr(X)) {
+            k_copy_out<<<ceil_div(n * B, 256), 256, 0, ctx->stream>>>(S_.X, Bp, X, ldx, B, n);
+            HD_CHECK_LAUNCH(ctx);
+        } else {
+            HD_CUDA(ctx, cudaMemcpy2DAsync(X, (size_t)ldx * 4, S_.X, (size_t)Bp * 4, (size_t)B * 4, n,
+                                           cudaMemcpyDeviceToHost, ctx->stream));
+            HD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        }
+    }
+    return HD_OK;
+}
+
+// ------------------------------------------------------------------ spectral products on their own
+static int lowrank_setup(hd_ctx* ctx, const hd_eig* e, int32_t Bp, LowRank& lr, double** coef_ones, WsCarver& cv) {
+    lr.e = e;
+    lr.rpad = (e->r + 63) / 64 * 64;
+    lr.Bp16 = (Bp + 15) / 16 * 16;
+    lr.nchunk = lr_use_tensor_cores(e) ? lr_tc_nchunk(ctx, e->n) : simt_nchunk(ctx, e->n, lr.rpad, Bp);
+    lr.part = cv.take<float>((size_t)lr.nchunk * lr.rpad * Bp);
+    lr.C = cv.take<double>((size_t)lr.rpad * Bp);
+    lr.H = cv.take<float>((size_t)lr.rpad * Bp);
+    lr.Hhi = cv.take<__nv_bfloat16>((size_t)lr.Bp16 * lr.rpad);
+    lr.Hlo = cv.take<__nv_bfloat16>((size_t)lr.Bp16 * lr.rpad);
+    *coef_ones = cv.take<double>(lr.rpad);
+    std::vector<double> on(lr.rpad, 0.0);
+    for (int k = 0; k < e->r; ++k) on[k] = 1.0;
+    HD_CUDA(ctx, cudaMemcpyAsync(*coef_ones, on.data(), lr.rpad * 8, cudaMemcpyHostToDevice, ctx->stream));
+    HD_CUDA(ctx, cudaMemsetAsync(lr.Hhi, 0, (size_t)lr.Bp16 * lr.rpad * 2, ctx->stream));
+    HD_CUDA(ctx, cudaMemsetAsync(lr.Hlo, 0, (size_t)lr.Bp16 * lr.rpad * 2, ctx->stream));
+    return HD_OK;
+}
+
+static size_t lowrank_bytes(hd_ctx* ctx, const hd_eig* e, int32_t Bp) {
+    int rpad = (e->r + 63) / 64 * 64;
+    int nch = std::max(lr_tc_nchunk(ctx, e->n), simt_nchunk(ctx, e->n, rpad, Bp));
+    return ws_size((size_t)nch * rpad * Bp * 4) + ws_size((size_t)rpad * Bp * 8) + ws_size((size_t)rpad * Bp * 4) +
+           2 * ws_size((size_t)((Bp + 15) / 16 * 16) * rpad * 2) + ws_size(rpad * 8);
+}
+
+extern "C" int hd_eig_project(hd_ctx* ctx, const hd_eig* e, const float* V, int32_t B, double* C_out) {
+    if (!ctx || !e || !V || !C_out || B <= 0 || B % 4 || B > 256 || e->r <= 0) return HD_ERR_INVALID_ARG;
+    if (!hd_is_device_ptr(V)) return hd_fail(ctx, HD_ERR_INVALID_ARG, "V must be device memory");
+    void* ws;
+    int rc = hd_ws_reserve(ctx, lowrank_bytes(ctx, e, B), &ws);
+    if (rc) return rc;
+    WsCarver cv(ws);
+    LowRank lr;
+    double* ones;
+    if ((rc = lowrank_setup(ctx, e, B, lr, &ones, cv))) return rc;
+    if ((rc = lr_reduce(ctx, lr, V, e->n, B))) return rc;
+    if ((rc = lr_finish(ctx, lr, B, ones))) return rc;
+    // rows 0..r-1 of C (fp64, r x B)
+    cudaMemcpyKind kind = hd_is_device_ptr(C_out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    HD_CUDA(ctx, cudaMemcpyAsync(C_out, lr.C, (size_t)e->r * B * 8, kind, ctx->stream));
+    HD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return HD_OK;
+}
+
+// H (fp64, r x B) -> the fp32 partial layout [1][rpad][B], zero beyond r.
+__global__ void k_h_to_part(const double* Hin, int r, int32_t B, int rpad, float* part) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= (int64_t)rpad * B) return;
+    int k = (int)(e / B);
+    part[e] = k < r ? (float)Hin[e] : 0.0f;
+}
+
+extern "C" int hd_eig_expand(hd_ctx* ctx, const hd_eig* e, const double* H, int32_t B, float* X_out) {
+    if (!ctx || !e || !H || !X_out || B <= 0 || B % 4 || B > 256 || e->r <= 0) return HD_ERR_INVALID_ARG;
+    if (!hd_is_device_ptr(X_out)) return hd_fail(ctx, HD_ERR_INVALID_ARG, "X_out must be device memory");
+    void* ws;
+    int rc = hd_ws_reserve(ctx, lowrank_bytes(ctx, e, B) + ws_size((size_t)e->r * B * 8), &ws);
+    if (rc) return rc;
+    WsCarver cv(ws);
+    LowRank lr;
+    double* ones;
+    if ((rc = lowrank_setup(ctx, e, B, lr, &ones, cv))) return rc;
+    double* Hs = cv.take<double>((size_t)e->r * B);
+    const void* Hd;
+    if ((rc = hd_stage_in(ctx, H, (size_t)e->r * B * 8, Hs, &Hd))) return rc;
+    lr.nchunk = 1;
+    k_h_to_part<<<ceil_div((int64_t)lr.rpad * B, 256), 256, 0, ctx->stream>>>((const double*)Hd, e->r, B, lr.rpad,
+                                                                             lr.part);
+    HD_CHECK_LAUNCH(ctx);
+    if ((rc = lr_finish(ctx, lr, B, ones))) return rc;
+    if ((rc = lr_expand(ctx, lr, EXP_SET_X, X_out, nullptr, nullptr, e->n, B, nullptr))) return rc;
+    HD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return HD_OK;
+}

@@ -1,0 +1,50 @@
+// Shared declarations of the online query path (Eq. 17-20).
+#pragma once
+#include "hd_internal.cuh"
+
+// Per-column CG state, fp64 scalars.
+struct ColState {
+    double rho;     // r^T z (z = r without preconditioner)
+    double sigma;   // p^T A p
+    double a;       // step length rho / sigma (0 when inactive)
+    double beta;    // rho' / rho (0 when inactive)
+    double rr;      // ||r||^2
+    double bb;      // ||b||^2
+    double tol2;    // tol^2 ||b||^2
+    int active;
+    int iters;
+    int status;
+    int pad;
+};
+
+// Low-rank product helpers (storage-specific implementations).
+//  reduce: part[c][k][j] = sum over rows of chunk c of U[i][k] * V[i][j]
+//  expand: out = f(U H) for each row (see ExpandOp)
+enum ExpandOp {
+    EXP_SET_X = 0,      // x_i   = U_i H
+    EXP_SUB_R = 1,      // r_i  -= U_i H
+    EXP_ADD_Q = 2,      // q_i  += U_i H
+    EXP_DIRECTION = 3,  // p_i   = r_i + U_i H + beta p_i
+};
+
+struct LowRank {
+    const hd_eig* e;
+    int32_t rpad;       // r rounded up to 64
+    int32_t nchunk;     // row chunks of the reduction partials
+    float* part;        // [nchunk][rpad][Bp]
+    double* C;          // [rpad][Bp] fp64
+    float* H;           // [rpad][Bp] fp32
+    __nv_bfloat16* Hhi; // [Bp16][rpad] bf16 (transposed, K-major) high part of H
+    __nv_bfloat16* Hlo; // low part
+    int32_t Bp16;
+};
+
+int lr_reduce(hd_ctx* ctx, const LowRank& lr, const float* V, int64_t n, int32_t Bp);
+int lr_finish(hd_ctx* ctx, const LowRank& lr, int32_t Bp, const double* coef);
+int lr_expand(hd_ctx* ctx, const LowRank& lr, int op, float* out, const float* Rv, const float* Pv, int64_t n,
+              int32_t Bp, const ColState* st);
+bool lr_use_tensor_cores(const hd_eig* e);
+int lr_tc_reduce(hd_ctx* ctx, const LowRank& lr, const float* V, int64_t n, int32_t Bp);
+int lr_tc_expand(hd_ctx* ctx, const LowRank& lr, int op, float* out, const float* Rv, const float* Pv, int64_t n,
+                 int32_t Bp, const ColState* st);
+int lr_tc_nchunk(hd_ctx* ctx, int64_t n);

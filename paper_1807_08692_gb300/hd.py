@@ -1,0 +1,352 @@
+"""Thin ctypes binding of libhd.so (include/hd.h), same entry-point names.
+
+Only argument marshalling happens here: torch tensors pass their data_ptr(),
+numpy arrays pass host pointers, and every computation runs in the library's
+CUDA kernels.  PyTorch provides device memory and the current CUDA stream.
+If the library is missing, loading raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhd.so")
+
+OK = 0
+ERR_INVALID_ARG = -1
+ERR_OOM = -2
+ERR_CUDA = -3
+ERR_TIMEOUT = -4
+ERR_NOT_CONVERGED = -5
+PENDING = -6
+F32, BF16, FP8 = 0, 1, 2
+SYM_UNION, SYM_MUTUAL = 0, 1
+MODE_PAPER, MODE_PROJ, MODE_PCG = 0, 1, 2
+COL_CONVERGED, COL_MAX_ITER, COL_BREAKDOWN, COL_EMPTY = 0, 1, 2, 3
+
+MODES = {"paper": MODE_PAPER, "proj": MODE_PROJ, "pcg": MODE_PCG}
+STORAGES = {"f32": F32, "bf16": BF16, "fp8": FP8}
+
+_lib = None
+
+vp, i32, i64, f32, f64, u64 = C.c_void_p, C.c_int32, C.c_int64, C.c_float, C.c_double, C.c_uint64
+
+_SIGS = {
+    "hd_create": (C.c_int, [C.POINTER(vp), C.c_int, vp]),
+    "hd_set_stream": (C.c_int, [vp, vp]),
+    "hd_destroy": (C.c_int, [vp]),
+    "hd_last_error": (C.c_char_p, [vp]),
+    "hd_launch_count": (i64, [vp]),
+    "hd_num_sms": (C.c_int, [vp]),
+    "hd_profile_enable": (C.c_int, [vp, C.c_int]),
+    "hd_profile_read": (C.c_int, [vp, C.c_char_p, C.POINTER(i64), C.POINTER(f64)]),
+    "hd_graph_from_csr": (C.c_int, [vp, i64, i64, vp, vp, vp, C.c_int, C.POINTER(vp)]),
+    "hd_build_graph": (C.c_int, [vp, vp, i64, i32, C.c_int, i32, f32, C.c_int, C.POINTER(vp)]),
+    "hd_knn": (C.c_int, [vp, vp, i64, i32, C.c_int, vp, i64, i32, C.c_int, vp, vp]),
+    "hd_observe": (C.c_int, [vp, vp, i64, i32, C.c_int, vp, i32, i32, f32, vp, vp, vp]),
+    "hd_graph_info": (C.c_int, [vp, C.POINTER(i64), C.POINTER(i64)]),
+    "hd_graph_export": (C.c_int, [vp, vp, vp, vp, vp, vp]),
+    "hd_graph_destroy": (C.c_int, [vp]),
+    "hd_eig_from_host": (C.c_int, [vp, vp, i32, vp, vp, C.c_int, C.POINTER(vp)]),
+    "hd_eigendecompose": (C.c_int, [vp, vp, i32, i32, i32, f64, i32, C.c_int, u64, C.POINTER(vp), vp, vp]),
+    "hd_eig_info": (C.c_int, [vp, C.POINTER(i32), C.POINTER(C.c_int)]),
+    "hd_eig_export": (C.c_int, [vp, vp, vp, vp]),
+    "hd_eig_destroy": (C.c_int, [vp]),
+    "hd_query_batch": (C.c_int, [vp, vp, vp, C.c_int, i32, vp, vp, vp, f32, vp, i32, vp, i32, vp, vp, vp]),
+    "hd_rank": (C.c_int, [vp, vp, i64, i32, i32, vp, i32, i32, vp, vp]),
+    "hd_eig_project": (C.c_int, [vp, vp, vp, i32, vp]),
+    "hd_eig_expand": (C.c_int, [vp, vp, vp, i32, vp]),
+}
+
+
+class HDError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"hd error {code}: {msg}")
+        self.code = code
+
+
+def lib():
+    """Load libhd.so (built by paper_1807_08692_gb300.build); raise if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: run __graft_entry__.build() (no CPU fallback exists)")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name, None)
+            if fn is None:
+                continue
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return [n for n in _SIGS if hasattr(lib(), n)]
+
+
+def _ptr(x):
+    """Pointer of a torch tensor, a numpy array or None."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        assert x.flags["C_CONTIGUOUS"], "numpy arrays must be C-contiguous"
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        assert x.dim() == 0 or x.stride(-1) == 1, "tensors must be row-major with unit column stride"
+        return x.data_ptr()
+    if isinstance(x, int):
+        return x
+    raise TypeError(type(x))
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+class Context:
+    """A library context on one device and one stream (hd_create)."""
+
+    def __init__(self, device: int = 0, stream=None):
+        import torch
+        torch.cuda.init()
+        self._h = vp()
+        rc = lib().hd_create(C.byref(self._h), device, _stream_handle(stream))
+        if rc != OK:
+            raise HDError(rc, "hd_create failed")
+        self.device = device
+
+    @property
+    def handle(self):
+        return self._h
+
+    def check(self, rc, what=""):
+        if rc != OK:
+            raise HDError(rc, f"{what}: {lib().hd_last_error(self._h).decode()}")
+        return rc
+
+    def set_stream(self, stream=None):
+        self.check(lib().hd_set_stream(self._h, _stream_handle(stream)), "hd_set_stream")
+
+    def launches(self) -> int:
+        return int(lib().hd_launch_count(self._h))
+
+    def num_sms(self) -> int:
+        return int(lib().hd_num_sms(self._h))
+
+    def profile(self, on: bool = True):
+        self.check(lib().hd_profile_enable(self._h, int(on)), "hd_profile_enable")
+
+    def profile_read(self, name: str):
+        """(launches, total_ms) of a kernel family since the last read."""
+        cnt, ms = i64(), f64()
+        self.check(lib().hd_profile_read(self._h, name.encode(), C.byref(cnt), C.byref(ms)), "hd_profile_read")
+        return cnt.value, ms.value
+
+    def close(self):
+        if self._h:
+            lib().hd_destroy(self._h)
+            self._h = vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Graph:
+    def __init__(self, ctx: Context, h):
+        self.ctx, self._h = ctx, h
+        n, nnz = i64(), i64()
+        lib().hd_graph_info(h, C.byref(n), C.byref(nnz))
+        self.n, self.nnz = n.value, nnz.value
+
+    @property
+    def handle(self):
+        return self._h
+
+    def export(self):
+        """(row_ptr, col, val, dinv) as numpy arrays (host copies)."""
+        rp = np.empty(self.n + 1, np.int32)
+        col = np.empty(self.nnz, np.int32)
+        val = np.empty(self.nnz, np.float32)
+        dinv = np.empty(self.n, np.float32)
+        self.ctx.check(lib().hd_graph_export(self.ctx.handle, self._h, _ptr(rp), _ptr(col), _ptr(val), _ptr(dinv)),
+                       "hd_graph_export")
+        return rp, col, val, dinv
+
+    def close(self):
+        if self._h:
+            lib().hd_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Eig:
+    def __init__(self, ctx: Context, h, n):
+        self.ctx, self._h, self.n = ctx, h, n
+        r, st = i32(), C.c_int()
+        lib().hd_eig_info(h, C.byref(r), C.byref(st))
+        self.r, self.storage = r.value, st.value
+
+    @property
+    def handle(self):
+        return self._h
+
+    def export(self):
+        lam = np.empty(self.r, np.float64)
+        U = np.empty((self.n, self.r), np.float32)
+        self.ctx.check(lib().hd_eig_export(self.ctx.handle, self._h, _ptr(lam), _ptr(U)), "hd_eig_export")
+        return lam, U
+
+    def close(self):
+        if self._h:
+            lib().hd_eig_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _dtype_code(X):
+    import torch
+    if isinstance(X, np.ndarray):
+        if X.dtype == np.float32:
+            return F32
+        if X.dtype == np.uint16:
+            return BF16
+        raise TypeError(X.dtype)
+    if X.dtype == torch.float32:
+        return F32
+    if X.dtype == torch.bfloat16:
+        return BF16
+    raise TypeError(X.dtype)
+
+
+def graph_from_csr(ctx: Context, row_ptr, col, val, normalized: bool = False) -> Graph:
+    n = len(row_ptr) - 1
+    nnz = len(col)
+    h = vp()
+    ctx.check(lib().hd_graph_from_csr(ctx.handle, n, nnz, _ptr(row_ptr), _ptr(col), _ptr(val), int(normalized),
+                                      C.byref(h)), "hd_graph_from_csr")
+    return Graph(ctx, h)
+
+
+def build_graph(ctx: Context, X, k: int, gamma: float = 3.0, sym: int = SYM_UNION) -> Graph:
+    n, d = X.shape
+    h = vp()
+    ctx.check(lib().hd_build_graph(ctx.handle, _ptr(X), n, d, _dtype_code(X), k, gamma, sym, C.byref(h)),
+              "hd_build_graph")
+    return Graph(ctx, h)
+
+
+def knn(ctx: Context, X, Q, k: int, exclude_self: bool = False):
+    """Neighbour lists (idx, sim) as device tensors when X is on the device, else numpy."""
+    import torch
+    n, d = X.shape
+    nq = Q.shape[0]
+    if hasattr(X, "is_cuda") and X.is_cuda:
+        idx = torch.empty((nq, k), dtype=torch.int32, device=X.device)
+        sim = torch.empty((nq, k), dtype=torch.float32, device=X.device)
+    else:
+        idx = np.empty((nq, k), np.int32)
+        sim = np.empty((nq, k), np.float32)
+    ctx.check(lib().hd_knn(ctx.handle, _ptr(X), n, d, _dtype_code(X), _ptr(Q), nq, k, int(exclude_self), _ptr(idx),
+                           _ptr(sim)), "hd_knn")
+    return idx, sim
+
+
+def observe(ctx: Context, X, Q, k_y: int, gamma: float = 3.0):
+    """Observation vectors: (y_ptr, y_idx, y_val) host numpy arrays."""
+    n, d = X.shape
+    nq = Q.shape[0]
+    ptr = np.empty(nq + 1, np.int32)
+    idx = np.empty(nq * k_y, np.int32)
+    val = np.empty(nq * k_y, np.float32)
+    ctx.check(lib().hd_observe(ctx.handle, _ptr(X), n, d, _dtype_code(X), _ptr(Q), nq, k_y, gamma, _ptr(ptr),
+                               _ptr(idx), _ptr(val)), "hd_observe")
+    m = int(ptr[-1])
+    return ptr, idx[:m].copy(), val[:m].copy()
+
+
+def eig_from_host(ctx: Context, g: Graph, lam, U, storage="bf16") -> Eig:
+    lam = np.ascontiguousarray(lam, dtype=np.float64)
+    r = lam.size
+    if not hasattr(U, "data_ptr"):
+        U = np.ascontiguousarray(U, dtype=np.float32)
+    h = vp()
+    ctx.check(lib().hd_eig_from_host(ctx.handle, g.handle, r, _ptr(lam), _ptr(U),
+                                     STORAGES.get(storage, storage), C.byref(h)), "hd_eig_from_host")
+    return Eig(ctx, h, g.n)
+
+
+def eigendecompose(ctx: Context, g: Graph, r: int, block: int = 32, max_basis: int = 0, tol: float = 1e-6,
+                   max_restarts: int = 30, storage="bf16", seed: int = 1):
+    """Largest r eigenpairs by block Lanczos: (Eig, eigenvalues, residuals, converged)."""
+    lam = np.zeros(r, np.float64)
+    res = np.zeros(r, np.float64)
+    h = vp()
+    rc = lib().hd_eigendecompose(ctx.handle, g.handle, r, block, max_basis, tol, max_restarts,
+                                 STORAGES.get(storage, storage), seed, C.byref(h), _ptr(lam), _ptr(res))
+    if rc not in (OK, ERR_NOT_CONVERGED):
+        ctx.check(rc, "hd_eigendecompose")
+    return Eig(ctx, h, g.n), lam, res, rc == OK
+
+
+def query_batch(ctx: Context, g: Graph, eig, mode, y_ptr, y_idx, y_val, alpha: float, tol, max_iter: int,
+                X=None, ldx=None, iters=None, relres=None, status=None):
+    """Solve B ranking vectors; X defaults to a new (n x B) device tensor.
+
+    Returns (X, iters, relres, status); the per-column arrays are numpy unless
+    device tensors were passed in.
+    """
+    import torch
+    B = len(y_ptr) - 1
+    if isinstance(mode, str):
+        mode = MODES[mode]
+    if np.isscalar(tol):
+        tol = np.full(B, tol, np.float32)
+    if isinstance(tol, np.ndarray):
+        tol = np.ascontiguousarray(tol, dtype=np.float32)
+    if X is None:
+        X = torch.empty((g.n, B), dtype=torch.float32, device=f"cuda:{ctx.device}")
+    if ldx is None:
+        ldx = X.shape[1] if X.ndim == 2 else B
+    iters = np.zeros(B, np.int32) if iters is None else iters
+    relres = np.zeros(B, np.float32) if relres is None else relres
+    status = np.zeros(B, np.int32) if status is None else status
+    rc = lib().hd_query_batch(ctx.handle, g.handle, eig.handle if eig is not None else None, mode, B, _ptr(y_ptr),
+                              _ptr(y_idx), _ptr(y_val), alpha, _ptr(tol), max_iter, _ptr(X), ldx, _ptr(iters),
+                              _ptr(relres), _ptr(status))
+    ctx.check(rc, "hd_query_batch")
+    return X, iters, relres, status
+
+
+def rank(ctx: Context, X, K, Kmax: int | None = None, pool: int = 0, n: int | None = None, idx=None, score=None):
+    """Per-column top-K of device scores X (n x B): (idx, score), each B x Kmax."""
+    B = X.shape[1]
+    ldx = X.stride(0)
+    n = X.shape[0] if n is None else n
+    K = np.ascontiguousarray(np.broadcast_to(np.asarray(K, dtype=np.int32), (B,)))
+    Kmax = int(K.max()) if Kmax is None else Kmax
+    if idx is None:
+        idx = np.empty((B, Kmax), np.int32)
+        score = np.empty((B, Kmax), np.float32)
+    ctx.check(lib().hd_rank(ctx.handle, _ptr(X), n, B, ldx, _ptr(K), Kmax, pool, _ptr(idx), _ptr(score)), "hd_rank")
+    return idx, score

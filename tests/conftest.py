@@ -26,3 +26,31 @@ def small_graph():
     A = graph.adjacency(X, 6)
     W, dinv = graph.normalize(A)
     return {"X": X, "A": A, "W": W, "dinv": dinv, "lab": lab, "n": 60}
+
+
+@pytest.fixture(scope="session")
+def cfg1_data():
+    """The 2,000-node workload (d=128, 20 vMF components, k=30, 16 queries,
+    top-10 observations), built entirely by the oracle in fp64."""
+    import numpy as np
+    import synth
+    from oracle import graph, observe, spectral, diffusion
+    c = synth.get_config("cfg1")
+    X, lab = synth.database(c.seed, c.n, c.d, c.ncl, c.kappa_lo, c.kappa_hi, c.sizes)
+    Qv = synth.queries(c.seed, c.batch, c.d, c.ncl, c.kappa_lo, c.kappa_hi, c.sizes)
+    A = graph.adjacency(X, c.k, c.gamma)
+    W, dinv = graph.normalize(A)
+    yp, yi, yv = observe.observe(X, Qv, c.k_y, c.gamma)
+    Y = observe.dense(c.n, yp, yi, yv)
+    lam, U = spectral.eigh_desc(W)
+    xstar = diffusion.closed_form(W, Y, c.alpha)
+    return {"cfg": c, "X": X, "Q": Qv, "A": A, "W": W, "dinv": dinv, "yp": yp, "yi": yi, "yv": yv, "Y": Y,
+            "lam": lam, "U": U, "xstar": xstar}
+
+
+@pytest.fixture(scope="session")
+def gpu_ctx():
+    import paper_1807_08692_gb300 as hd
+    ctx = hd.Context(0)
+    yield ctx
+    ctx.close()
