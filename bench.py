@@ -50,6 +50,10 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--quick", action="store_true", help="skip the r=0 leg and calibration (profiling runs)")
+    ap.add_argument("--serve-rates", default="1000,4000,16000",
+                    help="Poisson arrival rates (req/s) of the serving leg; empty to skip")
+    ap.add_argument("--serve-requests", type=int, default=1500)
+    ap.add_argument("--serve-slots", type=int, default=128)
     return ap.parse_args()
 
 
@@ -128,8 +132,7 @@ def build_workload(args, ctx, rank):
     Qv = synth.queries(c.seed + 1000 * rank, nq, d, c.ncl, c.kappa_lo, c.kappa_hi, c.sizes, c.zipf_s)
     Qt = torch.from_numpy(Qv).to(Xt.dtype).cuda()
     yp, yi, yv = hd.observe(ctx, Xt, Qt, c.k_y, c.gamma)
-    del Xt, Qt
-    torch.cuda.empty_cache()
+    del Qt
     B = args.batch
     cal = (yp[:B + 1].copy(), yi[:yp[B]].copy(), yv[:yp[B]].copy())
     off = yp[B]
@@ -141,7 +144,7 @@ def build_workload(args, ctx, rank):
                                                 storage=args.storage)
     torch.cuda.synchronize()
     t_eig = time.time() - t0
-    return {"cfg": c, "n": n, "d": d, "g": g, "cal": cal, "tim": tim, "eig": eig, "lam": lam, "res": res,
+    return {"cfg": c, "n": n, "d": d, "g": g, "Xt": Xt, "cal": cal, "tim": tim, "eig": eig, "lam": lam, "res": res,
             "conv": conv, "t_gen": t_gen, "t_graph": t_graph, "t_eig": t_eig}
 
 
@@ -286,6 +289,65 @@ def cpu_oracle(wl, args, alpha, tol, columns):
     return dt, iters
 
 
+# ------------------------------------------------------------------ serving (continuous batching)
+def serve_leg(ctx, wl, eig, args, rates, alpha):
+    """Open-loop Poisson arrivals into the continuous-batching server; each
+    request draws its tolerance from {1e-2, 1e-4, 1e-6} and K from {10, 100,
+    1000}.  Latency = completion (ranking on the host) - scheduled arrival."""
+    import torch
+    import paper_1807_08692_gb300 as hd
+    import synth
+    c = wl["cfg"]
+    nreq = args.serve_requests
+    Qv = synth.queries(c.seed + 5000, nreq, wl["d"], c.ncl, c.kappa_lo, c.kappa_hi, c.sizes, c.zipf_s)
+    yp, yi, yv = hd.observe(ctx, wl["Xt"], torch.from_numpy(Qv).to(wl["Xt"].dtype).cuda(), c.k_y, c.gamma)
+    tols, Ks = synth.request_draws(c.seed, nreq)
+    out = []
+    for rate in rates:
+        srv = hd.Server(ctx, wl["g"], eig, "pcg" if eig is not None else "paper", alpha, max_slots=args.serve_slots,
+                        max_iter=2000, Kmax=1000)
+        arr = synth.poisson_arrivals(c.seed + int(rate), rate, nreq)
+        lat, tick = [], {}
+        # warm-up: a few requests through the server before the clock starts
+        for j in range(min(8, nreq)):
+            tick[srv.submit(yi[yp[j]:yp[j + 1]], yv[yp[j]:yp[j + 1]], 1e-4, 10)] = (10, None)
+        while srv.step(2):
+            pass
+        for t in list(tick):
+            srv.poll(t, 10)
+        tick.clear()
+        t0 = time.monotonic()
+        nxt = 0
+        done = 0
+        last_done = t0
+        iters = []
+        while done < nreq:
+            now = time.monotonic() - t0
+            while nxt < nreq and arr[nxt] <= now:
+                t = srv.submit(yi[yp[nxt]:yp[nxt + 1]], yv[yp[nxt]:yp[nxt + 1]], float(tols[nxt]), int(Ks[nxt]))
+                tick[t] = (int(Ks[nxt]), t0 + arr[nxt])
+                nxt += 1
+            busy = srv.step(2)
+            for t in list(tick):
+                res = srv.poll(t, tick[t][0])
+                if res is not None:
+                    lat.append(res[2]["done_s"] - tick[t][1])
+                    iters.append(res[2]["iters"])
+                    last_done = max(last_done, res[2]["done_s"])
+                    del tick[t]
+                    done += 1
+            if not busy and nxt < nreq:
+                time.sleep(max(0.0, min(arr[nxt] - (time.monotonic() - t0), 0.002)))
+        span = last_done - (t0 + arr[0])
+        lat_ms = 1e3 * np.asarray(lat)
+        out.append({"rate": rate, "requests": nreq, "qps": round(nreq / span, 1),
+                    "p50_ms": round(float(np.percentile(lat_ms, 50)), 3),
+                    "p99_ms": round(float(np.percentile(lat_ms, 99)), 3),
+                    "mean_iters": round(float(np.mean(iters)), 2), "slots": srv.slots})
+        srv.close()
+    return out
+
+
 # ------------------------------------------------------------------ main
 def main():
     args = parse()
@@ -343,6 +405,11 @@ def main():
         es, h2d, d2h = e2e_leg(ctx, wl, eig, args.mode, tol_h, alpha, args.steps, B, args.topk)
         e2e = {"value": B * args.steps / es * world, "unit": "queries/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h)}
+    # ---- serving: continuous batching under Poisson load
+    serving = None
+    rates = [float(x) for x in args.serve_rates.split(",") if x.strip()]
+    if rates:
+        serving = serve_leg(ctx, wl, eig, args, rates, alpha)
     # ---- roofline of the dominant kernel
     ab = algorithmic_bytes(wl, B, eig)
     fam = hyb["fam"]
@@ -389,7 +456,7 @@ def main():
                    "setup_s": {"gen": round(wl["t_gen"], 1), "graph": round(wl["t_graph"], 1),
                                "eig": round(wl["t_eig"], 1)}},
         "p50_ms": round(float(np.percentile(hyb["ms"], 50)), 4), "p99_ms": round(float(np.percentile(hyb["ms"], 99)), 4),
-        "cg_r0": cg, "e2e": e2e, "gpu_launches": int(hyb["launches"]), "roofline": roofline, "cpu_baseline": cpu,
+        "cg_r0": cg, "serving": serving, "e2e": e2e, "gpu_launches": int(hyb["launches"]), "roofline": roofline, "cpu_baseline": cpu,
         "clocks": clocks, "wall_s_timed": round(t_wall, 3),
     }
     if rank == 0:

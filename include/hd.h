@@ -16,7 +16,7 @@
  *    call.  Pointers marked "device" must be device memory on the context's
  *    device.  All input buffers stay owned by the caller and are only read
  *    during the call; output buffers are caller-provided.
- *  - Handles (hd_ctx, hd_graph, hd_eig) are allocated by the
+ *  - Handles (hd_ctx, hd_graph, hd_eig, hd_server) are allocated by the
  *    library and released with the matching *_destroy call.
  *  - All device work of a context is issued on the context's stream, in
  *    order.  Calls are thread-compatible per context, not thread-safe.
@@ -67,6 +67,7 @@ extern "C" {
 typedef struct hd_ctx hd_ctx;
 typedef struct hd_graph hd_graph;
 typedef struct hd_eig hd_eig;
+typedef struct hd_server hd_server;
 
 /* ---- context ------------------------------------------------------------- */
 
@@ -204,6 +205,47 @@ int hd_query_batch(hd_ctx* ctx, const hd_graph* g, const hd_eig* eig, int mode, 
  * offset j*Kmax; entries past K[j] are -1 / 0. */
 int hd_rank(hd_ctx* ctx, const float* X, int64_t n, int32_t B, int32_t ldx, const int32_t* K,
             int32_t Kmax, int32_t pool, int32_t* idx_out, float* score_out);
+
+/* ---- serving: continuous batching (spec serving pattern) ---------------- */
+
+typedef struct hd_req_stats {
+    double submit_s;    /* host steady clock (s) at hd_serve_submit */
+    double admit_s;     /* when the request got a column of the batch */
+    double done_s;      /* when its ranking had been copied to the host */
+    int32_t iters;      /* CG iterations the request used */
+    int32_t status;     /* HD_COL_* */
+    float relres;       /* final relative residual ||r|| / ||y|| */
+    int32_t slot;       /* batch column it ran in */
+} hd_req_stats;
+
+/* Open a server over a graph and optional eigenpairs.  The server owns one
+ * persistent batch of up to max_slots columns (<= 256); with mem_budget > 0
+ * the slot count is cut to what fits (each slot needs 4*n*4 + Kmax*8 bytes for
+ * its R, P, Q, X columns and ranking).  With eigenpairs the mode must be
+ * HD_MODE_PCG (the paper's form needs a per-request spectral term at
+ * admission); without, it is temporal CG.  Kmax <= 2048 bounds per-request K.
+ * Errors: HD_ERR_OOM when not even one slot fits the budget or the device. */
+int hd_serve_open(hd_ctx* ctx, const hd_graph* g, const hd_eig* eig, int mode, float alpha,
+                  int32_t max_slots, size_t mem_budget, int32_t max_iter, int32_t Kmax,
+                  hd_server** out);
+/* Columns of the persistent batch. */
+int hd_serve_slots(const hd_server* s);
+/* Queue one request: its observation (nnz_y <= 512 host entries, indices in
+ * [0, n), duplicates summed), residual tolerance and K <= Kmax.  Copies the
+ * arrays; returns a ticket.  Errors: HD_ERR_INVALID_ARG. */
+int hd_serve_submit(hd_server* s, int32_t nnz_y, const int32_t* idx, const float* val, float tol,
+                    int32_t K, uint64_t* ticket);
+/* Admit queued requests into free columns, run `iters` CG iterations of the
+ * whole batch, then retire every column that stopped (converged, max_iter,
+ * breakdown, empty): its top-K is ranked on the device and copied to the host.
+ * *busy (may be NULL) receives the number of queued plus running requests. */
+int hd_serve_step(hd_server* s, int32_t iters, int32_t* busy);
+/* HD_PENDING while the request runs; then copies its K ids / scores (host)
+ * and stats, forgets the ticket and returns HD_OK.  HD_ERR_NOT_FOUND for an
+ * unknown ticket. */
+int hd_serve_poll(hd_server* s, uint64_t ticket, int32_t* idx_out, float* score_out,
+                  hd_req_stats* st);
+int hd_serve_close(hd_server* s);
 
 #ifdef __cplusplus
 }

@@ -224,10 +224,12 @@ __global__ void __launch_bounds__(THREADS, 1)
                         } else {
                             const float4 rr = *reinterpret_cast<const float4*>(a.R + row * a.Bp + j);
                             const float4 pp = *reinterpret_cast<const float4*>(a.P + row * a.Bp + j);
-                            w.x = rr.x + v[4 * q] + (float)a.st[j].beta * pp.x;
-                            w.y = rr.y + v[4 * q + 1] + (float)a.st[j + 1].beta * pp.y;
-                            w.z = rr.z + v[4 * q + 2] + (float)a.st[j + 2].beta * pp.z;
-                            w.w = rr.w + v[4 * q + 3] + (float)a.st[j + 3].beta * pp.w;
+                            const float b0 = (float)a.st[j].beta, b1 = (float)a.st[j + 1].beta;
+                            const float b2 = (float)a.st[j + 2].beta, b3 = (float)a.st[j + 3].beta;
+                            w.x = rr.x + v[4 * q] + (b0 == 0.0f ? 0.0f : b0 * pp.x);
+                            w.y = rr.y + v[4 * q + 1] + (b1 == 0.0f ? 0.0f : b1 * pp.y);
+                            w.z = rr.z + v[4 * q + 2] + (b2 == 0.0f ? 0.0f : b2 * pp.z);
+                            w.w = rr.w + v[4 * q + 3] + (b3 == 0.0f ? 0.0f : b3 * pp.w);
                         }
                         *o = w;
                     }

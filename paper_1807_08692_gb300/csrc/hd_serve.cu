@@ -1,0 +1,395 @@
+// Continuous-batching query server over the multi-RHS CG engine.
+//
+// A server owns one persistent batch of `slots` columns (R, P, Q, X of n x Bp).
+// Requests queue on the host; at each step free columns take queued requests
+// (admission: the column is marked fresh, the next CG update resets it and its
+// observation is scattered in, and the scalar step starts its iteration),
+// every column then advances the same CG iterations, and columns whose
+// residual met their own tolerance retire: their top-K is ranked and copied
+// out and the column is free again.  A column's arithmetic never depends on
+// its slot or on the other columns, so a request gets the same bits alone or
+// in a mix.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <deque>
+#include <unordered_map>
+#include <vector>
+
+#include "hd_solve.cuh"
+
+namespace {
+
+double now_s() {
+    using namespace std::chrono;
+    return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+struct Req {
+    uint64_t ticket = 0;
+    std::vector<int32_t> idx;
+    std::vector<float> val;
+    double bb = 0.0;
+    float tol = 0.f;
+    int32_t K = 0;
+    int32_t slot = -1;
+    double submit_s = 0, admit_s = 0, done_s = 0;
+    int32_t iters = 0, status = 0;
+    float relres = 0.f;
+    bool done = false;
+    std::vector<int32_t> out_idx;
+    std::vector<float> out_score;
+};
+
+struct AdmitRec {
+    int32_t slot;
+    int32_t off;    // into the staged index/value arrays
+    int32_t cnt;
+    float tol;
+    double bb;
+};
+
+__global__ void k_admit_mark(const AdmitRec* recs, int nrec, ColState* st) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nrec) return;
+    const AdmitRec a = recs[t];
+    ColState& s = st[a.slot];
+    s.fresh = 1;
+    s.active = 0;
+    s.a = 0.0;
+    s.beta = 0.0;
+    s.bb = a.bb;
+    s.tol2 = (double)a.tol * (double)a.tol * a.bb;
+}
+
+__global__ void k_admit_scatter(const AdmitRec* recs, int nrec, const int32_t* yidx, const float* yval, float* R,
+                                int32_t ld) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nrec) return;
+    const AdmitRec a = recs[t];
+    for (int e = 0; e < a.cnt; ++e) R[(int64_t)yidx[a.off + e] * ld + a.slot] += yval[a.off + e];
+}
+
+}  // namespace
+
+struct hd_server {
+    hd_ctx* ctx = nullptr;
+    const hd_graph* g = nullptr;
+    const hd_eig* eig = nullptr;
+    int32_t slots = 0, Kmax = 0, max_iter = 0;
+    Engine E;
+    void* dev = nullptr;
+    // admission staging
+    AdmitRec* d_rec = nullptr;
+    int32_t* d_yidx = nullptr;
+    float* d_yval = nullptr;
+    AdmitRec* h_rec = nullptr;
+    int32_t* h_yidx = nullptr;
+    float* h_yval = nullptr;
+    int32_t cap_nnz = 0;
+    int nrec = 0;
+    // ranking outputs
+    int32_t* d_idx = nullptr;
+    float* d_sc = nullptr;
+    int32_t* h_idx = nullptr;
+    float* h_sc = nullptr;
+    ColState* h_st = nullptr;
+    std::deque<Req*> queue;
+    std::vector<Req*> slot_req;
+    std::unordered_map<uint64_t, Req*> reqs;
+    uint64_t next_ticket = 1;
+    bool polled = true;
+};
+
+static void server_free(hd_server* s) {
+    if (!s) return;
+    if (s->ctx) cudaStreamSynchronize(s->ctx->stream);
+    cudaFree(s->dev);
+    cudaFreeHost(s->h_rec);
+    cudaFreeHost(s->h_yidx);
+    cudaFreeHost(s->h_yval);
+    cudaFreeHost(s->h_idx);
+    cudaFreeHost(s->h_sc);
+    cudaFreeHost(s->h_st);
+    for (auto& kv : s->reqs) delete kv.second;
+    delete s;
+}
+
+static int admit_cb(void* arg) {
+    hd_server* s = (hd_server*)arg;
+    if (!s->nrec) return HD_OK;
+    hd_ctx* ctx = s->ctx;
+    k_admit_scatter<<<ceil_div(s->nrec, 64), 64, 0, ctx->stream>>>(s->d_rec, s->nrec, s->d_yidx, s->d_yval, s->E.R,
+                                                                   s->E.Bp);
+    HD_CHECK_LAUNCH(ctx);
+    s->nrec = 0;
+    return HD_OK;
+}
+
+extern "C" {
+
+int hd_serve_open(hd_ctx* ctx, const hd_graph* g, const hd_eig* eig, int mode, float alpha, int32_t max_slots,
+                  size_t mem_budget, int32_t max_iter, int32_t Kmax, hd_server** out) {
+    if (!ctx || !g || !out || max_slots < 1 || max_slots > 256 || Kmax < 1 || Kmax > 2048 || max_iter < 1)
+        return HD_ERR_INVALID_ARG;
+    if (!(alpha >= 0.0f && alpha < 1.0f)) return hd_fail(ctx, HD_ERR_INVALID_ARG, "alpha=%g", alpha);
+    const bool lr_on = eig && eig->r > 0;
+    if (lr_on && mode != HD_MODE_PCG)
+        return hd_fail(ctx, HD_ERR_INVALID_ARG, "the server runs PCG with eigenpairs (mode %d unsupported)", mode);
+    *out = nullptr;
+    HD_CUDA(ctx, cudaSetDevice(ctx->device));
+    const int64_t n = g->n;
+    // admission by device memory: each slot holds R, P, Q, X columns and its ranking
+    const size_t per_slot = (size_t)4 * n * 4 + (size_t)Kmax * 8;
+    int32_t slots = max_slots;
+    if (mem_budget > 0) slots = (int32_t)std::min<size_t>(max_slots, mem_budget / per_slot);
+    if (slots < 1) return hd_fail(ctx, HD_ERR_OOM, "memory budget %zu below one slot (%zu bytes)", mem_budget, per_slot);
+    hd_server* s = new hd_server();
+    s->ctx = ctx;
+    s->g = g;
+    s->eig = eig;
+    s->slots = slots;
+    s->Kmax = Kmax;
+    s->max_iter = max_iter;
+    Engine& E = s->E;
+    E.ctx = ctx;
+    E.g = g;
+    E.n = n;
+    E.B = slots;
+    E.Bp = (slots + 3) / 4 * 4;
+    E.vl = vec_launch(ctx, n, E.Bp);
+    E.has_lr = lr_on;
+    E.r = lr_on ? eig->r : 0;
+    E.eff_mode = lr_on ? HD_MODE_PCG : HD_MODE_PAPER;
+    E.c1 = (float)(1.0 / (1.0 - (double)alpha));
+    E.c2 = (float)((double)alpha / (1.0 - (double)alpha));
+    E.xs = 1.0f;
+    E.max_iter = max_iter;
+    const int32_t Bp = E.Bp;
+    const int rpad = lr_on ? (eig->r + 63) / 64 * 64 : 0;
+    const int Bp16 = (Bp + 15) / 16 * 16;
+    int nchunk = 0;
+    if (lr_on) nchunk = lr_use_tensor_cores(eig) ? lr_tc_nchunk(ctx, n) : simt_nchunk(ctx, n, rpad, Bp);
+    s->cap_nnz = Bp * 512;
+    const size_t vec = (size_t)n * Bp * 4;
+    size_t bytes = 4 * ws_size(vec) + ws_size((size_t)E.vl.nblk * Bp * 8) + ws_size(Bp * sizeof(ColState)) +
+                   ws_size(64) + ws_size(Bp * sizeof(AdmitRec)) + 2 * ws_size((size_t)s->cap_nnz * 4) +
+                   2 * ws_size((size_t)Bp * Kmax * 4);
+    if (lr_on)
+        bytes += ws_size((size_t)nchunk * rpad * Bp * 4) + ws_size((size_t)rpad * Bp * 8) +
+                 ws_size((size_t)rpad * Bp * 4) + 2 * ws_size((size_t)Bp16 * rpad * 2) + ws_size(rpad * 8);
+    if (cudaMalloc(&s->dev, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        server_free(s);
+        return hd_fail(ctx, HD_ERR_OOM, "server buffers: %zu bytes", bytes);
+    }
+    s->slot_req.assign(slots, nullptr);
+    WsCarver cv(s->dev);
+    E.R = cv.take<float>((size_t)n * Bp);
+    E.P = cv.take<float>((size_t)n * Bp);
+    E.Q = cv.take<float>((size_t)n * Bp);
+    E.X = cv.take<float>((size_t)n * Bp);
+    E.part = cv.take<float2>((size_t)E.vl.nblk * Bp);
+    E.st = cv.take<ColState>(Bp);
+    E.num_active = cv.take<int>(16);
+    E.err = E.num_active + 1;
+    s->d_rec = cv.take<AdmitRec>(Bp);
+    s->d_yidx = cv.take<int32_t>(s->cap_nnz);
+    s->d_yval = cv.take<float>(s->cap_nnz);
+    s->d_idx = cv.take<int32_t>((size_t)Bp * Kmax);
+    s->d_sc = cv.take<float>((size_t)Bp * Kmax);
+    if (lr_on) {
+        E.lr.e = eig;
+        E.lr.rpad = rpad;
+        E.lr.nchunk = nchunk;
+        E.lr.Bp16 = Bp16;
+        E.lr.part = cv.take<float>((size_t)nchunk * rpad * Bp);
+        E.lr.C = cv.take<double>((size_t)rpad * Bp);
+        E.lr.H = cv.take<float>((size_t)rpad * Bp);
+        E.lr.Hhi = cv.take<__nv_bfloat16>((size_t)Bp16 * rpad);
+        E.lr.Hlo = cv.take<__nv_bfloat16>((size_t)Bp16 * rpad);
+        E.dcoef = cv.take<double>(rpad);
+        std::vector<double> dc(rpad, 0.0);
+        for (int k = 0; k < eig->r; ++k) {
+            const double l = std::max(0.0, eig->lambda_h[k]);
+            dc[k] = (double)alpha * l / (1.0 - (double)alpha * l);
+        }
+        HD_CUDA(ctx, cudaMemcpyAsync(E.dcoef, dc.data(), rpad * 8, cudaMemcpyHostToDevice, ctx->stream));
+        HD_CUDA(ctx, cudaMemsetAsync(E.lr.Hhi, 0, (size_t)Bp16 * rpad * 2, ctx->stream));
+        HD_CUDA(ctx, cudaMemsetAsync(E.lr.Hlo, 0, (size_t)Bp16 * rpad * 2, ctx->stream));
+    }
+    HD_CUDA(ctx, cudaMemsetAsync(s->dev, 0, 4 * ws_size(vec), ctx->stream));
+    std::vector<ColState> st0(Bp);
+    for (auto& c : st0) {
+        memset(&c, 0, sizeof c);
+        c.status = HD_COL_EMPTY;
+    }
+    HD_CUDA(ctx, cudaMemcpyAsync(E.st, st0.data(), Bp * sizeof(ColState), cudaMemcpyHostToDevice, ctx->stream));
+    if (cudaMallocHost(&s->h_rec, Bp * sizeof(AdmitRec)) || cudaMallocHost(&s->h_yidx, (size_t)s->cap_nnz * 4) ||
+        cudaMallocHost(&s->h_yval, (size_t)s->cap_nnz * 4) || cudaMallocHost(&s->h_idx, (size_t)Bp * Kmax * 4) ||
+        cudaMallocHost(&s->h_sc, (size_t)Bp * Kmax * 4) || cudaMallocHost(&s->h_st, Bp * sizeof(ColState))) {
+        server_free(s);
+        return hd_fail(ctx, HD_ERR_OOM, "pinned host buffers");
+    }
+    HD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    *out = s;
+    return HD_OK;
+}
+
+int hd_serve_slots(const hd_server* s) { return s ? s->slots : 0; }
+
+int hd_serve_submit(hd_server* s, int32_t nnz_y, const int32_t* idx, const float* val, float tol, int32_t K,
+                    uint64_t* ticket) {
+    if (!s || !ticket || nnz_y < 0 || (nnz_y > 0 && (!idx || !val)) || K < 0 || K > s->Kmax || nnz_y > 512)
+        return s ? hd_fail(s->ctx, HD_ERR_INVALID_ARG, "bad request (nnz %d, K %d)", nnz_y, K) : HD_ERR_INVALID_ARG;
+    Req* r = new Req();
+    // duplicates are summed; ||y||^2 is the norm of the summed vector
+    std::vector<std::pair<int32_t, float>> e(nnz_y);
+    for (int t = 0; t < nnz_y; ++t) {
+        if (idx[t] < 0 || idx[t] >= s->g->n) {
+            delete r;
+            return hd_fail(s->ctx, HD_ERR_INVALID_ARG, "observation index %d out of range", idx[t]);
+        }
+        e[t] = {idx[t], val[t]};
+    }
+    r->idx.assign(idx, idx + nnz_y);
+    r->val.assign(val, val + nnz_y);
+    std::stable_sort(e.begin(), e.end(), [](auto& a, auto& b) { return a.first < b.first; });
+    double bb = 0.0;
+    for (size_t t = 0; t < e.size();) {
+        float acc = 0.0f;
+        size_t u = t;
+        for (; u < e.size() && e[u].first == e[t].first; ++u) acc += e[u].second;
+        bb += (double)acc * (double)acc;
+        t = u;
+    }
+    r->bb = bb;
+    r->tol = tol;
+    r->K = K;
+    r->ticket = s->next_ticket++;
+    r->submit_s = now_s();
+    s->queue.push_back(r);
+    s->reqs[r->ticket] = r;
+    *ticket = r->ticket;
+    return HD_OK;
+}
+
+int hd_serve_step(hd_server* s, int32_t iters, int32_t* busy) {
+    if (!s || iters < 0) return HD_ERR_INVALID_ARG;
+    hd_ctx* ctx = s->ctx;
+    Engine& E = s->E;
+    const int32_t Bp = E.Bp;
+    // ---- admission into free columns
+    s->nrec = 0;
+    int32_t off = 0;
+    for (int j = 0; j < s->slots && !s->queue.empty(); ++j) {
+        if (s->slot_req[j]) continue;
+        Req* r = s->queue.front();
+        if (off + (int32_t)r->idx.size() > s->cap_nnz) break;
+        s->queue.pop_front();
+        r->slot = j;
+        r->admit_s = now_s();
+        s->slot_req[j] = r;
+        AdmitRec& a = s->h_rec[s->nrec++];
+        a.slot = j;
+        a.off = off;
+        a.cnt = (int32_t)r->idx.size();
+        a.tol = r->tol;
+        a.bb = r->bb;
+        std::copy(r->idx.begin(), r->idx.end(), s->h_yidx + off);
+        std::copy(r->val.begin(), r->val.end(), s->h_yval + off);
+        off += a.cnt;
+    }
+    if (s->nrec) {
+        HD_CUDA(ctx, cudaMemcpyAsync(s->d_rec, s->h_rec, s->nrec * sizeof(AdmitRec), cudaMemcpyHostToDevice, ctx->stream));
+        HD_CUDA(ctx, cudaMemcpyAsync(s->d_yidx, s->h_yidx, (size_t)off * 4, cudaMemcpyHostToDevice, ctx->stream));
+        HD_CUDA(ctx, cudaMemcpyAsync(s->d_yval, s->h_yval, (size_t)off * 4, cudaMemcpyHostToDevice, ctx->stream));
+        k_admit_mark<<<ceil_div(s->nrec, 64), 64, 0, ctx->stream>>>(s->d_rec, s->nrec, E.st);
+        HD_CHECK_LAUNCH(ctx);
+        if (iters < 1) iters = 1;  // the admission completes inside the next iteration
+    }
+    bool running = s->nrec > 0;
+    for (int j = 0; j < s->slots && !running; ++j) running = s->slot_req[j] != nullptr;
+    // ---- iterations of every column
+    for (int t = 0; t < iters && running; ++t) {
+        int rc = engine_iteration(E, admit_cb, s);
+        if (rc) return rc;
+    }
+    // ---- poll and retire
+    if (running) {
+        HD_CUDA(ctx, cudaMemcpyAsync(s->h_st, E.st, Bp * sizeof(ColState), cudaMemcpyDeviceToHost, ctx->stream));
+        HD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        std::vector<int32_t> Kc(Bp, 0);
+        std::vector<int> fin;
+        for (int j = 0; j < s->slots; ++j) {
+            Req* r = s->slot_req[j];
+            if (r && !s->h_st[j].active && !s->h_st[j].fresh) {
+                Kc[j] = r->K;
+                fin.push_back(j);
+            }
+        }
+        if (!fin.empty()) {
+            int rc;
+            {
+                HD_PROF(ctx, "rank");
+                rc = hd_rank_impl(ctx, E.X, E.n, Bp, Bp, Kc.data(), s->Kmax, 0, s->d_idx, s->d_sc);
+            }
+            if (rc) return rc;
+            for (int j : fin) {
+                HD_CUDA(ctx, cudaMemcpyAsync(s->h_idx + (size_t)j * s->Kmax, s->d_idx + (size_t)j * s->Kmax,
+                                             (size_t)s->Kmax * 4, cudaMemcpyDeviceToHost, ctx->stream));
+                HD_CUDA(ctx, cudaMemcpyAsync(s->h_sc + (size_t)j * s->Kmax, s->d_sc + (size_t)j * s->Kmax,
+                                             (size_t)s->Kmax * 4, cudaMemcpyDeviceToHost, ctx->stream));
+            }
+            HD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+            const double t_done = now_s();
+            for (int j : fin) {
+                Req* r = s->slot_req[j];
+                const ColState& c = s->h_st[j];
+                r->iters = c.iters;
+                r->status = c.status;
+                r->relres = c.bb > 0 ? (float)std::sqrt(c.rr / c.bb) : 0.f;
+                r->out_idx.assign(s->h_idx + (size_t)j * s->Kmax, s->h_idx + (size_t)j * s->Kmax + r->K);
+                r->out_score.assign(s->h_sc + (size_t)j * s->Kmax, s->h_sc + (size_t)j * s->Kmax + r->K);
+                r->done_s = t_done;
+                r->done = true;
+                s->slot_req[j] = nullptr;
+            }
+        }
+    }
+    if (busy) {
+        int32_t b = (int32_t)s->queue.size();
+        for (int j = 0; j < s->slots; ++j) b += s->slot_req[j] != nullptr;
+        *busy = b;
+    }
+    return HD_OK;
+}
+
+int hd_serve_poll(hd_server* s, uint64_t ticket, int32_t* idx_out, float* score_out, hd_req_stats* st) {
+    if (!s) return HD_ERR_INVALID_ARG;
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return HD_ERR_NOT_FOUND;
+    Req* r = it->second;
+    if (!r->done) return HD_PENDING;
+    if (idx_out) std::copy(r->out_idx.begin(), r->out_idx.end(), idx_out);
+    if (score_out) std::copy(r->out_score.begin(), r->out_score.end(), score_out);
+    if (st) {
+        st->submit_s = r->submit_s;
+        st->admit_s = r->admit_s;
+        st->done_s = r->done_s;
+        st->iters = r->iters;
+        st->status = r->status;
+        st->relres = r->relres;
+        st->slot = r->slot;
+    }
+    s->reqs.erase(it);
+    delete r;
+    return HD_OK;
+}
+
+int hd_serve_close(hd_server* s) {
+    server_free(s);
+    return HD_OK;
+}
+
+}  // extern "C"

@@ -150,6 +150,9 @@ __global__ void __launch_bounds__(256) k_update(float* __restrict__ X, float* __
     const int col = blockIdx.y * S + 4 * g;
     const float a0 = (float)st[col].a, a1 = (float)st[col + 1].a, a2 = (float)st[col + 2].a, a3 = (float)st[col + 3].a;
     const float x0 = xs * a0, x1 = xs * a1, x2 = xs * a2, x3 = xs * a3;
+    // a column being (re)admitted starts from x = 0, r = 0 (its y is scattered next)
+    const bool f0 = st[col].fresh, f1 = st[col + 1].fresh, f2 = st[col + 2].fresh, f3 = st[col + 3].fresh;
+    const bool any_fresh = f0 | f1 | f2 | f3;
     KSum acc[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
     for (int64_t row = (int64_t)blockIdx.x * RPB + threadIdx.x / L; row < n; row += (int64_t)gridDim.x * RPB) {
         const int64_t o = row * ld + col;
@@ -157,6 +160,12 @@ __global__ void __launch_bounds__(256) k_update(float* __restrict__ X, float* __
         float4 x = ld4v(X + o), r = ld4v(R + o);
         x.x = fmaf(x0, p.x, x.x); x.y = fmaf(x1, p.y, x.y); x.z = fmaf(x2, p.z, x.z); x.w = fmaf(x3, p.w, x.w);
         r.x = fmaf(-a0, q.x, r.x); r.y = fmaf(-a1, q.y, r.y); r.z = fmaf(-a2, q.z, r.z); r.w = fmaf(-a3, q.w, r.w);
+        if (any_fresh) {
+            if (f0) x.x = r.x = 0.0f;
+            if (f1) x.y = r.y = 0.0f;
+            if (f2) x.z = r.z = 0.0f;
+            if (f3) x.w = r.w = 0.0f;
+        }
         st4(X + o, x);
         st4(R + o, r);
         ksum_add(acc[0], r.x * r.x);
@@ -181,119 +190,155 @@ __global__ void __launch_bounds__(256) k_direction(float* __restrict__ P, const 
         const int64_t o = row * ld + col;
         const float4 r = ld4v(R + o);
         float4 p = ld4v(P + o);
-        p.x = fmaf(b0, p.x, r.x); p.y = fmaf(b1, p.y, r.y); p.z = fmaf(b2, p.z, r.z); p.w = fmaf(b3, p.w, r.w);
+        p.x = b0 == 0.0f ? r.x : fmaf(b0, p.x, r.x);
+        p.y = b1 == 0.0f ? r.y : fmaf(b1, p.y, r.y);
+        p.z = b2 == 0.0f ? r.z : fmaf(b2, p.z, r.z);
+        p.w = b3 == 0.0f ? r.w : fmaf(b3, p.w, r.w);
         st4(P + o, p);
     }
 }
 
-// ---- per-column scalar kernels (one block) ----
-__device__ __forceinline__ double sum_part(const float2* part, int nblk, int ld, int j) {
+// ---- per-column scalar kernels: one block per column, fp64 reductions ----
+// Block-wide fp64 sum (all threads get the result).
+__device__ __forceinline__ double block_sum_f64(double v) {
+    __shared__ double sm[32];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) sm[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += sm[i];
+    return t;
+}
+
+// sum over blocks of column j's compensated partials
+__device__ __forceinline__ double col_sum(const float2* part, int nblk, int ld, int j) {
     double s = 0.0;
-    for (int b = 0; b < nblk; ++b) {
-        float2 v = part[(int64_t)b * ld + j];
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
+        const float2 v = part[(int64_t)b * ld + j];
         s += (double)v.x + (double)v.y;
     }
-    return s;
+    return block_sum_f64(s);
+}
+
+// sum_k coef_k C_kj^2
+__device__ __forceinline__ double col_lowrank(const double* C, const double* coef, int r, int ld, int j) {
+    double s = 0.0;
+    if (C)
+        for (int k = threadIdx.x; k < r; k += blockDim.x) {
+            const double c = C[(int64_t)k * ld + j];
+            s += coef[k] * c * c;
+        }
+    return block_sum_f64(s);
 }
 
 // Setup: bb = ||b||^2; rho = bb (+ sum D C^2 for PCG); activity and 0-iteration convergence.
 __global__ void k_fin_setup(const float2* part, int nblk, int32_t Bp, int32_t B, const float* tol, ColState* st,
                             const double* C, const double* coef, int32_t r, int* num_active) {
-    __shared__ int cnt;
-    if (threadIdx.x == 0) cnt = 0;
-    __syncthreads();
-    for (int j = threadIdx.x; j < Bp; j += blockDim.x) {
-        ColState s;
-        double bb = sum_part(part, nblk, Bp, j);
-        s.bb = bb;
-        s.rr = bb;
-        double rho = bb;
-        if (C)
-            for (int k = 0; k < r; ++k) rho += coef[k] * C[(int64_t)k * Bp + j] * C[(int64_t)k * Bp + j];
-        s.rho = rho;
-        double t = j < B ? (double)tol[j] : 0.0;
-        s.tol2 = t * t * bb;
-        s.sigma = 0.0;
-        s.a = 0.0;
-        s.beta = 0.0;
-        s.iters = 0;
-        s.pad = 0;
-        if (j >= B || bb == 0.0) {
-            s.active = 0;
-            s.status = HD_COL_EMPTY;
-        } else if (bb <= s.tol2) {
-            s.active = 0;
-            s.status = HD_COL_CONVERGED;
-        } else {
-            s.active = 1;
-            s.status = HD_COL_MAX_ITER;
-            atomicAdd(&cnt, 1);
-        }
-        st[j] = s;
+    const int j = blockIdx.x;
+    const double bb = col_sum(part, nblk, Bp, j);
+    const double lrt = col_lowrank(C, coef, r, Bp, j);
+    if (threadIdx.x != 0) return;
+    ColState s;
+    s.bb = bb;
+    s.rr = bb;
+    s.rho = bb + lrt;
+    const double t = j < B ? (double)tol[j] : 0.0;
+    s.tol2 = t * t * bb;
+    s.sigma = 0.0;
+    s.a = 0.0;
+    s.beta = 0.0;
+    s.iters = 0;
+    s.fresh = 0;
+    if (j >= B || bb == 0.0) {
+        s.active = 0;
+        s.status = HD_COL_EMPTY;
+    } else if (bb <= s.tol2) {
+        s.active = 0;
+        s.status = HD_COL_CONVERGED;
+    } else {
+        s.active = 1;
+        s.status = HD_COL_MAX_ITER;
+        atomicAdd(num_active, 1);
     }
-    __syncthreads();
-    if (threadIdx.x == 0) *num_active = cnt;
+    st[j] = s;
 }
 
 // a = rho / sigma with sigma = SpMM partials (+ sum_k coef_k C_k^2).
 __global__ void k_fin_sigma(const float2* part, int nblk, int32_t Bp, ColState* st, const double* C,
                             const double* coef, int32_t r) {
-    for (int j = threadIdx.x; j < Bp; j += blockDim.x) {
-        ColState& s = st[j];
-        if (!s.active) {
-            s.a = 0.0;
-            continue;
-        }
-        double sig = sum_part(part, nblk, Bp, j);
-        if (C)
-            for (int k = 0; k < r; ++k) sig += coef[k] * C[(int64_t)k * Bp + j] * C[(int64_t)k * Bp + j];
-        s.sigma = sig;
-        if (!(sig > 0.0) || !isfinite(sig)) {
-            s.active = 0;
-            s.status = HD_COL_BREAKDOWN;
-            s.a = 0.0;
-        } else {
-            s.a = s.rho / sig;
-        }
+    const int j = blockIdx.x;
+    ColState& s = st[j];
+    if (!s.active) {
+        if (threadIdx.x == 0) s.a = 0.0;
+        return;
+    }
+    const double sig = col_sum(part, nblk, Bp, j) + col_lowrank(C, coef, r, Bp, j);
+    if (threadIdx.x != 0) return;
+    s.sigma = sig;
+    if (!(sig > 0.0) || !isfinite(sig)) {
+        s.active = 0;
+        s.status = HD_COL_BREAKDOWN;
+        s.a = 0.0;
+    } else {
+        s.a = s.rho / sig;
     }
 }
 
 // After the update: rr, convergence, beta.  With C: PCG rho' = rr + sum_k coef_k C_k^2.
+// num_active must be zero before the launch.
 __global__ void k_fin_rr(const float2* part, int nblk, int32_t Bp, ColState* st, int32_t max_iter,
                          const double* C, const double* coef, int32_t r, int* num_active) {
-    __shared__ int cnt;
-    if (threadIdx.x == 0) cnt = 0;
-    __syncthreads();
-    for (int j = threadIdx.x; j < Bp; j += blockDim.x) {
-        ColState& s = st[j];
-        if (!s.active) {
-            s.beta = 0.0;
-            continue;
-        }
-        double rr = sum_part(part, nblk, Bp, j);
-        double rho = rr;
-        if (C)
-            for (int k = 0; k < r; ++k) rho += coef[k] * C[(int64_t)k * Bp + j] * C[(int64_t)k * Bp + j];
-        s.iters += 1;
-        s.rr = rr;
-        s.beta = rho / s.rho;
-        s.rho = rho;
-        if (!isfinite(rr)) {
+    const int j = blockIdx.x;
+    ColState& s = st[j];
+    const bool fresh = s.fresh, active = s.active;
+    if (!fresh && !active) {
+        if (threadIdx.x == 0) s.beta = 0.0;
+        return;
+    }
+    const double rr = fresh ? 0.0 : col_sum(part, nblk, Bp, j);
+    const double lrt = col_lowrank(C, coef, r, Bp, j);
+    if (threadIdx.x != 0) return;
+    if (fresh) {
+        // (re)admitted column: r0 = y with ||y||^2 = bb set at admission
+        s.fresh = 0;
+        s.rr = s.bb;
+        s.rho = s.bb + lrt;
+        s.beta = 0.0;
+        s.a = 0.0;
+        s.iters = 0;
+        if (s.bb == 0.0) {
             s.active = 0;
-            s.status = HD_COL_BREAKDOWN;
-            s.beta = 0.0;
-        } else if (rr <= s.tol2) {
+            s.status = HD_COL_EMPTY;
+        } else if (s.bb <= s.tol2) {
             s.active = 0;
             s.status = HD_COL_CONVERGED;
-        } else if (s.iters >= max_iter) {
-            s.active = 0;
-            s.status = HD_COL_MAX_ITER;
         } else {
-            atomicAdd(&cnt, 1);
+            s.active = 1;
+            s.status = HD_COL_MAX_ITER;
+            atomicAdd(num_active, 1);
         }
+        return;
     }
-    __syncthreads();
-    if (threadIdx.x == 0) *num_active = cnt;
+    const double rho = rr + lrt;
+    s.iters += 1;
+    s.rr = rr;
+    s.beta = rho / s.rho;
+    s.rho = rho;
+    if (!isfinite(rr)) {
+        s.active = 0;
+        s.status = HD_COL_BREAKDOWN;
+        s.beta = 0.0;
+    } else if (rr <= s.tol2) {
+        s.active = 0;
+        s.status = HD_COL_CONVERGED;
+    } else if (s.iters >= max_iter) {
+        s.active = 0;
+        s.status = HD_COL_MAX_ITER;
+    } else {
+        atomicAdd(num_active, 1);
+    }
 }
 
 __global__ void k_outputs(const ColState* st, int32_t B, int32_t* iters, float* relres, int32_t* status) {
@@ -355,13 +400,23 @@ __global__ void __launch_bounds__(256) k_lr_reduce_simt(const T* __restrict__ U,
 }
 
 // C = sum over chunks (fp64); H = coef o C (fp32 and bf16 hi/lo transposed).
-__global__ void k_lr_finish(const float* __restrict__ part, int nchunk, int rpad, int32_t Bp, const double* coef,
-                            double* C, float* H, __nv_bfloat16* Hhi, __nv_bfloat16* Hlo) {
-    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e >= (int64_t)rpad * Bp) return;
-    const int k = (int)(e / Bp), j = (int)(e % Bp);
+// Block: 32 consecutive entries x 8 warps splitting the chunks.
+__global__ void __launch_bounds__(256) k_lr_finish(const float* __restrict__ part, int nchunk, int rpad, int32_t Bp,
+                                                   const double* coef, double* C, float* H, __nv_bfloat16* Hhi,
+                                                   __nv_bfloat16* Hlo) {
+    __shared__ double sm[8][33];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t e = (int64_t)blockIdx.x * 32 + lane;
+    const int64_t tot = (int64_t)rpad * Bp;
     double s = 0.0;
-    for (int c = 0; c < nchunk; ++c) s += (double)part[((int64_t)c * rpad + k) * Bp + j];
+    if (e < tot)
+        for (int c = w; c < nchunk; c += 8) s += (double)part[(int64_t)c * tot + e];
+    sm[w][lane] = s;
+    __syncthreads();
+    if (w != 0 || e >= tot) return;
+    s = 0.0;
+    for (int i = 0; i < 8; ++i) s += sm[i][lane];
+    const int k = (int)(e / Bp), j = (int)(e % Bp);
     C[e] = s;
     const double h = coef[k] * s;
     H[e] = (float)h;
@@ -419,16 +474,16 @@ __global__ void __launch_bounds__(256) k_lr_expand_simt(const T* __restrict__ U,
             v.x += acc.x; v.y += acc.y; v.z += acc.z; v.w += acc.w;
         } else {
             const float4 rr = ld4v(Rv + o), pp = ld4v(Pv + o);
-            v.x = rr.x + acc.x + b0 * pp.x;
-            v.y = rr.y + acc.y + b1 * pp.y;
-            v.z = rr.z + acc.z + b2 * pp.z;
-            v.w = rr.w + acc.w + b3 * pp.w;
+            v.x = rr.x + acc.x + (b0 == 0.0f ? 0.0f : b0 * pp.x);
+            v.y = rr.y + acc.y + (b1 == 0.0f ? 0.0f : b1 * pp.y);
+            v.z = rr.z + acc.z + (b2 == 0.0f ? 0.0f : b2 * pp.z);
+            v.w = rr.w + acc.w + (b3 == 0.0f ? 0.0f : b3 * pp.w);
         }
         st4(out + o, v);
     }
 }
 
-static int simt_nchunk(hd_ctx* ctx, int64_t n, int rpad, int Bp) {
+int simt_nchunk(hd_ctx* ctx, int64_t n, int rpad, int Bp) {
     int blocks_per_chunk = (rpad / 64) * ceil_div(Bp, 16);
     int nc = ceil_div(4 * ctx->num_sms, blocks_per_chunk);
     int64_t maxc = std::max<int64_t>(1, n / 64);
@@ -457,7 +512,7 @@ int lr_reduce(hd_ctx* ctx, const LowRank& lr, const float* V, int64_t n, int32_t
 int lr_finish(hd_ctx* ctx, const LowRank& lr, int32_t Bp, const double* coef) {
     HD_PROF(ctx, "scalar");
     int64_t tot = (int64_t)lr.rpad * Bp;
-    k_lr_finish<<<ceil_div(tot, 256), 256, 0, ctx->stream>>>(lr.part, lr.nchunk, lr.rpad, Bp, coef, lr.C,
+    k_lr_finish<<<ceil_div(tot, 32), 256, 0, ctx->stream>>>(lr.part, lr.nchunk, lr.rpad, Bp, coef, lr.C,
                                                              lr.H, lr.Hhi, lr.Hlo);
     HD_CHECK_LAUNCH(ctx);
     return HD_OK;
@@ -492,11 +547,7 @@ int lr_expand(hd_ctx* ctx, const LowRank& lr, int op, float* out, const float* R
 }
 
 // ------------------------------------------------------------------ launch helpers
-struct VecLaunch {
-    int S;       // columns per row group slab
-    int nblk;    // grid.x
-    int slabs;   // grid.y
-};
+
 
 static int pick_slab(int32_t Bp) {
     static int forced = -1;
@@ -510,7 +561,7 @@ static int pick_slab(int32_t Bp) {
     return 4;
 }
 
-static VecLaunch vec_launch(hd_ctx* ctx, int64_t n, int32_t Bp) {
+VecLaunch vec_launch(hd_ctx* ctx, int64_t n, int32_t Bp) {
     VecLaunch v;
     v.S = pick_slab(Bp);
     int rpb = 256 / (v.S / 4);
@@ -541,21 +592,7 @@ int hd_spmm_apply(hd_ctx* ctx, const hd_graph* g, const float* P, float* Q, int3
 }
 
 // ------------------------------------------------------------------ the solve
-struct Solve {
-    hd_ctx* ctx;
-    const hd_graph* g;
-    int64_t n;
-    int32_t B, Bp;
-    VecLaunch vl;
-    float *R, *P, *Q, *X;
-    float2* part;
-    ColState* st;
-    int* num_active;
-    int* err;
-    LowRank lr;
-    bool has_lr = false;
-    double *gcoef, *hcoef, *opcoef, *dcoef, *ones;
-};
+
 
 #define LAUNCH_VEC(kernel, ...)                                                                 \
     do {                                                                                        \
@@ -565,6 +602,62 @@ struct Solve {
         HD_DISPATCH_S(S_.vl.S, (kernel<SS><<<grid_, 256, 0, S_.ctx->stream>>>(__VA_ARGS__)));   \
         HD_CHECK_LAUNCH(S_.ctx);                                                                \
     } while (0)
+
+
+// One CG iteration of every column (Eq. 20 operator, CG update, direction).
+// `after_update`, if given, runs right after the X/R update (the serving loop
+// scatters newly admitted observations there).
+int engine_iteration(Engine& S_, int (*after_update)(void*), void* arg) {
+    hd_ctx* ctx = S_.ctx;
+    const hd_graph* g = S_.g;
+    const int64_t n = S_.n;
+    const int32_t Bp = S_.Bp;
+    const int r = S_.r;
+    const bool lr_on = S_.has_lr;
+    const int eff_mode = S_.eff_mode;
+    const float c1 = S_.c1, c2 = S_.c2, xs = S_.xs;
+    const int32_t max_iter = S_.max_iter;
+    const double* Cd = lr_on ? S_.lr.C : nullptr;
+    int rc;
+    if (eff_mode == HD_MODE_PCG) {
+        LAUNCH_VEC(k_spmm, g->row_ptr, g->col, g->val, S_.P, S_.Q, n, Bp, c1, c2, S_.part);
+        { HD_PROF(ctx, "scalar");
+        k_fin_sigma<<<Bp, 128, 0, ctx->stream>>>(S_.part, S_.vl.nblk, Bp, S_.st, nullptr, nullptr, 0); }
+        HD_CHECK_LAUNCH(ctx);
+        LAUNCH_VEC(k_update, S_.X, S_.R, S_.P, S_.Q, n, Bp, S_.st, xs, S_.part);
+    if (after_update && (rc = after_update(arg))) return rc;
+        if ((rc = lr_reduce(ctx, S_.lr, S_.R, n, Bp))) return rc;
+        if ((rc = lr_finish(ctx, S_.lr, Bp, S_.dcoef))) return rc;
+        { HD_PROF(ctx, "scalar");
+        HD_CUDA(ctx, cudaMemsetAsync(S_.num_active, 0, sizeof(int), ctx->stream));
+        k_fin_rr<<<Bp, 128, 0, ctx->stream>>>(S_.part, S_.vl.nblk, Bp, S_.st, max_iter, Cd, S_.dcoef, r,
+                                             S_.num_active); }
+        HD_CHECK_LAUNCH(ctx);
+        if ((rc = lr_expand(ctx, S_.lr, EXP_DIRECTION, S_.P, S_.R, S_.P, n, Bp, S_.st))) return rc;
+    } else {
+        LAUNCH_VEC(k_spmm, g->row_ptr, g->col, g->val, S_.P, S_.Q, n, Bp, c1, c2, S_.part);
+        if (lr_on) {
+            if ((rc = lr_expand(ctx, S_.lr, EXP_ADD_Q, S_.Q, nullptr, nullptr, n, Bp, S_.st))) return rc;
+        }
+        { HD_PROF(ctx, "scalar");
+        k_fin_sigma<<<Bp, 128, 0, ctx->stream>>>(S_.part, S_.vl.nblk, Bp, S_.st, Cd,
+                                                lr_on ? S_.opcoef : nullptr, r); }
+        HD_CHECK_LAUNCH(ctx);
+        LAUNCH_VEC(k_update, S_.X, S_.R, S_.P, S_.Q, n, Bp, S_.st, xs, S_.part);
+    if (after_update && (rc = after_update(arg))) return rc;
+        { HD_PROF(ctx, "scalar");
+        HD_CUDA(ctx, cudaMemsetAsync(S_.num_active, 0, sizeof(int), ctx->stream));
+        k_fin_rr<<<Bp, 128, 0, ctx->stream>>>(S_.part, S_.vl.nblk, Bp, S_.st, max_iter, nullptr, nullptr, 0,
+                                             S_.num_active); }
+        HD_CHECK_LAUNCH(ctx);
+        LAUNCH_VEC(k_direction, S_.P, S_.R, n, Bp, S_.st);
+        if (lr_on) {
+            if ((rc = lr_reduce(ctx, S_.lr, S_.P, n, Bp))) return rc;
+            if ((rc = lr_finish(ctx, S_.lr, Bp, S_.opcoef))) return rc;
+        }
+    }
+    return HD_OK;
+}
 
 extern "C" int hd_query_batch(hd_ctx* ctx, const hd_graph* g, const hd_eig* eig, int mode, int32_t B,
                               const int32_t* y_ptr, const int32_t* y_idx, const float* y_val, float alpha,
@@ -579,7 +672,7 @@ extern "C" int hd_query_batch(hd_ctx* ctx, const hd_graph* g, const hd_eig* eig,
     if (eig && eig->n != g->n) return hd_fail(ctx, HD_ERR_INVALID_ARG, "eigenpairs for n=%lld, graph n=%lld",
                                               (long long)eig->n, (long long)g->n);
     HD_CUDA(ctx, cudaSetDevice(ctx->device));
-    Solve S_;
+    Engine S_;
     S_.ctx = ctx;
     S_.g = g;
     S_.n = g->n;
@@ -590,6 +683,7 @@ extern "C" int hd_query_batch(hd_ctx* ctx, const hd_graph* g, const hd_eig* eig,
     const int32_t Bp = S_.Bp;
     const bool lr_on = eig && eig->r > 0;
     S_.has_lr = lr_on;
+    S_.lr = LowRank{};
     const int r = lr_on ? eig->r : 0;
     const int rpad = lr_on ? (r + 63) / 64 * 64 : 0;
     const int Bp16 = (Bp + 15) / 16 * 16;
@@ -696,7 +790,8 @@ extern "C" int hd_query_batch(hd_ctx* ctx, const hd_graph* g, const hd_eig* eig,
     const double* Cd = lr_on ? S_.lr.C : nullptr;
     if (eff_mode == HD_MODE_PAPER) {
         LAUNCH_VEC(k_colsq, S_.R, n, Bp, S_.part);
-        k_fin_setup<<<1, 256, 0, ctx->stream>>>(S_.part, S_.vl.nblk, Bp, B, (const float*)tl, S_.st, nullptr, nullptr,
+        HD_CUDA(ctx, cudaMemsetAsync(S_.num_active, 0, sizeof(int), ctx->stream));
+        k_fin_setup<<<Bp, 128, 0, ctx->stream>>>(S_.part, S_.vl.nblk, Bp, B, (const float*)tl, S_.st, nullptr, nullptr,
                                                 0, S_.num_active);
         HD_CHECK_LAUNCH(ctx);
         HD_CUDA(ctx, cudaMemcpyAsync(S_.P, S_.R, vec, cudaMemcpyDeviceToDevice, ctx->stream));
@@ -714,7 +809,8 @@ extern "C" int hd_query_batch(hd_ctx* ctx, const hd_graph* g, const hd_eig* eig,
         if ((rc = lr_finish(ctx, S_.lr, Bp, S_.ones))) return rc;
         if ((rc = lr_expand(ctx, S_.lr, EXP_SUB_R, S_.R, nullptr, nullptr, n, Bp, S_.st))) return rc;
         LAUNCH_VEC(k_colsq, S_.R, n, Bp, S_.part);
-        k_fin_setup<<<1, 256, 0, ctx->stream>>>(S_.part, S_.vl.nblk, Bp, B, (const float*)tl, S_.st, nullptr, nullptr,
+        HD_CUDA(ctx, cudaMemsetAsync(S_.num_active, 0, sizeof(int), ctx->stream));
+        k_fin_setup<<<Bp, 128, 0, ctx->stream>>>(S_.part, S_.vl.nblk, Bp, B, (const float*)tl, S_.st, nullptr, nullptr,
                                                 0, S_.num_active);
         HD_CHECK_LAUNCH(ctx);
         HD_CUDA(ctx, cudaMemcpyAsync(S_.P, S_.R, vec, cudaMemcpyDeviceToDevice, ctx->stream));
@@ -724,7 +820,8 @@ extern "C" int hd_query_batch(hd_ctx* ctx, const hd_graph* g, const hd_eig* eig,
         LAUNCH_VEC(k_colsq, S_.R, n, Bp, S_.part);
         if ((rc = lr_reduce(ctx, S_.lr, S_.R, n, Bp))) return rc;
         if ((rc = lr_finish(ctx, S_.lr, Bp, S_.dcoef))) return rc;
-        k_fin_setup<<<1, 256, 0, ctx->stream>>>(S_.part, S_.vl.nblk, Bp, B, (const float*)tl, S_.st, Cd, S_.dcoef, r,
+        HD_CUDA(ctx, cudaMemsetAsync(S_.num_active, 0, sizeof(int), ctx->stream));
+        k_fin_setup<<<Bp, 128, 0, ctx->stream>>>(S_.part, S_.vl.nblk, Bp, B, (const float*)tl, S_.st, Cd, S_.dcoef, r,
                                                 S_.num_active);
         HD_CHECK_LAUNCH(ctx);
         HD_CUDA(ctx, cudaMemsetAsync(S_.P, 0, vec, ctx->stream));
@@ -732,6 +829,12 @@ extern "C" int hd_query_batch(hd_ctx* ctx, const hd_graph* g, const hd_eig* eig,
     }
 
     // ---------------- iterations
+    S_.eff_mode = eff_mode;
+    S_.c1 = c1;
+    S_.c2 = c2;
+    S_.xs = xs;
+    S_.r = r;
+    S_.max_iter = max_iter;
     const int poll_every = 4;
     int it = 0;
     HD_CUDA(ctx, cudaMemcpyAsync(ctx->h_poll, S_.num_active, 2 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
@@ -740,39 +843,7 @@ extern "C" int hd_query_batch(hd_ctx* ctx, const hd_graph* g, const hd_eig* eig,
     int active = ctx->h_poll[0];
     while (active > 0 && it < max_iter) {
         for (int t = 0; t < poll_every && it < max_iter; ++t, ++it) {
-            if (eff_mode == HD_MODE_PCG) {
-                LAUNCH_VEC(k_spmm, g->row_ptr, g->col, g->val, S_.P, S_.Q, n, Bp, c1, c2, S_.part);
-                { HD_PROF(ctx, "scalar");
-                k_fin_sigma<<<1, 256, 0, ctx->stream>>>(S_.part, S_.vl.nblk, Bp, S_.st, nullptr, nullptr, 0); }
-                HD_CHECK_LAUNCH(ctx);
-                LAUNCH_VEC(k_update, S_.X, S_.R, S_.P, S_.Q, n, Bp, S_.st, xs, S_.part);
-                if ((rc = lr_reduce(ctx, S_.lr, S_.R, n, Bp))) return rc;
-                if ((rc = lr_finish(ctx, S_.lr, Bp, S_.dcoef))) return rc;
-                { HD_PROF(ctx, "scalar");
-                k_fin_rr<<<1, 256, 0, ctx->stream>>>(S_.part, S_.vl.nblk, Bp, S_.st, max_iter, Cd, S_.dcoef, r,
-                                                     S_.num_active); }
-                HD_CHECK_LAUNCH(ctx);
-                if ((rc = lr_expand(ctx, S_.lr, EXP_DIRECTION, S_.P, S_.R, S_.P, n, Bp, S_.st))) return rc;
-            } else {
-                LAUNCH_VEC(k_spmm, g->row_ptr, g->col, g->val, S_.P, S_.Q, n, Bp, c1, c2, S_.part);
-                if (lr_on) {
-                    if ((rc = lr_expand(ctx, S_.lr, EXP_ADD_Q, S_.Q, nullptr, nullptr, n, Bp, S_.st))) return rc;
-                }
-                { HD_PROF(ctx, "scalar");
-                k_fin_sigma<<<1, 256, 0, ctx->stream>>>(S_.part, S_.vl.nblk, Bp, S_.st, Cd,
-                                                        lr_on ? S_.opcoef : nullptr, r); }
-                HD_CHECK_LAUNCH(ctx);
-                LAUNCH_VEC(k_update, S_.X, S_.R, S_.P, S_.Q, n, Bp, S_.st, xs, S_.part);
-                { HD_PROF(ctx, "scalar");
-                k_fin_rr<<<1, 256, 0, ctx->stream>>>(S_.part, S_.vl.nblk, Bp, S_.st, max_iter, nullptr, nullptr, 0,
-                                                     S_.num_active); }
-                HD_CHECK_LAUNCH(ctx);
-                LAUNCH_VEC(k_direction, S_.P, S_.R, n, Bp, S_.st);
-                if (lr_on) {
-                    if ((rc = lr_reduce(ctx, S_.lr, S_.P, n, Bp))) return rc;
-                    if ((rc = lr_finish(ctx, S_.lr, Bp, S_.opcoef))) return rc;
-                }
-            }
+            if ((rc = engine_iteration(S_, nullptr, nullptr))) return rc;
         }
         HD_CUDA(ctx, cudaMemcpyAsync(ctx->h_poll, S_.num_active, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
         HD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));

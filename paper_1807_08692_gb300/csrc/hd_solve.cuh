@@ -14,7 +14,8 @@ struct ColState {
     int active;
     int iters;
     int status;
-    int pad;
+    int fresh;      // 1: the column was just (re)admitted; the update resets it and
+                    // the next scalar step starts its iteration from r0 = y (bb given)
 };
 
 // Low-rank product helpers (storage-specific implementations).
@@ -48,3 +49,34 @@ int lr_tc_reduce(hd_ctx* ctx, const LowRank& lr, const float* V, int64_t n, int3
 int lr_tc_expand(hd_ctx* ctx, const LowRank& lr, int op, float* out, const float* Rv, const float* Pv, int64_t n,
                  int32_t Bp, const ColState* st);
 int lr_tc_nchunk(hd_ctx* ctx, int64_t n);
+
+// ------------------------------------------------------------------ iteration engine
+struct VecLaunch {
+    int S;       // columns per row-group slab
+    int nblk;    // grid.x
+    int slabs;   // grid.y
+};
+
+struct Engine {
+    hd_ctx* ctx = nullptr;
+    const hd_graph* g = nullptr;
+    int64_t n = 0;
+    int32_t B = 0, Bp = 0;
+    VecLaunch vl{};
+    float *R = nullptr, *P = nullptr, *Q = nullptr, *X = nullptr;
+    float2* part = nullptr;
+    ColState* st = nullptr;
+    int* num_active = nullptr;
+    int* err = nullptr;
+    LowRank lr{};
+    bool has_lr = false;
+    double *gcoef = nullptr, *hcoef = nullptr, *opcoef = nullptr, *dcoef = nullptr, *ones = nullptr;
+    int eff_mode = HD_MODE_PAPER;
+    float c1 = 0.f, c2 = 0.f, xs = 1.f;
+    int r = 0;
+    int32_t max_iter = 0;
+};
+
+VecLaunch vec_launch(hd_ctx* ctx, int64_t n, int32_t Bp);
+int simt_nchunk(hd_ctx* ctx, int64_t n, int rpad, int Bp);
+int engine_iteration(Engine& E, int (*after_update)(void*), void* arg);

@@ -58,6 +58,12 @@ _SIGS = {
     "hd_query_batch": (C.c_int, [vp, vp, vp, C.c_int, i32, vp, vp, vp, f32, vp, i32, vp, i32, vp, vp, vp]),
     "hd_rank": (C.c_int, [vp, vp, i64, i32, i32, vp, i32, i32, vp, vp]),
     "hd_eig_project": (C.c_int, [vp, vp, vp, i32, vp]),
+    "hd_serve_open": (C.c_int, [vp, vp, vp, C.c_int, f32, i32, C.c_size_t, i32, i32, C.POINTER(vp)]),
+    "hd_serve_slots": (C.c_int, [vp]),
+    "hd_serve_submit": (C.c_int, [vp, i32, vp, vp, f32, i32, C.POINTER(u64)]),
+    "hd_serve_step": (C.c_int, [vp, i32, C.POINTER(i32)]),
+    "hd_serve_poll": (C.c_int, [vp, u64, vp, vp, vp]),
+    "hd_serve_close": (C.c_int, [vp]),
     "hd_eig_expand": (C.c_int, [vp, vp, vp, i32, vp]),
 }
 
@@ -350,3 +356,58 @@ def rank(ctx: Context, X, K, Kmax: int | None = None, pool: int = 0, n: int | No
         score = np.empty((B, Kmax), np.float32)
     ctx.check(lib().hd_rank(ctx.handle, _ptr(X), n, B, ldx, _ptr(K), Kmax, pool, _ptr(idx), _ptr(score)), "hd_rank")
     return idx, score
+
+
+class ReqStats(C.Structure):
+    _fields_ = [("submit_s", C.c_double), ("admit_s", C.c_double), ("done_s", C.c_double),
+                ("iters", C.c_int32), ("status", C.c_int32), ("relres", C.c_float), ("slot", C.c_int32)]
+
+
+class Server:
+    """Continuous-batching server (hd_serve_*): submit requests, step, poll."""
+
+    def __init__(self, ctx: Context, g: Graph, eig=None, mode="pcg", alpha: float = 0.99, max_slots: int = 64,
+                 mem_budget: int = 0, max_iter: int = 1000, Kmax: int = 1000):
+        self.ctx = ctx
+        self.Kmax = Kmax
+        self._h = vp()
+        m = MODES[mode] if isinstance(mode, str) else mode
+        ctx.check(lib().hd_serve_open(ctx.handle, g.handle, eig.handle if eig is not None else None, m, alpha,
+                                      max_slots, mem_budget, max_iter, Kmax, C.byref(self._h)), "hd_serve_open")
+        self.slots = int(lib().hd_serve_slots(self._h))
+
+    def submit(self, idx, val, tol: float, K: int) -> int:
+        idx = np.ascontiguousarray(idx, np.int32)
+        val = np.ascontiguousarray(val, np.float32)
+        t = u64()
+        self.ctx.check(lib().hd_serve_submit(self._h, idx.size, _ptr(idx), _ptr(val), tol, K, C.byref(t)),
+                       "hd_serve_submit")
+        return t.value
+
+    def step(self, iters: int = 1) -> int:
+        busy = i32()
+        self.ctx.check(lib().hd_serve_step(self._h, iters, C.byref(busy)), "hd_serve_step")
+        return busy.value
+
+    def poll(self, ticket: int, K: int):
+        """None while pending, else (ids, scores, stats dict)."""
+        ids = np.empty(max(K, 1), np.int32)
+        sc = np.empty(max(K, 1), np.float32)
+        st = ReqStats()
+        rc = lib().hd_serve_poll(self._h, ticket, _ptr(ids), _ptr(sc), C.byref(st))
+        if rc == PENDING:
+            return None
+        self.ctx.check(rc, "hd_serve_poll")
+        stats = {f: getattr(st, f) for f, _ in ReqStats._fields_}
+        return ids[:K], sc[:K], stats
+
+    def close(self):
+        if self._h:
+            lib().hd_serve_close(self._h)
+            self._h = vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

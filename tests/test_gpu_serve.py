@@ -1,0 +1,118 @@
+"""Continuous-batching server: each request's result is the same alone and in
+a mix (bitwise), rankings match the fp64 oracle, per-request tolerance and K
+are honoured, and admission respects the memory budget."""
+import numpy as np
+import pytest
+
+import synth
+from _helpers import csr_of
+from oracle import diffusion as D
+from oracle import observe
+from oracle import rank as ORank
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def served(gpu_ctx, cfg1_data):
+    import paper_1807_08692_gb300 as hd
+    c = cfg1_data["cfg"]
+    g = hd.graph_from_csr(gpu_ctx, *csr_of(cfg1_data["A"]))
+    r = 50
+    eig = hd.eig_from_host(gpu_ctx, g, cfg1_data["lam"][:r], cfg1_data["U"][:, :r], "bf16")
+    # 40 extra observation vectors from fresh queries of the same mixture
+    Qx = synth.queries(c.seed + 77, 40, c.d, c.ncl, c.kappa_lo, c.kappa_hi)
+    yp, yi, yv = observe.observe(cfg1_data["X"], Qx, c.k_y, c.gamma)
+    reqs = [(yi[yp[j]:yp[j + 1]], yv[yp[j]:yp[j + 1]]) for j in range(40)]
+    return g, eig, reqs
+
+
+def _run(server, items, iters=2, max_steps=2000):
+    """items: list of (step_to_submit, idx, val, tol, K); returns results by position."""
+    tickets = {}
+    out = {}
+    waiting = list(range(len(items)))
+    step = 0
+    while (waiting or len(out) < len(items)) and step < max_steps:
+        for pos in [p for p in waiting if items[p][0] <= step]:
+            at, idx, val, tol, K = items[pos]
+            tickets[pos] = (server.submit(idx, val, tol, K), K)
+            waiting.remove(pos)
+        server.step(iters)
+        for pos, (t, K) in list(tickets.items()):
+            if pos not in out:
+                res = server.poll(t, K)
+                if res is not None:
+                    out[pos] = res
+        step += 1
+    assert len(out) == len(items)
+    return [out[i] for i in range(len(items))]
+
+
+def test_alone_equals_mix_bitwise(gpu_ctx, served):
+    import paper_1807_08692_gb300 as hd
+    g, eig, reqs = served
+    q_idx, q_val = reqs[0]
+    srv = hd.Server(gpu_ctx, g, eig, "pcg", 0.99, max_slots=12, max_iter=500, Kmax=200)
+    alone = _run(srv, [(0, q_idx, q_val, 1e-6, 100)])[0]
+    mix_items = [(s // 3, i, v, [1e-2, 1e-4, 1e-6][s % 3], [10, 100, 200][s % 3]) for s, (i, v) in enumerate(reqs[1:])]
+    mix_items.insert(17, (4, q_idx, q_val, 1e-6, 100))
+    mixed = _run(srv, mix_items)
+    m = mixed[17]
+    assert np.array_equal(alone[0], m[0])
+    assert np.array_equal(alone[1].view(np.uint32), m[1].view(np.uint32))
+    assert alone[2]["iters"] == m[2]["iters"] and alone[2]["status"] == 0
+    # columns ran in several slots while others were admitted and retired
+    slots = {r[2]["slot"] for r in mixed}
+    assert len(slots) > 4
+    srv.close()
+
+
+def test_served_rankings_match_oracle(gpu_ctx, cfg1_data, served):
+    import paper_1807_08692_gb300 as hd
+    g, eig, reqs = served
+    W = cfg1_data["W"]
+    n = cfg1_data["cfg"].n
+    srv = hd.Server(gpu_ctx, g, eig, "pcg", 0.99, max_slots=8, max_iter=500, Kmax=100)
+    items = [(s // 4, i, v, 1e-6, 100) for s, (i, v) in enumerate(reqs[:16])]
+    res = _run(srv, items)
+    for (at, i, v, tol, K), (ids, sc, st) in zip(items, res):
+        Y = np.zeros((n, 1))
+        np.add.at(Y[:, 0], i, v.astype(np.float64))
+        x = D.closed_form(W, Y, 0.99)[:, 0]
+        ref, _ = ORank.topk(x, K)
+        assert ORank.ranks_match(ids, ref, x, 1e-5 * x.max())
+        assert st["status"] == 0 and st["relres"] <= 1e-6 * 1.01
+        assert st["done_s"] >= st["admit_s"] >= st["submit_s"]
+    srv.close()
+
+
+def test_tolerance_and_k_per_request(gpu_ctx, served):
+    import paper_1807_08692_gb300 as hd
+    g, eig, reqs = served
+    srv = hd.Server(gpu_ctx, g, None, "paper", 0.99, max_slots=4, max_iter=800, Kmax=1000)
+    i, v = reqs[3]
+    loose, tight = _run(srv, [(0, i, v, 1e-2, 10), (0, i, v, 1e-6, 1000)])
+    assert loose[2]["iters"] < tight[2]["iters"]
+    assert len(loose[0]) == 10 and len(tight[0]) == 1000
+    assert loose[2]["relres"] <= 1e-2 and tight[2]["relres"] <= 1e-6 * 1.01
+    srv.close()
+
+
+def test_admission_by_memory_and_errors(gpu_ctx, served, cfg1_data):
+    import paper_1807_08692_gb300 as hd
+    g, eig, reqs = served
+    n = cfg1_data["cfg"].n
+    per_slot = 4 * n * 4 + 100 * 8
+    srv = hd.Server(gpu_ctx, g, None, "paper", 0.99, max_slots=64, mem_budget=3 * per_slot + 7, Kmax=100)
+    assert srv.slots == 3
+    with pytest.raises(hd.HDError):
+        srv.submit(np.array([n], np.int32), np.array([1.0], np.float32), 1e-6, 10)
+    with pytest.raises(hd.HDError):
+        srv.submit(np.array([0], np.int32), np.array([1.0], np.float32), 1e-6, 101)
+    items = [(0, i, v, 1e-4, 10) for i, v in reqs[:7]]
+    res = _run(srv, items)
+    assert {r[2]["slot"] for r in res} <= {0, 1, 2}
+    srv.close()
+    with pytest.raises(hd.HDError):
+        hd.Server(gpu_ctx, g, None, "paper", 0.99, max_slots=4, mem_budget=100, Kmax=10)
