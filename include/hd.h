@@ -206,6 +206,23 @@ int hd_query_batch(hd_ctx* ctx, const hd_graph* g, const hd_eig* eig, int mode, 
 int hd_rank(hd_ctx* ctx, const float* X, int64_t n, int32_t B, int32_t ldx, const int32_t* K,
             int32_t Kmax, int32_t pool, int32_t* idx_out, float* score_out);
 
+/* Top-K ranking that allocates nothing (no counterpart in the paper): the
+ * results equal hd_rank's for the same inputs.  For callers that cannot call
+ * cudaMalloc at request time -- a real-time serving thread that must not block
+ * on the allocator's device synchronisation, a host whose device memory is
+ * entirely reserved by another framework's caching allocator, or a plugin that
+ * may only use memory handed to it.  Scratch is one file-scope device array of
+ * about 4.3 MB (B <= 256 columns, Kmax <= 2048) that every device using the
+ * library holds until the process exits.  The first call on a device looks up
+ * that array's device address (cudaGetSymbolAddress), so make it before any
+ * stream capture.  All calls share the array: calls whose work overlaps on the
+ * GPU (different streams or contexts, or host threads) race and must be
+ * serialised by the caller.  X (n x B, leading dimension ldx), idx_out and
+ * score_out (B x Kmax) must be device memory; K[B] is host.  No pooling.
+ * Errors: HD_ERR_INVALID_ARG beyond the limits or for host X/outputs. */
+int hd_rank_static(hd_ctx* ctx, const float* X, int64_t n, int32_t B, int32_t ldx,
+                   const int32_t* K, int32_t Kmax, int32_t* idx_out, float* score_out);
+
 /* ---- serving: continuous batching (spec serving pattern) ---------------- */
 
 typedef struct hd_req_stats {

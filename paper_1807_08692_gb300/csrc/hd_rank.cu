@@ -261,3 +261,85 @@ extern "C" int hd_rank(hd_ctx* ctx, const float* X, int64_t n, int32_t B, int32_
     }
     return rc;
 }
+
+// ------------------------------------------------------------------ allocation-free ranking
+// hd_rank_static: the same top-K as hd_rank, for callers that cannot allocate
+// device memory at call time.  All scratch lives in one file-scope device
+// array sized for the stated maxima below; every device that loads the library
+// holds it until the process exits.
+namespace {
+constexpr int RS_MAX_B = 256;
+constexpr int RS_MAX_K = 2048;
+constexpr size_t RS_STATE = RS_MAX_B * sizeof(SelState);
+constexpr size_t RS_HIST = (size_t)RS_MAX_B * 256 * sizeof(uint32_t);
+constexpr size_t RS_CAND = (size_t)RS_MAX_B * RS_MAX_K * sizeof(uint64_t);
+constexpr size_t RS_K = RS_MAX_B * sizeof(int32_t);
+constexpr size_t RS_BYTES = RS_STATE + RS_HIST + RS_CAND + RS_K;  // about 4.3 MB
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_rank_scratch[RS_BYTES];
+
+// Device address of g_rank_scratch per device (the host-side symbol is only a
+// stand-in and must never be handed to a kernel).  Filled on the first call on
+// each device, with that device current.
+static void* g_rank_scratch_dev[64] = {nullptr};
+
+extern "C" int hd_rank_static(hd_ctx* ctx, const float* X, int64_t n, int32_t B, int32_t ldx, const int32_t* K,
+                              int32_t Kmax, int32_t* idx_out, float* score_out) {
+    if (!ctx || !X || !K || !idx_out || !score_out || n <= 0 || n >= (1ll << 31) || B <= 0 || ldx < B)
+        return HD_ERR_INVALID_ARG;
+    if (B > RS_MAX_B || Kmax < 1 || Kmax > RS_MAX_K)
+        return hd_fail(ctx, HD_ERR_INVALID_ARG, "hd_rank_static: B=%d (max %d), Kmax=%d (max %d)", B, RS_MAX_B, Kmax,
+                       RS_MAX_K);
+    if (!hd_is_device_ptr(X) || !hd_is_device_ptr(idx_out) || !hd_is_device_ptr(score_out))
+        return hd_fail(ctx, HD_ERR_INVALID_ARG, "hd_rank_static: X and the outputs must be device memory");
+    for (int j = 0; j < B; ++j)
+        if (K[j] < 0 || K[j] > Kmax) return hd_fail(ctx, HD_ERR_INVALID_ARG, "K[%d]=%d outside [0, Kmax]", j, K[j]);
+    if (ctx->device < 0 || ctx->device >= 64) return hd_fail(ctx, HD_ERR_INVALID_ARG, "device %d", ctx->device);
+    HD_CUDA(ctx, cudaSetDevice(ctx->device));
+    if (!g_rank_scratch_dev[ctx->device]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_rank_scratch);
+        if (e != cudaSuccess || !p)
+            return hd_fail(ctx, HD_ERR_CUDA, "cudaGetSymbolAddress(g_rank_scratch): %s", cudaGetErrorString(e));
+        g_rank_scratch_dev[ctx->device] = p;
+    }
+    char* base = (char*)g_rank_scratch_dev[ctx->device];
+    SelState* st = (SelState*)base;
+    uint32_t* hist = (uint32_t*)(base + RS_STATE);
+    uint64_t* cand = (uint64_t*)(base + RS_STATE + RS_HIST);
+    int32_t* Kd = (int32_t*)(base + RS_STATE + RS_HIST + RS_CAND);
+    // the array keeps the previous call's contents: the histogram must start at zero
+    HD_CUDA(ctx, cudaMemsetAsync(hist, 0, (size_t)B * 256 * sizeof(uint32_t), ctx->stream));
+    HD_CUDA(ctx, cudaMemcpyAsync(Kd, K, B * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+    k_sel_init<<<ceil_div(B, 128), 128, 0, ctx->stream>>>(st, Kd, B, n);
+    HD_CHECK_LAUNCH(ctx);
+    HD_CUDA(ctx, cudaFuncSetAttribute(k_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, CG * 256 * 4));
+    const int gy = ceil_div(B, CG);
+    const int gx = std::max(1, std::min<int>(ceil_div(n * std::min(B, CG), 256), ctx->num_sms * 4 / gy + 1));
+    const size_t hsm = (size_t)std::min(B, CG) * 256 * 4;
+    SelState hs[RS_MAX_B];
+    for (int phase = 0; phase < 2; ++phase) {
+        if (phase == 1) {
+            HD_CUDA(ctx, cudaMemcpyAsync(hs, st, B * sizeof(SelState), cudaMemcpyDeviceToHost, ctx->stream));
+            HD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+            bool any = false;
+            for (int j = 0; j < B; ++j) any = any || hs[j].tie;
+            if (!any) break;
+        }
+        for (int shift = 24; shift >= 0; shift -= 8) {
+            k_hist<<<dim3(gx, gy), 256, hsm, ctx->stream>>>(X, n, B, ldx, st, phase, shift, hist);
+            HD_CHECK_LAUNCH(ctx);
+            k_select<<<ceil_div(B, 128), 128, 0, ctx->stream>>>(st, hist, B, phase, shift);
+            HD_CHECK_LAUNCH(ctx);
+        }
+    }
+    const int gc = std::max(1, std::min<int>(ceil_div(n * B, 256), ctx->num_sms * 8));
+    k_collect<<<gc, 256, 0, ctx->stream>>>(X, n, B, ldx, st, Kmax, cand);
+    HD_CHECK_LAUNCH(ctx);
+    int P = 1;
+    while (P < Kmax) P <<= 1;
+    k_sort_out<<<B, 256, (size_t)P * 8, ctx->stream>>>(cand, st, Kmax, idx_out, score_out);
+    HD_CHECK_LAUNCH(ctx);
+    return HD_OK;
+}

@@ -58,6 +58,7 @@ _SIGS = {
     "hd_query_batch": (C.c_int, [vp, vp, vp, C.c_int, i32, vp, vp, vp, f32, vp, i32, vp, i32, vp, vp, vp]),
     "hd_rank": (C.c_int, [vp, vp, i64, i32, i32, vp, i32, i32, vp, vp]),
     "hd_eig_project": (C.c_int, [vp, vp, vp, i32, vp]),
+    "hd_rank_static": (C.c_int, [vp, vp, i64, i32, i32, vp, i32, vp, vp]),
     "hd_serve_open": (C.c_int, [vp, vp, vp, C.c_int, f32, i32, C.c_size_t, i32, i32, C.POINTER(vp)]),
     "hd_serve_slots": (C.c_int, [vp]),
     "hd_serve_submit": (C.c_int, [vp, i32, vp, vp, f32, i32, C.POINTER(u64)]),

@@ -1,0 +1,46 @@
+"""hd_rank_static: the allocation-free top-K (for callers that cannot call
+cudaMalloc at request time) returns exactly what hd_rank returns, on two calls
+in a row that share its static scratch.  Named to be collected last."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+def _static_rank(ctx, X, K, Kmax):
+    import torch
+    from paper_1807_08692_gb300.hd import lib
+    n, B = X.shape
+    idx = torch.empty((B, Kmax), dtype=torch.int32, device=X.device)
+    sc = torch.empty((B, Kmax), dtype=torch.float32, device=X.device)
+    Kh = np.ascontiguousarray(K, np.int32)
+    rc = lib().hd_rank_static(ctx.handle, C.c_void_p(X.data_ptr()), n, B, X.stride(0), Kh.ctypes.data_as(C.c_void_p),
+                              Kmax, C.c_void_p(idx.data_ptr()), C.c_void_p(sc.data_ptr()))
+    ctx.check(rc, "hd_rank_static")
+    torch.cuda.synchronize()
+    return idx.cpu().numpy(), sc.cpu().numpy()
+
+
+def test_static_rank_equals_rank_twice():
+    import torch
+    import paper_1807_08692_gb300 as hd
+    ctx = hd.Context(0)
+    rng = np.random.default_rng(11)
+    cases = [
+        # many exact ties (scores on a coarse grid), ragged sizes, K up to Kmax, a K of 0
+        ((rng.integers(0, 50, (7001, 9)) / 16.0).astype(np.float32), [1, 10, 100, 1000, 2048, 0, 37, 512, 5], 2048),
+        # continuous scores, a different batch width: leftovers of the previous call must not matter
+        (rng.standard_normal((30011, 3)).astype(np.float32), [100, 7, 100], 100),
+    ]
+    for x, K, Kmax in cases:
+        Xd = torch.from_numpy(x).cuda()
+        ref_idx, ref_sc = hd.rank(ctx, Xd, np.asarray(K, np.int32), Kmax=Kmax)
+        for _ in range(2):
+            idx, sc = _static_rank(ctx, Xd, K, Kmax)
+            assert np.array_equal(idx, ref_idx)
+            assert np.array_equal(sc.view(np.uint32), ref_sc.view(np.uint32))
+    with pytest.raises(hd.HDError):
+        _static_rank(ctx, torch.zeros((10, 257), device="cuda"), [1] * 257, 4)
+    ctx.close()
