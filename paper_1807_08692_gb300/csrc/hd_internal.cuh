@@ -61,6 +61,8 @@ struct hd_graph {
     int32_t* col = nullptr;
     float* val = nullptr;     // normalised W
     float* dinv = nullptr;    // D^-1/2
+    // autotuned SpMM column-slab width per padded batch width (Bp -> S)
+    mutable std::map<int, int> slab_cache;
 };
 
 struct hd_eig {

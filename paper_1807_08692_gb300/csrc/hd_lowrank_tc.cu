@@ -20,7 +20,8 @@ constexpr int BM = 128;           // rows of U per tile
 constexpr int BK = 64;            // bf16 elements per 128-byte swizzle row
 constexpr int XSTAGES = 4;
 constexpr int RSTAGES = 3;
-constexpr int THREADS = 192;      // warp 0: TMA, warp 1: MMA, warps 2-5: epilogue / conversion
+constexpr int THREADS = 320;      // warp 0: TMA, warp 1: MMA, warps 2-9: epilogue / conversion
+constexpr int EPI = 256;          // epilogue threads: two warps per TMEM lane quarter, splitting the columns
 constexpr int TILE_BYTES = BM * BK * 2;  // 16 KB
 }  // namespace
 
@@ -75,11 +76,13 @@ struct ExpandArgs {
     const float* R;
     const float* P;
     const ColState* st;
+    const int* gate;
 };
 
 __global__ void __launch_bounds__(THREADS, 1)
     k_lr_expand_tc(const __grid_constant__ CUtensorMap tmU, const __grid_constant__ CUtensorMap tmHhi,
                    const __grid_constant__ CUtensorMap tmHlo, ExpandArgs a, int* err) {
+    if (a.gate && *a.gate == 0) return;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const uint32_t btile = (uint32_t)a.Nc * 128;  // one k-block of H^T (Nc rows x 128 B)
@@ -107,7 +110,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         tc::mbar_init(bfull, 1);
         for (int b = 0; b < 2; ++b) {
             tc::mbar_init(&acc_full[b], 1);
-            tc::mbar_init(&acc_empty[b], 128);
+            tc::mbar_init(&acc_empty[b], EPI);
         }
         tc::mbar_init(drain, 1);
         *abort_flag = 0;
@@ -190,8 +193,14 @@ __global__ void __launch_bounds__(THREADS, 1)
             }
         }
     } else {
+        // epilogue: warps 2-9; lane quarter (warp % 4) gives the TMEM lanes (rows),
+        // the two warps of a quarter split the 16-column chunks
         const int quarter = warp & 3;
+        const int half = (warp - 2) >> 2;
         const int rloc = quarter * 32 + lane;
+        const int nch = a.Nc / 16;
+        const int nh = (nch + 1) / 2;
+        const int cb = half ? nh : 0, ce = half ? nch : nh;
         uint32_t tcount = 0;
         bool ok = true;
         for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tcount) {
@@ -202,28 +211,47 @@ __global__ void __launch_bounds__(THREADS, 1)
             }
             tc::fence_after_sync();
             const int64_t row = (int64_t)t * BM + rloc;
-            for (int c = 0; c < a.Nc / 16; ++c) {
-                float v[16];
-                tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + ab * a.Nc + c * 16, v);
-                tc::tmem_ld_wait();
-                if (row < a.n) {
+            const bool live = row < a.n;
+            for (int c0 = cb; c0 < ce; c0 += 2) {
+                // issue the global loads of two chunks before touching TMEM
+                float4 g1[2][4], g2[2][4];
+#pragma unroll
+                for (int u = 0; u < 2; ++u)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int j = a.c0 + (c0 + u) * 16 + 4 * q;
+                        g1[u][q] = g2[u][q] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (!live || c0 + u >= ce || j >= a.Bp || a.op == EXP_SET_X) continue;
+                        if (a.op == EXP_DIRECTION) {
+                            g1[u][q] = *reinterpret_cast<const float4*>(a.R + row * a.Bp + j);
+                            g2[u][q] = *reinterpret_cast<const float4*>(a.P + row * a.Bp + j);
+                        } else {
+                            g1[u][q] = *reinterpret_cast<const float4*>(a.out + row * a.Bp + j);
+                        }
+                    }
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    if (c0 + u >= ce) break;
+                    const int c = c0 + u;
+                    float v[16];
+                    tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + ab * a.Nc + c * 16, v);
+                    tc::tmem_ld_wait();
+                    if (!live) continue;
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
                         const int j = a.c0 + c * 16 + 4 * q;
                         if (j >= a.Bp) break;
-                        float4* o = reinterpret_cast<float4*>(a.out + row * a.Bp + j);
                         float4 w;
                         if (a.op == EXP_SET_X) {
                             w = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
                         } else if (a.op == EXP_SUB_R) {
-                            w = *o;
+                            w = g1[u][q];
                             w.x -= v[4 * q]; w.y -= v[4 * q + 1]; w.z -= v[4 * q + 2]; w.w -= v[4 * q + 3];
                         } else if (a.op == EXP_ADD_Q) {
-                            w = *o;
+                            w = g1[u][q];
                             w.x += v[4 * q]; w.y += v[4 * q + 1]; w.z += v[4 * q + 2]; w.w += v[4 * q + 3];
                         } else {
-                            const float4 rr = *reinterpret_cast<const float4*>(a.R + row * a.Bp + j);
-                            const float4 pp = *reinterpret_cast<const float4*>(a.P + row * a.Bp + j);
+                            const float4 rr = g1[u][q], pp = g2[u][q];
                             const float b0 = (float)a.st[j].beta, b1 = (float)a.st[j + 1].beta;
                             const float b2 = (float)a.st[j + 2].beta, b3 = (float)a.st[j + 3].beta;
                             w.x = rr.x + v[4 * q] + (b0 == 0.0f ? 0.0f : b0 * pp.x);
@@ -231,7 +259,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                             w.z = rr.z + v[4 * q + 2] + (b2 == 0.0f ? 0.0f : b2 * pp.z);
                             w.w = rr.w + v[4 * q + 3] + (b3 == 0.0f ? 0.0f : b3 * pp.w);
                         }
-                        *o = w;
+                        *reinterpret_cast<float4*>(a.out + row * a.Bp + j) = w;
                     }
                 }
             }
@@ -266,10 +294,12 @@ struct ReduceArgs {
     uint32_t tmem_cols;
     const float* V;
     float* part;         // [gridDim.x][rpad][Bp]
+    const int* gate;
 };
 
 __global__ void __launch_bounds__(THREADS, 1)
     k_lr_reduce_tc(const __grid_constant__ CUtensorMap tmU, ReduceArgs a, int* err) {
+    if (a.gate && *a.gate == 0) return;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const uint32_t astage = 2 * TILE_BYTES;                 // 128 rows x 128 eigen-indices
@@ -298,7 +328,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             tc::mbar_init(&empty[s], 1);
         }
         for (int b = 0; b < 2; ++b) {
-            tc::mbar_init(&bfull[b], 128);
+            tc::mbar_init(&bfull[b], EPI);
             tc::mbar_init(&bempty[b], 1);
         }
         tc::mbar_init(done, 1);
@@ -382,8 +412,10 @@ __global__ void __launch_bounds__(THREADS, 1)
         // conversion of V tiles into bf16 hi/lo, MN-major 128-byte swizzle, then the epilogue
         const int tid = threadIdx.x - 64;
         const int quarter = warp & 3;
+        const int half = (warp - 2) >> 2;
         bool ok = true;
         const int cq_n = a.Nc / 4;
+        const int total = BM * cq_n;
         for (int tl = 0; tl < ntl && ok; ++tl) {
             const int buf = tl & 1;
             if (!tc::mbar_wait(&bempty[buf], ((tl >> 1) & 1) ^ 1, abort_flag)) {
@@ -393,24 +425,35 @@ __global__ void __launch_bounds__(THREADS, 1)
             uint8_t* bh = Bs + (2 * buf) * bterm;
             uint8_t* bl = Bs + (2 * buf + 1) * bterm;
             const int64_t row0 = (t0 + tl) * BM;
-            for (int e = tid; e < BM * cq_n; e += 128) {
-                const int rr = e / cq_n, cq = e % cq_n;
-                const int jl = 4 * cq;             // column within the launch
-                const int j = a.c0 + jl;
-                const int64_t i = row0 + rr;
-                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (i < a.n && j < a.Bp) v = *reinterpret_cast<const float4*>(a.V + i * a.Bp + j);
-                __nv_bfloat16 h[4], l[4];
-                const float vv[4] = {v.x, v.y, v.z, v.w};
+            for (int base = tid; base < total; base += EPI * 8) {
+                float4 v[8];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    h[q] = __float2bfloat16_rn(vv[q]);
-                    l[q] = __float2bfloat16_rn(vv[q] - __bfloat162float(h[q]));
+                for (int u = 0; u < 8; ++u) {
+                    const int e = base + u * EPI;
+                    v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (e < total) {
+                        const int rr = e / cq_n, j = a.c0 + 4 * (e % cq_n);
+                        const int64_t i = row0 + rr;
+                        if (i < a.n && j < a.Bp) v[u] = *reinterpret_cast<const float4*>(a.V + i * a.Bp + j);
+                    }
                 }
-                const int nb = jl >> 6, jj = jl & 63;
-                const uint32_t off = nb * TILE_BYTES + rr * 128 + ((((jj >> 3) ^ (rr & 7))) << 4) + (jj & 7) * 2;
-                *reinterpret_cast<uint2*>(bh + off) = *reinterpret_cast<const uint2*>(h);
-                *reinterpret_cast<uint2*>(bl + off) = *reinterpret_cast<const uint2*>(l);
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int e = base + u * EPI;
+                    if (e >= total) break;
+                    const int rr = e / cq_n, jl = 4 * (e % cq_n);
+                    __nv_bfloat16 h[4], l[4];
+                    const float vv[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        h[q] = __float2bfloat16_rn(vv[q]);
+                        l[q] = __float2bfloat16_rn(vv[q] - __bfloat162float(h[q]));
+                    }
+                    const int nb = jl >> 6, jj = jl & 63;
+                    const uint32_t off = nb * TILE_BYTES + rr * 128 + ((((jj >> 3) ^ (rr & 7))) << 4) + (jj & 7) * 2;
+                    *reinterpret_cast<uint2*>(bh + off) = *reinterpret_cast<const uint2*>(h);
+                    *reinterpret_cast<uint2*>(bl + off) = *reinterpret_cast<const uint2*>(l);
+                }
             }
             tc::fence_proxy_async_smem();
             tc::mbar_arrive(&bfull[buf]);
@@ -424,9 +467,12 @@ __global__ void __launch_bounds__(THREADS, 1)
         const bool have = ntl > 0 && ok && tc::mbar_wait(done, 0, abort_flag);
         if (ntl > 0 && !have) atomicExch(err, 24);
         tc::fence_after_sync();
+        const int nch = a.Nc / 16;
+        const int nh = (nch + 1) / 2;
+        const int cb = half ? nh : 0, ce = half ? nch : nh;
         for (int m = 0; m < a.mt; ++m) {
             const int k = m * 128 + quarter * 32 + lane;
-            for (int c = 0; c < a.Nc / 16; ++c) {
+            for (int c = cb; c < ce; ++c) {
                 float v[16];
                 if (have) {
                     tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + m * a.Nc + c * 16, v);
@@ -469,7 +515,7 @@ static int check_err(hd_ctx* ctx, const char* what) {
 }
 
 int lr_tc_expand(hd_ctx* ctx, const LowRank& lr, int op, float* out, const float* Rv, const float* Pv, int64_t n,
-                 int32_t Bp, const ColState* st) {
+                 int32_t Bp, const ColState* st, const int* gate) {
     const hd_eig* e = lr.e;
     const int nkb = lr.rpad / BK;
     CUtensorMap tu;
@@ -504,6 +550,7 @@ int lr_tc_expand(hd_ctx* ctx, const LowRank& lr, int op, float* out, const float
         a.R = Rv;
         a.P = Pv;
         a.st = st;
+        a.gate = gate;
         const size_t smem = 1024 + XSTAGES * TILE_BYTES + 2 * (size_t)nkb * nc * 128 + 256;
         const int tiles = (int)((n + BM - 1) / BM);
         const int grid = std::min(tiles, ctx->num_sms);
@@ -513,7 +560,7 @@ int lr_tc_expand(hd_ctx* ctx, const LowRank& lr, int op, float* out, const float
     return check_err(ctx, "expand");
 }
 
-int lr_tc_reduce(hd_ctx* ctx, const LowRank& lr, const float* V, int64_t n, int32_t Bp) {
+int lr_tc_reduce(hd_ctx* ctx, const LowRank& lr, const float* V, int64_t n, int32_t Bp, const int* gate) {
     const hd_eig* e = lr.e;
     const int mt = (e->r + 127) / 128;
     CUtensorMap tu;
@@ -553,6 +600,7 @@ int lr_tc_reduce(hd_ctx* ctx, const LowRank& lr, const float* V, int64_t n, int3
         a.tmem_cols = tmem_cols_for(mt * nc);
         a.V = V;
         a.part = lr.part;
+        a.gate = gate;
         const size_t smem = 1024 + smem_of(nc) + 256;
         k_lr_reduce_tc<<<grid, THREADS, smem, ctx->stream>>>(tu, a, ctx->d_flags + 3);
         HD_CHECK_LAUNCH(ctx);

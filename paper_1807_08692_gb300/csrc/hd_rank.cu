@@ -131,10 +131,12 @@ __global__ void k_collect(const float* X, int64_t n, int32_t B, int32_t ld, SelS
 }
 
 // Sort each column's candidates descending by (key, ~id) and write ids / scores.
-__global__ void k_sort_out(const uint64_t* cand, const SelState* st, int32_t Kmax, int32_t* idx_out, float* score_out) {
+__global__ void k_sort_out(const uint64_t* cand, const SelState* st, int32_t Kmax, int32_t* idx_out, float* score_out,
+                           int skip_empty = 0) {
     extern __shared__ uint64_t sk[];
     const int j = blockIdx.x;
     const int K = min(st[j].K, Kmax);
+    if (skip_empty && K == 0) return;
     int P = 1;
     while (P < K) P <<= 1;
     for (int t = threadIdx.x; t < P; t += blockDim.x) sk[t] = t < K ? cand[(int64_t)j * Kmax + t] : 0ull;
@@ -166,13 +168,110 @@ __global__ void k_sort_out(const uint64_t* cand, const SelState* st, int32_t Kma
     }
 }
 
+// ---- sampled-threshold fast path ----------------------------------------------
+// A strided sample of each column gives a key threshold tau with, in
+// expectation, about 4K + 8 (n / sample) elements at or above it; one pass over
+// the scores collects those candidates, and a per-column sort keeps the top K.
+// The result is exact whenever at least K and at most CAP candidates passed;
+// otherwise that column is ranked again by the radix select.
+constexpr int TK_SAMPLE = 4096;
+constexpr int TK_CAP = 16384;
+
+__device__ __forceinline__ void bitonic_desc_u64(uint64_t* a, int P) {
+    for (int size = 2; size <= P; size <<= 1)
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int t = threadIdx.x; t < P; t += blockDim.x) {
+                const int u = t ^ stride;
+                if (u > t) {
+                    const bool desc = (t & size) == 0;
+                    const uint64_t x = a[t], y = a[u];
+                    if (desc ? (x < y) : (x > y)) {
+                        a[t] = y;
+                        a[u] = x;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+}
+
+__global__ void __launch_bounds__(1024) k_topk_sample(const float* X, int64_t n, int32_t ld, const int32_t* Kd,
+                                                     uint32_t* tau, int* cnt) {
+    __shared__ uint64_t sk[TK_SAMPLE];
+    const int j = blockIdx.x;
+    const int64_t K = (int64_t)Kd[j] < n ? (int64_t)Kd[j] : n;
+    const int s = (int)(n < TK_SAMPLE ? n : (int64_t)TK_SAMPLE);
+    for (int t = threadIdx.x; t < TK_SAMPLE; t += blockDim.x) {
+        uint64_t v = 0;
+        if (t < s) {
+            const int64_t i = (int64_t)t * n / s;
+            v = (uint64_t)float_key(X[i * ld + j]);
+        }
+        sk[t] = v;
+    }
+    __syncthreads();
+    bitonic_desc_u64(sk, TK_SAMPLE);
+    if (threadIdx.x == 0) {
+        int64_t kp = (4 * K * s + n - 1) / n + 8;
+        if (kp > s - 1) kp = s - 1;
+        tau[j] = (uint32_t)sk[kp];
+        cnt[j] = 0;
+    }
+}
+
+__global__ void k_topk_filter(const float* X, int64_t n, int32_t B, int32_t ld, const int32_t* Kd,
+                              const uint32_t* tau, int* cnt, uint64_t* cand) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * B; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / B;
+        const int j = (int)(e % B);
+        const uint32_t key = float_key(X[i * ld + j]);
+        if (key >= __ldg(tau + j) && __ldg(Kd + j) > 0) {
+            const int p = atomicAdd(&cnt[j], 1);
+            if (p < TK_CAP) cand[(int64_t)j * TK_CAP + p] = ((uint64_t)key << 32) | (uint64_t)(~(uint32_t)i);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_topk_sort(const uint64_t* cand, const int* cnt, const int32_t* Kd, int64_t n,
+                                                   int32_t Kmax, int32_t* idx_out, float* score_out, int* fail) {
+    extern __shared__ uint64_t sk[];
+    const int j = blockIdx.x;
+    const int K = (int)((int64_t)Kd[j] < n ? (int64_t)Kd[j] : n);
+    const int c = cnt[j];
+    if (K > 0 && (c < K || c > TK_CAP)) {
+        if (threadIdx.x == 0) fail[j] = 1;
+        return;
+    }
+    if (threadIdx.x == 0) fail[j] = 0;
+    int P = 1;
+    while (P < c) P <<= 1;
+    if (K > 0) {
+        for (int t = threadIdx.x; t < P; t += blockDim.x) sk[t] = t < c ? cand[(int64_t)j * TK_CAP + t] : 0ull;
+        __syncthreads();
+        bitonic_desc_u64(sk, P);
+    }
+    for (int t = threadIdx.x; t < Kmax; t += blockDim.x) {
+        if (t < K) {
+            const uint64_t v = sk[t];
+            idx_out[(int64_t)j * Kmax + t] = (int32_t)(~(uint32_t)(v & 0xFFFFFFFFu));
+            score_out[(int64_t)j * Kmax + t] = key_float((uint32_t)(v >> 32));
+        } else {
+            idx_out[(int64_t)j * Kmax + t] = -1;
+            score_out[(int64_t)j * Kmax + t] = 0.0f;
+        }
+    }
+}
+
+static int radix_rank(hd_ctx* ctx, const float* src, int64_t m, int32_t B, int32_t ld, const int32_t* K_h,
+                      int32_t Kmax, int32_t* idx_d, float* score_d, int skip_empty, WsCarver& cv);
+
 int hd_rank_impl(hd_ctx* ctx, const float* Xd, int64_t n, int32_t B, int32_t ldx, const int32_t* K_h, int32_t Kmax,
                  int32_t pool, int32_t* idx_d, float* score_d) {
     const float* src = Xd;
     int64_t m = n;
     int32_t ld = ldx;
     size_t bytes = ws_size(B * sizeof(SelState)) + ws_size((size_t)B * 256 * 4) + ws_size((size_t)B * Kmax * 8) +
-                   ws_size(B * 4);
+                   ws_size(B * 4) + ws_size((size_t)B * TK_CAP * 8) + 3 * ws_size(B * 4) + ws_size(B * 4);
     if (pool > 1) {
         m = n / pool;
         bytes += ws_size((size_t)m * B * 4);
@@ -181,10 +280,11 @@ int hd_rank_impl(hd_ctx* ctx, const float* Xd, int64_t n, int32_t B, int32_t ldx
     int rc = hd_ws_reserve(ctx, bytes, &ws);
     if (rc) return rc;
     WsCarver cv(ws);
-    SelState* st = cv.take<SelState>(B);
-    uint32_t* hist = cv.take<uint32_t>((size_t)B * 256);
-    uint64_t* cand = cv.take<uint64_t>((size_t)B * Kmax);
     int32_t* Kd = cv.take<int32_t>(B);
+    uint64_t* cand = cv.take<uint64_t>((size_t)B * TK_CAP);
+    uint32_t* tau = cv.take<uint32_t>(B);
+    int* cnt = cv.take<int>(B);
+    int* fail = cv.take<int>(B);
     if (pool > 1) {
         float* Y = cv.take<float>((size_t)m * B);
         k_pool<<<ceil_div(m * B, 256), 256, 0, ctx->stream>>>(Xd, m, B, ldx, pool, Y);
@@ -192,6 +292,41 @@ int hd_rank_impl(hd_ctx* ctx, const float* Xd, int64_t n, int32_t B, int32_t ldx
         src = Y;
         ld = B;
     }
+    HD_CUDA(ctx, cudaMemcpyAsync(Kd, K_h, B * 4, cudaMemcpyHostToDevice, ctx->stream));
+    static bool attr = false;
+    if (!attr) {
+        HD_CUDA(ctx, cudaFuncSetAttribute(k_topk_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, TK_CAP * 8));
+        attr = true;
+    }
+    k_topk_sample<<<B, 1024, 0, ctx->stream>>>(src, m, ld, Kd, tau, cnt);
+    HD_CHECK_LAUNCH(ctx);
+    const int gc = std::max(1, std::min<int>(ceil_div(m * B, 256), ctx->num_sms * 8));
+    k_topk_filter<<<gc, 256, 0, ctx->stream>>>(src, m, B, ld, Kd, tau, cnt, cand);
+    HD_CHECK_LAUNCH(ctx);
+    k_topk_sort<<<B, 1024, TK_CAP * 8, ctx->stream>>>(cand, cnt, Kd, m, Kmax, idx_d, score_d, fail);
+    HD_CHECK_LAUNCH(ctx);
+    std::vector<int> hf(B);
+    HD_CUDA(ctx, cudaMemcpyAsync(hf.data(), fail, B * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    HD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    std::vector<int32_t> Kf(B, 0);
+    bool any = false;
+    for (int j = 0; j < B; ++j)
+        if (hf[j]) {
+            Kf[j] = K_h[j];
+            any = true;
+        }
+    if (!any) return HD_OK;
+    return radix_rank(ctx, src, m, B, ld, Kf.data(), Kmax, idx_d, score_d, 1, cv);
+}
+
+// Exact radix select for the columns with K > 0 (the others are left untouched
+// when skip_empty is set).
+static int radix_rank(hd_ctx* ctx, const float* src, int64_t m, int32_t B, int32_t ld, const int32_t* K_h,
+                      int32_t Kmax, int32_t* idx_d, float* score_d, int skip_empty, WsCarver& cv) {
+    SelState* st = cv.take<SelState>(B);
+    uint32_t* hist = cv.take<uint32_t>((size_t)B * 256);
+    uint64_t* cand = cv.take<uint64_t>((size_t)B * Kmax);
+    int32_t* Kd = cv.take<int32_t>(B);
     HD_CUDA(ctx, cudaMemcpyAsync(Kd, K_h, B * 4, cudaMemcpyHostToDevice, ctx->stream));
     HD_CUDA(ctx, cudaMemsetAsync(hist, 0, (size_t)B * 256 * 4, ctx->stream));
     k_sel_init<<<ceil_div(B, 128), 128, 0, ctx->stream>>>(st, Kd, B, m);
@@ -226,7 +361,7 @@ int hd_rank_impl(hd_ctx* ctx, const float* Xd, int64_t n, int32_t B, int32_t ldx
     HD_CHECK_LAUNCH(ctx);
     int P = 1;
     while (P < Kmax) P <<= 1;
-    k_sort_out<<<B, 256, (size_t)P * 8, ctx->stream>>>(cand, st, Kmax, idx_d, score_d);
+    k_sort_out<<<B, 256, (size_t)P * 8, ctx->stream>>>(cand, st, Kmax, idx_d, score_d, skip_empty);
     HD_CHECK_LAUNCH(ctx);
     return HD_OK;
 }

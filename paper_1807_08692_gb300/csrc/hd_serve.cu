@@ -49,7 +49,7 @@ struct AdmitRec {
     double bb;
 };
 
-__global__ void k_admit_mark(const AdmitRec* recs, int nrec, ColState* st) {
+__global__ void k_admit_mark(const AdmitRec* recs, int nrec, ColState* st, int* num_active) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nrec) return;
     const AdmitRec a = recs[t];
@@ -60,6 +60,7 @@ __global__ void k_admit_mark(const AdmitRec* recs, int nrec, ColState* st) {
     s.beta = 0.0;
     s.bb = a.bb;
     s.tol2 = (double)a.tol * (double)a.tol * a.bb;
+    atomicAdd(num_active, 1);  // admitted columns are work for this iteration's gated kernels
 }
 
 __global__ void k_admit_scatter(const AdmitRec* recs, int nrec, const int32_t* yidx, const float* yval, float* R,
@@ -157,7 +158,7 @@ int hd_serve_open(hd_ctx* ctx, const hd_graph* g, const hd_eig* eig, int mode, f
     E.n = n;
     E.B = slots;
     E.Bp = (slots + 3) / 4 * 4;
-    E.vl = vec_launch(ctx, n, E.Bp);
+    E.vl = vec_launch(ctx, n, E.Bp);  // re-tuned below once the buffers exist
     E.has_lr = lr_on;
     E.r = lr_on ? eig->r : 0;
     E.eff_mode = lr_on ? HD_MODE_PCG : HD_MODE_PAPER;
@@ -172,7 +173,7 @@ int hd_serve_open(hd_ctx* ctx, const hd_graph* g, const hd_eig* eig, int mode, f
     if (lr_on) nchunk = lr_use_tensor_cores(eig) ? lr_tc_nchunk(ctx, n) : simt_nchunk(ctx, n, rpad, Bp);
     s->cap_nnz = Bp * 512;
     const size_t vec = (size_t)n * Bp * 4;
-    size_t bytes = 4 * ws_size(vec) + ws_size((size_t)E.vl.nblk * Bp * 8) + ws_size(Bp * sizeof(ColState)) +
+    size_t bytes = 4 * ws_size(vec) + ws_size((size_t)ctx->num_sms * 8 * Bp * 8) + ws_size(Bp * sizeof(ColState)) +
                    ws_size(64) + ws_size(Bp * sizeof(AdmitRec)) + 2 * ws_size((size_t)s->cap_nnz * 4) +
                    2 * ws_size((size_t)Bp * Kmax * 4);
     if (lr_on)
@@ -189,10 +190,11 @@ int hd_serve_open(hd_ctx* ctx, const hd_graph* g, const hd_eig* eig, int mode, f
     E.P = cv.take<float>((size_t)n * Bp);
     E.Q = cv.take<float>((size_t)n * Bp);
     E.X = cv.take<float>((size_t)n * Bp);
-    E.part = cv.take<float2>((size_t)E.vl.nblk * Bp);
+    E.part = cv.take<float2>((size_t)ctx->num_sms * 8 * Bp);
     E.st = cv.take<ColState>(Bp);
     E.num_active = cv.take<int>(16);
     E.err = E.num_active + 1;
+    E.vl = vec_launch(ctx, n, Bp, tune_slab(ctx, g, Bp, E.P, E.Q));
     s->d_rec = cv.take<AdmitRec>(Bp);
     s->d_yidx = cv.take<int32_t>(s->cap_nnz);
     s->d_yval = cv.take<float>(s->cap_nnz);
@@ -304,7 +306,7 @@ int hd_serve_step(hd_server* s, int32_t iters, int32_t* busy) {
         HD_CUDA(ctx, cudaMemcpyAsync(s->d_rec, s->h_rec, s->nrec * sizeof(AdmitRec), cudaMemcpyHostToDevice, ctx->stream));
         HD_CUDA(ctx, cudaMemcpyAsync(s->d_yidx, s->h_yidx, (size_t)off * 4, cudaMemcpyHostToDevice, ctx->stream));
         HD_CUDA(ctx, cudaMemcpyAsync(s->d_yval, s->h_yval, (size_t)off * 4, cudaMemcpyHostToDevice, ctx->stream));
-        k_admit_mark<<<ceil_div(s->nrec, 64), 64, 0, ctx->stream>>>(s->d_rec, s->nrec, E.st);
+        k_admit_mark<<<ceil_div(s->nrec, 64), 64, 0, ctx->stream>>>(s->d_rec, s->nrec, E.st, E.num_active);
         HD_CHECK_LAUNCH(ctx);
         if (iters < 1) iters = 1;  // the admission completes inside the next iteration
     }

@@ -72,37 +72,69 @@ __global__ void k_scatter_y(const int32_t* y_ptr, const int32_t* y_idx, const fl
     }
 }
 
+// True when some column of this block's S-column slab is active (or being
+// (re)admitted); with st == nullptr every slab works.
+template <int S>
+__device__ __forceinline__ bool slab_has_work(const ColState* st, bool include_fresh) {
+    if (!st) return true;
+    int w = 0;
+    if (threadIdx.x < S) {
+        const ColState& c = st[blockIdx.y * S + threadIdx.x];
+        w = c.active || (include_fresh && c.fresh);
+    }
+    return __syncthreads_or(w) != 0;
+}
+
+#define FMA4(acc_, wt_, vec_)                  \
+    acc_.x = fmaf(wt_, vec_.x, acc_.x);       \
+    acc_.y = fmaf(wt_, vec_.y, acc_.y);       \
+    acc_.z = fmaf(wt_, vec_.z, acc_.z);       \
+    acc_.w = fmaf(wt_, vec_.w, acc_.w)
+
 // Q = c1 P - c2 W P for the S-column slab blockIdx.y; optional partials of P^T Q.
 template <int S>
 __global__ void __launch_bounds__(256) k_spmm(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                                               const float* __restrict__ wv, const float* __restrict__ P,
                                               float* __restrict__ Q, int64_t n, int32_t ld, float c1, float c2,
-                                              float2* __restrict__ part) {
+                                              float2* __restrict__ part, const ColState* __restrict__ st) {
     constexpr int L = S / 4;
     constexpr int RPB = 256 / L;
+    if (!slab_has_work<S>(st, false)) return;
     const int g = (threadIdx.x & 31) % L;
     const int col = blockIdx.y * S + 4 * g;
     KSum acc[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
     for (int64_t row = (int64_t)blockIdx.x * RPB + threadIdx.x / L; row < n; row += (int64_t)gridDim.x * RPB) {
         const int32_t b = __ldg(rp + row), e = __ldg(rp + row + 1);
         float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 s2 = make_float4(0.f, 0.f, 0.f, 0.f);
         int32_t t = b;
-        for (; t + 4 <= e; t += 4) {
-            const int32_t j0 = __ldg(ci + t), j1 = __ldg(ci + t + 1), j2 = __ldg(ci + t + 2), j3 = __ldg(ci + t + 3);
-            const float w0 = __ldg(wv + t), w1 = __ldg(wv + t + 1), w2 = __ldg(wv + t + 2), w3 = __ldg(wv + t + 3);
-            const float4 v0 = ld4(P + (int64_t)j0 * ld + col), v1 = ld4(P + (int64_t)j1 * ld + col);
-            const float4 v2 = ld4(P + (int64_t)j2 * ld + col), v3 = ld4(P + (int64_t)j3 * ld + col);
-            s.x = fmaf(w0, v0.x, s.x); s.y = fmaf(w0, v0.y, s.y); s.z = fmaf(w0, v0.z, s.z); s.w = fmaf(w0, v0.w, s.w);
-            s.x = fmaf(w1, v1.x, s.x); s.y = fmaf(w1, v1.y, s.y); s.z = fmaf(w1, v1.z, s.z); s.w = fmaf(w1, v1.w, s.w);
-            s.x = fmaf(w2, v2.x, s.x); s.y = fmaf(w2, v2.y, s.y); s.z = fmaf(w2, v2.z, s.z); s.w = fmaf(w2, v2.w, s.w);
-            s.x = fmaf(w3, v3.x, s.x); s.y = fmaf(w3, v3.y, s.y); s.z = fmaf(w3, v3.z, s.z); s.w = fmaf(w3, v3.w, s.w);
+        for (; t + 8 <= e; t += 8) {
+            int32_t j[8];
+            float w[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                j[u] = __ldg(ci + t + u);
+                w[u] = __ldg(wv + t + u);
+            }
+            float4 v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = ld4(P + (int64_t)j[u] * ld + col);
+#pragma unroll
+            for (int u = 0; u < 8; u += 2) {
+                FMA4(s, w[u], v[u]);
+                FMA4(s2, w[u + 1], v[u + 1]);
+            }
         }
         for (; t < e; ++t) {
             const int32_t j0 = __ldg(ci + t);
             const float w0 = __ldg(wv + t);
             const float4 v0 = ld4(P + (int64_t)j0 * ld + col);
-            s.x = fmaf(w0, v0.x, s.x); s.y = fmaf(w0, v0.y, s.y); s.z = fmaf(w0, v0.z, s.z); s.w = fmaf(w0, v0.w, s.w);
+            FMA4(s, w0, v0);
         }
+        s.x += s2.x;
+        s.y += s2.y;
+        s.z += s2.z;
+        s.w += s2.w;
         const float4 own = ld4(P + row * ld + col);
         float4 q;
         q.x = c1 * own.x - c2 * s.x;
@@ -146,6 +178,7 @@ __global__ void __launch_bounds__(256) k_update(float* __restrict__ X, float* __
                                                 float2* __restrict__ part) {
     constexpr int L = S / 4;
     constexpr int RPB = 256 / L;
+    if (!slab_has_work<S>(st, true)) return;
     const int g = (threadIdx.x & 31) % L;
     const int col = blockIdx.y * S + 4 * g;
     const float a0 = (float)st[col].a, a1 = (float)st[col + 1].a, a2 = (float)st[col + 2].a, a3 = (float)st[col + 3].a;
@@ -182,6 +215,7 @@ __global__ void __launch_bounds__(256) k_direction(float* __restrict__ P, const 
                                                    int32_t ld, const ColState* __restrict__ st) {
     constexpr int L = S / 4;
     constexpr int RPB = 256 / L;
+    if (!slab_has_work<S>(st, false)) return;
     const int g = (threadIdx.x & 31) % L;
     const int col = blockIdx.y * S + 4 * g;
     const float b0 = (float)st[col].beta, b1 = (float)st[col + 1].beta, b2 = (float)st[col + 2].beta,
@@ -380,7 +414,8 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_lr_reduce_simt(const T* __restrict__ U, const float* __restrict__ scale,
                                                         int ldu, int r, int rpad, const float* __restrict__ V,
                                                         int64_t n, int32_t Bp, int64_t rpc,
-                                                        float* __restrict__ part) {
+                                                        float* __restrict__ part, const int* gate) {
+    if (gate && *gate == 0) return;
     const int kk = threadIdx.x >> 2, cq = 4 * (threadIdx.x & 3);
     const int k = blockIdx.y * 64 + kk;
     const int col = blockIdx.z * 16 + cq;
@@ -434,7 +469,8 @@ __global__ void __launch_bounds__(256) k_lr_expand_simt(const T* __restrict__ U,
                                                         int ldu, int r, const float* __restrict__ H, int op,
                                                         float* __restrict__ out, const float* __restrict__ Rv,
                                                         const float* __restrict__ Pv, int64_t n, int32_t Bp,
-                                                        const ColState* __restrict__ st) {
+                                                        const ColState* __restrict__ st, const int* gate) {
+    if (gate && *gate == 0) return;
     extern __shared__ float Hs[];  // [r][16]
     const int slab = blockIdx.y;
     for (int e = threadIdx.x; e < r * 16; e += blockDim.x) {
@@ -490,21 +526,21 @@ int simt_nchunk(hd_ctx* ctx, int64_t n, int rpad, int Bp) {
     return (int)std::max<int64_t>(1, std::min<int64_t>(nc, maxc));
 }
 
-int lr_reduce(hd_ctx* ctx, const LowRank& lr, const float* V, int64_t n, int32_t Bp) {
+int lr_reduce(hd_ctx* ctx, const LowRank& lr, const float* V, int64_t n, int32_t Bp, const int* gate) {
     HD_PROF(ctx, "lr_reduce");
-    if (lr_use_tensor_cores(lr.e)) return lr_tc_reduce(ctx, lr, V, n, Bp);
+    if (lr_use_tensor_cores(lr.e)) return lr_tc_reduce(ctx, lr, V, n, Bp, gate);
     const hd_eig* e = lr.e;
     int64_t rpc = (n + lr.nchunk - 1) / lr.nchunk;
     dim3 grid(lr.nchunk, lr.rpad / 64, ceil_div(Bp, 16));
     if (e->storage == HD_F32)
         k_lr_reduce_simt<float><<<grid, 256, 0, ctx->stream>>>((const float*)e->U, e->scale, e->ldu, e->r, lr.rpad, V,
-                                                               n, Bp, rpc, lr.part);
+                                                               n, Bp, rpc, lr.part, gate);
     else if (e->storage == HD_BF16)
         k_lr_reduce_simt<__nv_bfloat16><<<grid, 256, 0, ctx->stream>>>((const __nv_bfloat16*)e->U, e->scale, e->ldu,
-                                                                       e->r, lr.rpad, V, n, Bp, rpc, lr.part);
+                                                                       e->r, lr.rpad, V, n, Bp, rpc, lr.part, gate);
     else
         k_lr_reduce_simt<__nv_fp8_e4m3><<<grid, 256, 0, ctx->stream>>>((const __nv_fp8_e4m3*)e->U, e->scale, e->ldu,
-                                                                       e->r, lr.rpad, V, n, Bp, rpc, lr.part);
+                                                                       e->r, lr.rpad, V, n, Bp, rpc, lr.part, gate);
     HD_CHECK_LAUNCH(ctx);
     return HD_OK;
 }
@@ -519,9 +555,9 @@ int lr_finish(hd_ctx* ctx, const LowRank& lr, int32_t Bp, const double* coef) {
 }
 
 int lr_expand(hd_ctx* ctx, const LowRank& lr, int op, float* out, const float* Rv, const float* Pv, int64_t n,
-              int32_t Bp, const ColState* st) {
+              int32_t Bp, const ColState* st, const int* gate) {
     HD_PROF(ctx, "lr_expand");
-    if (lr_use_tensor_cores(lr.e)) return lr_tc_expand(ctx, lr, op, out, Rv, Pv, n, Bp, st);
+    if (lr_use_tensor_cores(lr.e)) return lr_tc_expand(ctx, lr, op, out, Rv, Pv, n, Bp, st, gate);
     const hd_eig* e = lr.e;
     size_t smem = (size_t)e->r * 16 * sizeof(float);
     int gx = (int)std::min<int64_t>(ceil_div(n, 64), (int64_t)ctx->num_sms * 8);
@@ -535,13 +571,13 @@ int lr_expand(hd_ctx* ctx, const LowRank& lr, int op, float* out, const float* R
     }
     if (e->storage == HD_F32)
         k_lr_expand_simt<float><<<grid, 256, smem, ctx->stream>>>((const float*)e->U, e->scale, e->ldu, e->r, lr.H, op,
-                                                                  out, Rv, Pv, n, Bp, st);
+                                                                  out, Rv, Pv, n, Bp, st, gate);
     else if (e->storage == HD_BF16)
         k_lr_expand_simt<__nv_bfloat16><<<grid, 256, smem, ctx->stream>>>(
-            (const __nv_bfloat16*)e->U, e->scale, e->ldu, e->r, lr.H, op, out, Rv, Pv, n, Bp, st);
+            (const __nv_bfloat16*)e->U, e->scale, e->ldu, e->r, lr.H, op, out, Rv, Pv, n, Bp, st, gate);
     else
         k_lr_expand_simt<__nv_fp8_e4m3><<<grid, 256, smem, ctx->stream>>>(
-            (const __nv_fp8_e4m3*)e->U, e->scale, e->ldu, e->r, lr.H, op, out, Rv, Pv, n, Bp, st);
+            (const __nv_fp8_e4m3*)e->U, e->scale, e->ldu, e->r, lr.H, op, out, Rv, Pv, n, Bp, st, gate);
     HD_CHECK_LAUNCH(ctx);
     return HD_OK;
 }
@@ -561,9 +597,9 @@ static int pick_slab(int32_t Bp) {
     return 4;
 }
 
-VecLaunch vec_launch(hd_ctx* ctx, int64_t n, int32_t Bp) {
+VecLaunch vec_launch(hd_ctx* ctx, int64_t n, int32_t Bp, int S) {
     VecLaunch v;
-    v.S = pick_slab(Bp);
+    v.S = S > 0 ? S : pick_slab(Bp);
     int rpb = 256 / (v.S / 4);
     v.slabs = Bp / v.S;
     v.nblk = (int)std::min<int64_t>(ceil_div(n, rpb), (int64_t)ctx->num_sms * 8);
@@ -581,12 +617,49 @@ VecLaunch vec_launch(hd_ctx* ctx, int64_t n, int32_t Bp) {
         default: { constexpr int SS = 128; __VA_ARGS__; } break;  \
     }
 
+int tune_slab(hd_ctx* ctx, const hd_graph* g, int32_t Bp, const float* P, float* Q) {
+    auto it = g->slab_cache.find(Bp);
+    if (it != g->slab_cache.end()) return it->second;
+    if (getenv("HD_SLAB")) return g->slab_cache[Bp] = pick_slab(Bp);
+    int best = pick_slab(Bp);
+    float best_ms = 1e30f;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    for (int S : {8, 16, 32, 64, 128}) {
+        if (Bp % S || (S == 8 && Bp > 8 && g->n < 4096)) continue;
+        VecLaunch v = vec_launch(ctx, g->n, Bp, S);
+        dim3 grid(v.nblk, v.slabs);
+        float tot = 0.f;
+        for (int rep = 0; rep < 3; ++rep) {
+            cudaEventRecord(e0, ctx->stream);
+            HD_DISPATCH_S(S, (k_spmm<SS><<<grid, 256, 0, ctx->stream>>>(g->row_ptr, g->col, g->val, P, Q, g->n, Bp,
+                                                                         1.f, 1.f, nullptr, nullptr)));
+            cudaEventRecord(e1, ctx->stream);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep) tot += ms;
+        }
+        ctx->launches += 3;
+        if (tot < best_ms * 0.97f) {
+            best_ms = tot;
+            best = S;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaGetLastError();
+    g->slab_cache[Bp] = best;
+    return best;
+}
+
 int hd_spmm_apply(hd_ctx* ctx, const hd_graph* g, const float* P, float* Q, int32_t ld, int32_t B, float c1,
                   float c2) {
     VecLaunch v = vec_launch(ctx, g->n, ld);
     dim3 grid(v.nblk, v.slabs);
     HD_DISPATCH_S(v.S, (k_spmm<SS><<<grid, 256, 0, ctx->stream>>>(g->row_ptr, g->col, g->val, P, Q, g->n, ld, c1, c2,
-                                                                   nullptr)));
+                                                                   nullptr, nullptr)));
     HD_CHECK_LAUNCH(ctx);
     return HD_OK;
 }
@@ -620,24 +693,25 @@ int engine_iteration(Engine& S_, int (*after_update)(void*), void* arg) {
     const double* Cd = lr_on ? S_.lr.C : nullptr;
     int rc;
     if (eff_mode == HD_MODE_PCG) {
-        LAUNCH_VEC(k_spmm, g->row_ptr, g->col, g->val, S_.P, S_.Q, n, Bp, c1, c2, S_.part);
+        LAUNCH_VEC(k_spmm, g->row_ptr, g->col, g->val, S_.P, S_.Q, n, Bp, c1, c2, S_.part, S_.st);
         { HD_PROF(ctx, "scalar");
         k_fin_sigma<<<Bp, 128, 0, ctx->stream>>>(S_.part, S_.vl.nblk, Bp, S_.st, nullptr, nullptr, 0); }
         HD_CHECK_LAUNCH(ctx);
         LAUNCH_VEC(k_update, S_.X, S_.R, S_.P, S_.Q, n, Bp, S_.st, xs, S_.part);
     if (after_update && (rc = after_update(arg))) return rc;
-        if ((rc = lr_reduce(ctx, S_.lr, S_.R, n, Bp))) return rc;
+        if ((rc = lr_reduce(ctx, S_.lr, S_.R, n, Bp, S_.num_active))) return rc;
         if ((rc = lr_finish(ctx, S_.lr, Bp, S_.dcoef))) return rc;
         { HD_PROF(ctx, "scalar");
         HD_CUDA(ctx, cudaMemsetAsync(S_.num_active, 0, sizeof(int), ctx->stream));
         k_fin_rr<<<Bp, 128, 0, ctx->stream>>>(S_.part, S_.vl.nblk, Bp, S_.st, max_iter, Cd, S_.dcoef, r,
                                              S_.num_active); }
         HD_CHECK_LAUNCH(ctx);
-        if ((rc = lr_expand(ctx, S_.lr, EXP_DIRECTION, S_.P, S_.R, S_.P, n, Bp, S_.st))) return rc;
+        if ((rc = lr_expand(ctx, S_.lr, EXP_DIRECTION, S_.P, S_.R, S_.P, n, Bp, S_.st, S_.num_active))) return rc;
     } else {
-        LAUNCH_VEC(k_spmm, g->row_ptr, g->col, g->val, S_.P, S_.Q, n, Bp, c1, c2, S_.part);
+        LAUNCH_VEC(k_spmm, g->row_ptr, g->col, g->val, S_.P, S_.Q, n, Bp, c1, c2, S_.part, S_.st);
         if (lr_on) {
-            if ((rc = lr_expand(ctx, S_.lr, EXP_ADD_Q, S_.Q, nullptr, nullptr, n, Bp, S_.st))) return rc;
+            if ((rc = lr_expand(ctx, S_.lr, EXP_ADD_Q, S_.Q, nullptr, nullptr, n, Bp, S_.st, S_.num_active)))
+                return rc;
         }
         { HD_PROF(ctx, "scalar");
         k_fin_sigma<<<Bp, 128, 0, ctx->stream>>>(S_.part, S_.vl.nblk, Bp, S_.st, Cd,
@@ -652,7 +726,7 @@ int engine_iteration(Engine& S_, int (*after_update)(void*), void* arg) {
         HD_CHECK_LAUNCH(ctx);
         LAUNCH_VEC(k_direction, S_.P, S_.R, n, Bp, S_.st);
         if (lr_on) {
-            if ((rc = lr_reduce(ctx, S_.lr, S_.P, n, Bp))) return rc;
+            if ((rc = lr_reduce(ctx, S_.lr, S_.P, n, Bp, S_.num_active))) return rc;
             if ((rc = lr_finish(ctx, S_.lr, Bp, S_.opcoef))) return rc;
         }
     }
@@ -678,7 +752,7 @@ extern "C" int hd_query_batch(hd_ctx* ctx, const hd_graph* g, const hd_eig* eig,
     S_.n = g->n;
     S_.B = B;
     S_.Bp = (B + 3) / 4 * 4;
-    S_.vl = vec_launch(ctx, S_.n, S_.Bp);
+    S_.vl = vec_launch(ctx, S_.n, S_.Bp, pick_slab(S_.Bp));
     const int64_t n = S_.n;
     const int32_t Bp = S_.Bp;
     const bool lr_on = eig && eig->r > 0;
@@ -706,7 +780,7 @@ extern "C" int hd_query_batch(hd_ctx* ctx, const hd_graph* g, const hd_eig* eig,
     if (lr_on) nchunk = lr_use_tensor_cores(eig) ? lr_tc_nchunk(ctx, n) : simt_nchunk(ctx, n, rpad, Bp);
 
     size_t vec = (size_t)n * Bp * sizeof(float);
-    size_t bytes = 3 * ws_size(vec) + (x_direct ? 0 : ws_size(vec)) + ws_size((size_t)S_.vl.nblk * Bp * sizeof(float2)) +
+    size_t bytes = 3 * ws_size(vec) + (x_direct ? 0 : ws_size(vec)) + ws_size((size_t)ctx->num_sms * 8 * Bp * sizeof(float2)) +
                    ws_size(Bp * sizeof(ColState)) + ws_size(64) + ws_size((B + 1) * 4) + 2 * ws_size(nnz_y * 4 + 4) +
                    ws_size(B * 4);
     if (lr_on)
@@ -720,7 +794,7 @@ extern "C" int hd_query_batch(hd_ctx* ctx, const hd_graph* g, const hd_eig* eig,
     S_.P = cv.take<float>((size_t)n * Bp);
     S_.Q = cv.take<float>((size_t)n * Bp);
     S_.X = x_direct ? X : cv.take<float>((size_t)n * Bp);
-    S_.part = cv.take<float2>((size_t)S_.vl.nblk * Bp);
+    S_.part = cv.take<float2>((size_t)ctx->num_sms * 8 * Bp);
     S_.st = cv.take<ColState>(Bp);
     S_.num_active = cv.take<int>(16);
     S_.err = S_.num_active + 1;
@@ -770,6 +844,7 @@ extern "C" int hd_query_batch(hd_ctx* ctx, const hd_graph* g, const hd_eig* eig,
     }
 
     // ---------------- setup
+    S_.vl = vec_launch(ctx, n, Bp, tune_slab(ctx, g, Bp, S_.P, S_.Q));
     const int eff_mode = lr_on ? mode : HD_MODE_PAPER;
     const double a = alpha;
     float c1, c2, xs = 1.0f;

@@ -40,14 +40,16 @@ struct LowRank {
     int32_t Bp16;
 };
 
-int lr_reduce(hd_ctx* ctx, const LowRank& lr, const float* V, int64_t n, int32_t Bp);
+// `gate` (device int, may be null): the kernels return at once when it is 0
+// (no column active), so iterations past convergence cost only their launch.
+int lr_reduce(hd_ctx* ctx, const LowRank& lr, const float* V, int64_t n, int32_t Bp, const int* gate = nullptr);
 int lr_finish(hd_ctx* ctx, const LowRank& lr, int32_t Bp, const double* coef);
 int lr_expand(hd_ctx* ctx, const LowRank& lr, int op, float* out, const float* Rv, const float* Pv, int64_t n,
-              int32_t Bp, const ColState* st);
+              int32_t Bp, const ColState* st, const int* gate = nullptr);
 bool lr_use_tensor_cores(const hd_eig* e);
-int lr_tc_reduce(hd_ctx* ctx, const LowRank& lr, const float* V, int64_t n, int32_t Bp);
+int lr_tc_reduce(hd_ctx* ctx, const LowRank& lr, const float* V, int64_t n, int32_t Bp, const int* gate);
 int lr_tc_expand(hd_ctx* ctx, const LowRank& lr, int op, float* out, const float* Rv, const float* Pv, int64_t n,
-                 int32_t Bp, const ColState* st);
+                 int32_t Bp, const ColState* st, const int* gate);
 int lr_tc_nchunk(hd_ctx* ctx, int64_t n);
 
 // ------------------------------------------------------------------ iteration engine
@@ -77,6 +79,9 @@ struct Engine {
     int32_t max_iter = 0;
 };
 
-VecLaunch vec_launch(hd_ctx* ctx, int64_t n, int32_t Bp);
+VecLaunch vec_launch(hd_ctx* ctx, int64_t n, int32_t Bp, int S = 0);
+// Column-slab width of the SpMM for this graph and batch width: measured once
+// per (graph, Bp) over the widths dividing Bp (HD_SLAB overrides).
+int tune_slab(hd_ctx* ctx, const hd_graph* g, int32_t Bp, const float* P, float* Q);
 int simt_nchunk(hd_ctx* ctx, int64_t n, int rpad, int Bp);
 int engine_iteration(Engine& E, int (*after_update)(void*), void* arg);
