@@ -18,30 +18,31 @@ from __future__ import annotations
 import numpy as np
 import scipy.sparse as sp
 
-CHUNK = 2048
+CHUNK = 512
 
 
 def knn_rows(X: np.ndarray, rows: np.ndarray, k: int) -> tuple[np.ndarray, np.ndarray]:
     """Top-k neighbours (by dot product, self excluded) of the given rows.
 
     Returns (idx, sim), both (len(rows), k), ordered by decreasing similarity
-    with ties going to the smaller index.  FP64 throughout.
+    with ties going to the smaller index.  FP64 throughout.  The k-th largest
+    similarity of a row is found first; every entry at least that large is a
+    candidate, and the candidates are ordered by (-s, index) exactly.
     """
     X = np.asarray(X, dtype=np.float64)
     rows = np.asarray(rows, dtype=np.int64)
-    n = X.shape[0]
     idx = np.empty((rows.size, k), dtype=np.int64)
     sim = np.empty((rows.size, k), dtype=np.float64)
-    ids = np.arange(n)
     for s in range(0, rows.size, CHUNK):
         rr = rows[s:s + CHUNK]
         S = X[rr] @ X.T
-        for t, i in enumerate(rr):
-            srow = S[t].copy()
-            srow[i] = -np.inf                      # no self loop
-            order = np.lexsort((ids, -srow))       # decreasing s, then smaller id
-            idx[s + t] = order[:k]
-            sim[s + t] = srow[order[:k]]
+        S[np.arange(rr.size), rr] = -np.inf          # no self loop
+        kth = -np.partition(-S, k - 1, axis=1)[:, k - 1]
+        for t in range(rr.size):
+            cand = np.nonzero(S[t] >= kth[t])[0]
+            order = cand[np.lexsort((cand, -S[t, cand]))][:k]   # decreasing s, then smaller id
+            idx[s + t] = order
+            sim[s + t] = S[t, order]
     return idx, sim
 
 

@@ -314,7 +314,8 @@ extern "C" int hd_eigendecompose(hd_ctx* ctx, const hd_graph* g, int32_t r, int3
     std::vector<double> th(m), res(k), Th;
     bool converged = false;
     for (int restart = 0;; ++restart) {
-        // ---- grow the basis to m columns; the last remainder goes to Q[:, m : m + b]
+        // ---- grow the basis while a block fits in m columns; the orthogonalised
+        // remainder of the last product stays in the next slot Q[:, cols : cols + b]
         while (true) {
             double* V = L.Q + (size_t)(cols - L.b) * n;
             double* Wn = L.Q + (size_t)cols * n;  // next block slot
@@ -329,18 +330,21 @@ extern "C" int hd_eigendecompose(hd_ctx* ctx, const hd_graph* g, int32_t r, int3
             TRY(new_block(L, cols, Wn, seed, salt++));
             cols += L.b;
         }
-        // ---- Rayleigh-Ritz on T (m x m)
-        HD_CUDA(ctx, cudaMemcpyAsync(L.S, L.T, (size_t)m * m * 8, cudaMemcpyDeviceToDevice, ctx->stream));
-        SL(cusolverDnDsyevd(L.h.sol, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, m, L.S, m, L.theta, L.work,
+        // ---- Rayleigh-Ritz on the leading mc x mc block of T (mc = basis size reached)
+        const int mc = cols;
+        HD_CUDA(ctx, cudaMemcpy2DAsync(L.S, (size_t)mc * 8, L.T, (size_t)m * 8, (size_t)mc * 8, mc,
+                                       cudaMemcpyDeviceToDevice, ctx->stream));
+        SL(cusolverDnDsyevd(L.h.sol, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, mc, L.S, mc, L.theta, L.work,
                             L.lwork, L.info));
-        HD_CUDA(ctx, cudaMemcpyAsync(th.data(), L.theta, (size_t)m * 8, cudaMemcpyDeviceToHost, ctx->stream));
+        HD_CUDA(ctx, cudaMemcpyAsync(th.data(), L.theta, (size_t)mc * 8, cudaMemcpyDeviceToHost, ctx->stream));
         // eigenvalues ascending: the top k are the last k columns of S, taken in reverse
-        k_top_cols<<<ceil_div((int64_t)m * k, 256), 256, 0, ctx->stream>>>(L.S, m, k, L.Sd);
+        k_top_cols<<<ceil_div((int64_t)mc * k, 256), 256, 0, ctx->stream>>>(L.S, mc, k, L.Sd);
         HD_CHECK_LAUNCH(ctx);
-        BL(cublasDgemm(L.h.blas, CUBLAS_OP_N, CUBLAS_OP_N, (int)n, k, m, &one, L.Q, (int)n, L.Sd, m, &zero, L.Y, (int)n));
+        BL(cublasDgemm(L.h.blas, CUBLAS_OP_N, CUBLAS_OP_N, (int)n, k, mc, &one, L.Q, (int)n, L.Sd, mc, &zero, L.Y,
+                       (int)n));
         HD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
         std::vector<double> thk(k);
-        for (int t = 0; t < k; ++t) thk[t] = th[m - 1 - t];
+        for (int t = 0; t < k; ++t) thk[t] = th[mc - 1 - t];
         HD_CUDA(ctx, cudaMemcpyAsync(L.theta, thk.data(), (size_t)k * 8, cudaMemcpyHostToDevice, ctx->stream));
         // residuals with one SpMM of the Ritz block
         TRY(spmm_block(L, L.Y, k, L.WY));
@@ -353,6 +357,9 @@ extern "C" int hd_eigendecompose(hd_ctx* ctx, const hd_graph* g, int32_t r, int3
         double worst = 0.0;
         for (int t = 0; t < r; ++t) worst = std::max(worst, std::sqrt(res[t]));
         converged = worst <= tol;
+        if (getenv("HD_LANCZOS_TRACE"))
+            fprintf(stderr, "lanczos restart %d cols %d worst %.3e theta %.8f %.8f %.8f\n", restart, cols, worst,
+                    thk[0], thk[1], thk[std::min(r, k) - 1]);
         if (converged || restart >= max_restarts) {
             for (int t = 0; t < r; ++t) {
                 if (eigvals_out) eigvals_out[t] = thk[t];
@@ -373,7 +380,7 @@ extern "C" int hd_eigendecompose(hd_ctx* ctx, const hd_graph* g, int32_t r, int3
             return converged ? HD_OK : hd_fail(ctx, HD_ERR_NOT_CONVERGED, "max residual %.3e > tol %.1e", worst, tol);
         }
         // ---- thick restart: Q = [Y (k), remainder (b)], T = Q^T W Q for the first k + b columns
-        double* rem = L.Q + (size_t)m * n;                   // remainder block (already orthogonal to Q[:, :m])
+        double* rem = L.Q + (size_t)mc * n;                  // remainder block (already orthogonal to Q[:, :mc])
         HD_CUDA(ctx, cudaMemcpyAsync(L.W, rem, (size_t)n * L.b * 8, cudaMemcpyDeviceToDevice, ctx->stream));
         HD_CUDA(ctx, cudaMemcpyAsync(L.Q, L.Y, (size_t)n * k * 8, cudaMemcpyDeviceToDevice, ctx->stream));
         double* nb = L.Q + (size_t)k * n;
