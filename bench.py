@@ -54,6 +54,8 @@ def parse():
                     help="Poisson arrival rates (req/s) of the serving leg; empty to skip")
     ap.add_argument("--serve-requests", type=int, default=1500)
     ap.add_argument("--serve-slots", type=int, default=128)
+    ap.add_argument("--sweep", type=int, default=1, help="run the storage / rank / batch sweep")
+    ap.add_argument("--sweep-batches", default="1,16,256")
     return ap.parse_args()
 
 
@@ -127,33 +129,50 @@ def build_workload(args, ctx, rank):
     g = hd.build_graph(ctx, Xt, c.k, c.gamma)
     torch.cuda.synchronize()
     t_graph = time.time() - t0
-    # queries: one calibration batch and the timed batch (different draws)
-    nq = 2 * args.batch
+    # queries: one calibration batch and the timed batch (different draws), sized
+    # for the largest batch of the sweep
+    bmax = max([args.batch] + ([int(b) for b in args.sweep_batches.split(",") if b] if args.sweep else []))
+    nq = 2 * bmax
     Qv = synth.queries(c.seed + 1000 * rank, nq, d, c.ncl, c.kappa_lo, c.kappa_hi, c.sizes, c.zipf_s)
     Qt = torch.from_numpy(Qv).to(Xt.dtype).cuda()
     yp, yi, yv = hd.observe(ctx, Xt, Qt, c.k_y, c.gamma)
     del Qt
+    yall = (yp, yi, yv)
     B = args.batch
-    cal = (yp[:B + 1].copy(), yi[:yp[B]].copy(), yv[:yp[B]].copy())
-    off = yp[B]
-    tim = ((yp[B:] - off).astype(np.int32), yi[off:].copy(), yv[off:].copy())
+    cal, tim = split_batches(yall, B, bmax)
     t0 = time.time()
-    eig, lam, res, conv = None, None, None, None
+    eig, lam, res, conv, U32 = None, None, None, None, None
     if args.r > 0:
-        eig, lam, res, conv = hd.eigendecompose(ctx, g, args.r, block=32, tol=1e-5, max_restarts=args.restarts,
-                                                storage=args.storage)
+        # fp32 Ritz vectors once; each storage format is made from them
+        e32, lam, res, conv = hd.eigendecompose(ctx, g, args.r, block=32, tol=1e-5, max_restarts=args.restarts,
+                                                storage="f32")
+        _, U32 = e32.export()
+        e32.close()
+        eig = hd.eig_from_host(ctx, g, lam, U32, args.storage)
     torch.cuda.synchronize()
     t_eig = time.time() - t0
-    return {"cfg": c, "n": n, "d": d, "g": g, "Xt": Xt, "cal": cal, "tim": tim, "eig": eig, "lam": lam, "res": res,
-            "conv": conv, "t_gen": t_gen, "t_graph": t_graph, "t_eig": t_eig}
+    return {"cfg": c, "n": n, "d": d, "g": g, "Xt": Xt, "cal": cal, "tim": tim, "yall": yall, "bmax": bmax,
+            "eig": eig, "lam": lam, "U32": U32, "res": res, "conv": conv, "t_gen": t_gen, "t_graph": t_graph,
+            "t_eig": t_eig}
 
 
-def calibrate(ctx, wl, eig, mode, alpha):
+def split_batches(yall, B, bmax):
+    """Calibration batch = queries [0, B), timed batch = queries [bmax, bmax + B)."""
+    yp, yi, yv = yall
+
+    def take(q0):
+        s, e = yp[q0], yp[q0 + B]
+        return ((yp[q0:q0 + B + 1] - s).astype(np.int32), yi[s:e].copy(), yv[s:e].copy())
+
+    return take(0), take(bmax)
+
+
+def calibrate(ctx, wl, eig, mode, alpha, cal=None):
     """Loosest ladder tolerance whose max rel-l2 versus a tightly converged
     reference of the same batch is <= TOL_REL / 2."""
     import paper_1807_08692_gb300 as hd
     g = wl["g"]
-    yp, yi, yv = wl["cal"]
+    yp, yi, yv = wl["cal"] if cal is None else cal
     ref, *_ = hd.query_batch(ctx, g, wl["eig"] if wl["eig"] is not None else None, "pcg", yp, yi, yv, alpha,
                              1e-7, 2000)
     refn = ref.norm(dim=0)
@@ -169,11 +188,11 @@ def calibrate(ctx, wl, eig, mode, alpha):
 FAMILIES = ["spmm", "update", "direction", "lr_reduce", "lr_expand", "scalar", "rank"]
 
 
-def time_leg(ctx, wl, eig, mode, tol, alpha, K, W, B, topk, profile):
+def time_leg(ctx, wl, eig, mode, tol, alpha, K, W, B, topk, profile, tim=None):
     import torch
     import paper_1807_08692_gb300 as hd
     g = wl["g"]
-    yp, yi, yv = wl["tim"]
+    yp, yi, yv = wl["tim"] if tim is None else tim
     # inputs resident in HBM
     ypd = torch.from_numpy(yp).cuda()
     yid = torch.from_numpy(yi).cuda()
@@ -190,7 +209,7 @@ def time_leg(ctx, wl, eig, mode, tol, alpha, K, W, B, topk, profile):
     def step():
         hd.query_batch(ctx, g, eig, mode, ypd, yid, yvd, alpha, told, 2000, X=X, ldx=X.shape[1], iters=itd,
                        relres=rrd, status=std)
-        hd.rank(ctx, X[:, :B] if X.shape[1] == B else X, Kh, topk, idx=idx, score=sc)
+        hd.rank(ctx, X[:, :B], Kh, topk, idx=idx, score=sc)
 
     for _ in range(W):
         step()
@@ -238,7 +257,7 @@ def e2e_leg(ctx, wl, eig, mode, tol, alpha, K, B, topk):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         hd.query_batch(ctx, g, eig, mode, yp, yi, yv, alpha, tolh, 2000, X=X, ldx=X.shape[1])
-        hd.rank(ctx, X, Kh, topk, idx=idx, score=sc)
+        hd.rank(ctx, X[:, :B], Kh, topk, idx=idx, score=sc)
         torch.cuda.synchronize()
         if k:
             times.append(time.perf_counter() - t0)
@@ -278,7 +297,9 @@ def cpu_oracle(wl, args, alpha, tol, columns):
     W = sp.csr_matrix((val.astype(np.float64), col, rp), shape=(n, n))
     yp, yi, yv = wl["tim"]
     Y = observe.dense(n, yp[:columns + 1], yi[:yp[columns]], yv[:yp[columns]].astype(np.float64))
-    if wl["eig"] is not None:
+    if wl.get("U32") is not None:
+        lam, U = wl["lam"], wl["U32"].astype(np.float64)
+    elif wl["eig"] is not None:
         lam, U = wl["eig"].export()
         U = U.astype(np.float64)
     else:
@@ -287,6 +308,41 @@ def cpu_oracle(wl, args, alpha, tol, columns):
     x, iters = diffusion.hybrid_pcg(W, U, lam, Y, alpha, tol, 2000)
     dt = time.perf_counter() - t0
     return dt, iters
+
+
+# ------------------------------------------------------------------ sweep (storage, rank, batch)
+def sweep_leg(ctx, wl, args, alpha):
+    """Short timed legs over the recipe's knobs, each at its own calibrated
+    tolerance: U storage (f32 / bf16 / fp8 at r), a smaller rank, the paper's
+    form with bf16 U, and batch sizes."""
+    import paper_1807_08692_gb300 as hd
+    out = []
+    g, lam, U32 = wl["g"], wl["lam"], wl["U32"]
+
+    def run(label, eig, mode, B, **kw):
+        cal, tim = split_batches(wl["yall"], B, wl["bmax"])
+        tol, err, _ = calibrate(ctx, wl, eig, mode, alpha, cal=cal)
+        leg = time_leg(ctx, wl, eig, mode, tol, alpha, 5, 2, B, args.topk, False, tim=tim)
+        ms = leg["total_ms"] / 5
+        out.append({"leg": label, "mode": mode, "B": B, "tol": tol, "calib_rel_err": err,
+                    "meets_1e-4": bool(err is not None and err <= TOL_REL), "iters_max": int(leg["iters"].max()),
+                    "ms_per_batch": round(ms, 3), "qps": round(B / ms * 1e3, 1), **kw})
+
+    if U32 is not None:
+        r = U32.shape[1]
+        for st in ("f32", "fp8"):
+            e = hd.eig_from_host(ctx, g, lam, U32, st)
+            run(f"pcg r={r} {st}", e, "pcg", args.batch, r=r, storage=st)
+            e.close()
+        r2 = min(50, r)
+        e = hd.eig_from_host(ctx, g, lam[:r2], np.ascontiguousarray(U32[:, :r2]), "bf16")
+        run(f"pcg r={r2} bf16", e, "pcg", args.batch, r=r2, storage="bf16")
+        e.close()
+        run(f"paper r={r} {args.storage}", wl["eig"], "paper", args.batch, r=r, storage=args.storage)
+    for b in [int(x) for x in args.sweep_batches.split(",") if x]:
+        run(f"{args.mode} r={args.r} B={b}", wl["eig"], args.mode, b, r=args.r, storage=args.storage)
+        run(f"cg r=0 B={b}", None, "paper", b, r=0, storage=None)
+    return out
 
 
 # ------------------------------------------------------------------ serving (continuous batching)
@@ -405,6 +461,8 @@ def main():
         es, h2d, d2h = e2e_leg(ctx, wl, eig, args.mode, tol_h, alpha, args.steps, B, args.topk)
         e2e = {"value": B * args.steps / es * world, "unit": "queries/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h)}
+    # ---- sweep over storage, rank and batch
+    sweep = sweep_leg(ctx, wl, args, alpha) if (args.sweep and not args.quick) else None
     # ---- serving: continuous batching under Poisson load
     serving = None
     rates = [float(x) for x in args.serve_rates.split(",") if x.strip()]
@@ -456,7 +514,7 @@ def main():
                    "setup_s": {"gen": round(wl["t_gen"], 1), "graph": round(wl["t_graph"], 1),
                                "eig": round(wl["t_eig"], 1)}},
         "p50_ms": round(float(np.percentile(hyb["ms"], 50)), 4), "p99_ms": round(float(np.percentile(hyb["ms"], 99)), 4),
-        "cg_r0": cg, "serving": serving, "e2e": e2e, "gpu_launches": int(hyb["launches"]), "roofline": roofline, "cpu_baseline": cpu,
+        "cg_r0": cg, "sweep": sweep, "serving": serving, "e2e": e2e, "gpu_launches": int(hyb["launches"]), "roofline": roofline, "cpu_baseline": cpu,
         "clocks": clocks, "wall_s_timed": round(t_wall, 3),
     }
     if rank == 0:

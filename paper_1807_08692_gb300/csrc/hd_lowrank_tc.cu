@@ -194,13 +194,33 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
     } else {
         // epilogue: warps 2-9; lane quarter (warp % 4) gives the TMEM lanes (rows),
-        // the two warps of a quarter split the 16-column chunks
+        // the two warps of a quarter split the 16-column chunks.  The global
+        // operands of a tile's first two chunks are loaded one tile ahead, so
+        // their latency overlaps the MMAs of that tile.
         const int quarter = warp & 3;
         const int half = (warp - 2) >> 2;
         const int rloc = quarter * 32 + lane;
         const int nch = a.Nc / 16;
         const int nh = (nch + 1) / 2;
         const int cb = half ? nh : 0, ce = half ? nch : nh;
+        float4 g1[2][4], g2[2][4];
+        auto load_ops = [&](int64_t row_, int c0_) {
+#pragma unroll
+            for (int u = 0; u < 2; ++u)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int j = a.c0 + (c0_ + u) * 16 + 4 * q;
+                    g1[u][q] = g2[u][q] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (row_ >= a.n || c0_ + u >= ce || j >= a.Bp || a.op == EXP_SET_X) continue;
+                    if (a.op == EXP_DIRECTION) {
+                        g1[u][q] = *reinterpret_cast<const float4*>(a.R + row_ * a.Bp + j);
+                        g2[u][q] = *reinterpret_cast<const float4*>(a.P + row_ * a.Bp + j);
+                    } else {
+                        g1[u][q] = *reinterpret_cast<const float4*>(a.out + row_ * a.Bp + j);
+                    }
+                }
+        };
+        if ((int)blockIdx.x < ntiles && cb < ce) load_ops((int64_t)blockIdx.x * BM + rloc, cb);
         uint32_t tcount = 0;
         bool ok = true;
         for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tcount) {
@@ -213,22 +233,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             const int64_t row = (int64_t)t * BM + rloc;
             const bool live = row < a.n;
             for (int c0 = cb; c0 < ce; c0 += 2) {
-                // issue the global loads of two chunks before touching TMEM
-                float4 g1[2][4], g2[2][4];
-#pragma unroll
-                for (int u = 0; u < 2; ++u)
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int j = a.c0 + (c0 + u) * 16 + 4 * q;
-                        g1[u][q] = g2[u][q] = make_float4(0.f, 0.f, 0.f, 0.f);
-                        if (!live || c0 + u >= ce || j >= a.Bp || a.op == EXP_SET_X) continue;
-                        if (a.op == EXP_DIRECTION) {
-                            g1[u][q] = *reinterpret_cast<const float4*>(a.R + row * a.Bp + j);
-                            g2[u][q] = *reinterpret_cast<const float4*>(a.P + row * a.Bp + j);
-                        } else {
-                            g1[u][q] = *reinterpret_cast<const float4*>(a.out + row * a.Bp + j);
-                        }
-                    }
+                if (c0 != cb) load_ops(row, c0);
 #pragma unroll
                 for (int u = 0; u < 2; ++u) {
                     if (c0 + u >= ce) break;
@@ -265,6 +270,8 @@ __global__ void __launch_bounds__(THREADS, 1)
             }
             tc::fence_before_sync();
             tc::mbar_arrive(&acc_empty[ab]);
+            const int tn = t + gridDim.x;
+            if (tn < ntiles && cb < ce) load_ops((int64_t)tn * BM + rloc, cb);
         }
         if (!ok) {
             *abort_flag = 1;
@@ -416,6 +423,24 @@ __global__ void __launch_bounds__(THREADS, 1)
         bool ok = true;
         const int cq_n = a.Nc / 4;
         const int total = BM * cq_n;
+        // V of the next tile is loaded into registers while the current one is
+        // converted (one batch when a tile fits EPI x 8 float4, i.e. Nc <= 64)
+        const bool one_batch = total <= EPI * 8;
+        float4 v[8];
+        auto load_tile = [&](int tl_, int base_) {
+            const int64_t row0_ = (t0 + tl_) * BM;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int e = base_ + u * EPI;
+                v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (e < total) {
+                    const int rr = e / cq_n, j = a.c0 + 4 * (e % cq_n);
+                    const int64_t i = row0_ + rr;
+                    if (i < a.n && j < a.Bp) v[u] = *reinterpret_cast<const float4*>(a.V + i * a.Bp + j);
+                }
+            }
+        };
+        if (ntl > 0 && one_batch) load_tile(0, tid);
         for (int tl = 0; tl < ntl && ok; ++tl) {
             const int buf = tl & 1;
             if (!tc::mbar_wait(&bempty[buf], ((tl >> 1) & 1) ^ 1, abort_flag)) {
@@ -424,26 +449,19 @@ __global__ void __launch_bounds__(THREADS, 1)
             }
             uint8_t* bh = Bs + (2 * buf) * bterm;
             uint8_t* bl = Bs + (2 * buf + 1) * bterm;
-            const int64_t row0 = (t0 + tl) * BM;
             for (int base = tid; base < total; base += EPI * 8) {
-                float4 v[8];
+                if (!one_batch) load_tile(tl, base);
+                float4 cur[8];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int e = base + u * EPI;
-                    v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (e < total) {
-                        const int rr = e / cq_n, j = a.c0 + 4 * (e % cq_n);
-                        const int64_t i = row0 + rr;
-                        if (i < a.n && j < a.Bp) v[u] = *reinterpret_cast<const float4*>(a.V + i * a.Bp + j);
-                    }
-                }
+                for (int u = 0; u < 8; ++u) cur[u] = v[u];
+                if (one_batch && tl + 1 < ntl) load_tile(tl + 1, tid);
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
                     const int e = base + u * EPI;
                     if (e >= total) break;
                     const int rr = e / cq_n, jl = 4 * (e % cq_n);
                     __nv_bfloat16 h[4], l[4];
-                    const float vv[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+                    const float vv[4] = {cur[u].x, cur[u].y, cur[u].z, cur[u].w};
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
                         h[q] = __float2bfloat16_rn(vv[q]);

@@ -355,6 +355,9 @@ def rank(ctx: Context, X, K, Kmax: int | None = None, pool: int = 0, n: int | No
     if idx is None:
         idx = np.empty((B, Kmax), np.int32)
         score = np.empty((B, Kmax), np.float32)
+    size = (lambda a: a.size if isinstance(a, np.ndarray) else a.numel())
+    if size(idx) < B * Kmax or size(score) < B * Kmax:
+        raise ValueError("idx/score buffers must hold B x Kmax entries")
     ctx.check(lib().hd_rank(ctx.handle, _ptr(X), n, B, ldx, _ptr(K), Kmax, pool, _ptr(idx), _ptr(score)), "hd_rank")
     return idx, score
 
