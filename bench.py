@@ -222,18 +222,20 @@ def time_leg(ctx, wl, eig, mode, tol, alpha, K, W, B, topk, profile, tim=None):
     s = torch.cuda.current_stream()
     evs = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push(f"timed_{mode}_r{0 if eig is None else eig.r}")
     evs[0].record(s)
     for k in range(K):
         step()
         evs[k + 1].record(s)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     launches = ctx.launches() - l0
     per = [evs[k].elapsed_time(evs[k + 1]) for k in range(K)]
     fam = {}
     if profile:
         for f in FAMILIES:
-            cnt, ms = ctx.profile_read(f)
-            fam[f] = (cnt, ms)
+            cnt, ms, busy = ctx.profile_read(f, busy=True)
+            fam[f] = (cnt, ms, busy)
         ctx.profile(False)
     total_ms = evs[0].elapsed_time(evs[K])
     return {"ms": per, "total_ms": total_ms, "launches": launches, "fam": fam,
@@ -264,6 +266,27 @@ def e2e_leg(ctx, wl, eig, mode, tol, alpha, K, B, topk):
     h2d = yp.nbytes + yi.nbytes + yv.nbytes + tolh.nbytes
     d2h = idx.nbytes + sc.nbytes + 3 * 4 * B
     return float(np.sum(times)), h2d, d2h
+
+
+# DRAM bytes per launch of the SpMM measured by ncu (profiles/spmm_n1m_b64.md):
+# k_spmm<64> on a 1M-node k=50 graph (d=256 descriptors, nnz 62,097,728), B=64.
+# Scaled to another graph by nnz (the gathered rows dominate); reported only
+# while the kernel source still hashes to the value the counters were taken on.
+SPMM_NCU = {"dram_bytes": None, "nnz": 62097728, "n": 1000000, "B": 64, "src_sha1": None}
+
+
+def spmm_source_sha1():
+    import hashlib
+    src = open(os.path.join(ROOT, "paper_1807_08692_gb300", "csrc", "hd_solve.cu")).read()
+    a = src.index("__global__ void __launch_bounds__(256) k_spmm(")
+    b = src.index("\n}\n", a)
+    return hashlib.sha1(src[a:b].encode()).hexdigest()
+
+
+def spmm_traffic(wl, B):
+    if SPMM_NCU["dram_bytes"] is None or SPMM_NCU["src_sha1"] != spmm_source_sha1() or B != SPMM_NCU["B"]:
+        return None
+    return int(SPMM_NCU["dram_bytes"] * wl["g"].nnz / SPMM_NCU["nnz"])
 
 
 def algorithmic_bytes(wl, B, eig):
@@ -472,8 +495,8 @@ def main():
     ab = algorithmic_bytes(wl, B, eig)
     fam = hyb["fam"]
     dom = max((f for f in fam if f in ab), key=lambda f: fam[f][1])
-    cnt, ms = fam[dom]
-    avg_s = ms / 1e3 / max(cnt, 1)
+    cnt, ms, busy = fam[dom]
+    avg_s = ms / 1e3 / max(busy, 1)  # per launch that did work (idle launches return at once)
     peaks = {}
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -482,13 +505,19 @@ def main():
         pass
     peak = float(peaks.get("hbm_gbs", 6800.0))
     achieved = ab[dom] / avg_s / 1e9
+    nnz = wl["g"].nnz
+    gather = nnz * ((B + 3) // 4 * 4) * 4 + 8 * nnz + 4 * (wl["n"] + 1) + 2 * wl["n"] * ((B + 3) // 4 * 4) * 4
+    spmm_ms = fam["spmm"][1] / max(fam["spmm"][2], 1)
     roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": None,
+                "frac": round(achieved / peak, 4), "traffic": spmm_traffic(wl, B) if dom == "spmm" else None,
+                "spmm_gather_bytes_per_launch": int(gather),
+                "spmm_gather_gbs": round(gather / (spmm_ms / 1e3) / 1e9, 1) if spmm_ms > 0 else None,
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
                 "algorithmic_bytes_per_launch": int(ab[dom]), "avg_launch_ms": round(avg_s * 1e3, 4),
                 "share_of_step": round(ms / hyb["total_ms"], 4),
                 "families_ms": {f: round(v[1], 3) for f, v in fam.items()},
-                "families_launches": {f: v[0] for f, v in fam.items()}}
+                "families_launches": {f: v[0] for f, v in fam.items()},
+                "families_busy_launches": {f: v[2] for f, v in fam.items()}}
     # ---- CPU baseline: the oracle on host cores, bounded sample
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:

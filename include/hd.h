@@ -87,9 +87,13 @@ int hd_num_sms(const hd_ctx* ctx);
  * hd_profile_read synchronises the stream and returns, for the kernel family
  * `name` ("spmm", "update", "direction", "lr_reduce", "lr_expand", "scalar",
  * "rank", "knn"), the number of launches and their summed duration since the
- * last read, then clears that family. */
+ * last read, then clears that family.  busy_launches (may be NULL) counts the
+ * launches that took at least 5% of the family's longest one: kernels of an
+ * iteration return at once when none of their columns is active, and those
+ * idle launches are left out of it. */
 int hd_profile_enable(hd_ctx* ctx, int on);
-int hd_profile_read(hd_ctx* ctx, const char* name, int64_t* launches, double* total_ms);
+int hd_profile_read(hd_ctx* ctx, const char* name, int64_t* launches, double* total_ms,
+                    int64_t* busy_launches);
 
 /* ---- graph (Sec. 3; Sec. 5.1) -------------------------------------------- */
 

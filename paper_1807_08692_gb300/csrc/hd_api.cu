@@ -137,25 +137,31 @@ int hd_profile_enable(hd_ctx* ctx, int on) {
     return HD_OK;
 }
 
-int hd_profile_read(hd_ctx* ctx, const char* name, int64_t* launches, double* total_ms) {
+int hd_profile_read(hd_ctx* ctx, const char* name, int64_t* launches, double* total_ms, int64_t* busy_launches) {
     if (!ctx || !name) return HD_ERR_INVALID_ARG;
     HD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    double tot = 0.0;
-    int64_t cnt = 0;
+    double tot = 0.0, mx = 0.0;
+    int64_t cnt = 0, busy = 0;
+    std::vector<float> each;
     auto it = ctx->prof_ev.find(name);
     if (it != ctx->prof_ev.end()) {
         for (auto& pr : it->second) {
             float ms = 0.0f;
-            if (cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess) tot += ms;
+            if (cudaEventElapsedTime(&ms, pr.first, pr.second) != cudaSuccess) ms = 0.0f;
+            each.push_back(ms);
+            tot += ms;
+            mx = ms > mx ? ms : mx;
             ++cnt;
             ctx->ev_pool.push_back(pr.first);
             ctx->ev_pool.push_back(pr.second);
         }
         it->second.clear();
     }
+    for (float ms : each) busy += ms >= 0.05 * mx;
     cudaGetLastError();
     if (launches) *launches = cnt;
     if (total_ms) *total_ms = tot;
+    if (busy_launches) *busy_launches = busy;
     return HD_OK;
 }
 int64_t hd_launch_count(const hd_ctx* ctx) { return ctx ? ctx->launches : 0; }

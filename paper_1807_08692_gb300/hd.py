@@ -42,7 +42,7 @@ _SIGS = {
     "hd_launch_count": (i64, [vp]),
     "hd_num_sms": (C.c_int, [vp]),
     "hd_profile_enable": (C.c_int, [vp, C.c_int]),
-    "hd_profile_read": (C.c_int, [vp, C.c_char_p, C.POINTER(i64), C.POINTER(f64)]),
+    "hd_profile_read": (C.c_int, [vp, C.c_char_p, C.POINTER(i64), C.POINTER(f64), C.POINTER(i64)]),
     "hd_graph_from_csr": (C.c_int, [vp, i64, i64, vp, vp, vp, C.c_int, C.POINTER(vp)]),
     "hd_build_graph": (C.c_int, [vp, vp, i64, i32, C.c_int, i32, f32, C.c_int, C.POINTER(vp)]),
     "hd_knn": (C.c_int, [vp, vp, i64, i32, C.c_int, vp, i64, i32, C.c_int, vp, vp]),
@@ -151,11 +151,12 @@ class Context:
     def profile(self, on: bool = True):
         self.check(lib().hd_profile_enable(self._h, int(on)), "hd_profile_enable")
 
-    def profile_read(self, name: str):
-        """(launches, total_ms) of a kernel family since the last read."""
-        cnt, ms = i64(), f64()
-        self.check(lib().hd_profile_read(self._h, name.encode(), C.byref(cnt), C.byref(ms)), "hd_profile_read")
-        return cnt.value, ms.value
+    def profile_read(self, name: str, busy: bool = False):
+        """(launches, total_ms[, busy_launches]) of a kernel family since the last read."""
+        cnt, ms, b = i64(), f64(), i64()
+        self.check(lib().hd_profile_read(self._h, name.encode(), C.byref(cnt), C.byref(ms), C.byref(b)),
+                   "hd_profile_read")
+        return (cnt.value, ms.value, b.value) if busy else (cnt.value, ms.value)
 
     def close(self):
         if self._h:
