@@ -272,7 +272,8 @@ def e2e_leg(ctx, wl, eig, mode, tol, alpha, K, B, topk):
 # k_spmm<64> on a 1M-node k=50 graph (d=256 descriptors, nnz 62,097,728), B=64.
 # Scaled to another graph by nnz (the gathered rows dominate); reported only
 # while the kernel source still hashes to the value the counters were taken on.
-SPMM_NCU = {"dram_bytes": None, "nnz": 62097728, "n": 1000000, "B": 64, "src_sha1": None}
+SPMM_NCU = {"dram_bytes": 11657710000, "nnz": 62097728, "n": 1000000, "B": 64,
+            "src_sha1": "08002631e21e21b2a047d6aa0ee97372ea9f741d"}
 
 
 def spmm_source_sha1():
