@@ -191,7 +191,12 @@ int hd_eig_expand(hd_ctx* ctx, const hd_eig* e, const double* H, int32_t B, floa
  *             (host or device).  X = x^s + x^t.
  *  iters[B], relres[B], status[B] : per column (host or device, may be NULL).
  * The solve runs without host synchronisation except a poll of an active-
- * column count every few iterations.  Errors: HD_ERR_INVALID_ARG for bad
+ * column count every four iterations.  Those four iterations are one CUDA
+ * graph, captured on the context's own side stream the first time and
+ * replayed on the context's stream while the graph, eigenpairs, mode, batch
+ * width, alpha and max_iter stay the same (any change re-captures it; with
+ * hd_profile_enable on, kernels launch one by one instead).  The call is
+ * therefore not itself capturable into a caller's graph.  Errors: HD_ERR_INVALID_ARG for bad
  * sizes or indices out of range (checked on the device; X is then undefined),
  * HD_ERR_NOT_CONVERGED is NOT returned: per-column status says it. */
 int hd_query_batch(hd_ctx* ctx, const hd_graph* g, const hd_eig* eig, int mode, int32_t B,

@@ -119,6 +119,8 @@ int hd_destroy(hd_ctx* ctx) {
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->h_poll) cudaFreeHost(ctx->h_poll);
     if (ctx->d_flags) cudaFree(ctx->d_flags);
+    if (ctx->iter_exec) cudaGraphExecDestroy(ctx->iter_exec);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     for (auto& kv : ctx->prof_ev)
         for (auto& pr : kv.second) {
             cudaEventDestroy(pr.first);

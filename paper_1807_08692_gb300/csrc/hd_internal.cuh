@@ -24,6 +24,12 @@ struct hd_ctx {
     // pinned host words for polling device counters
     int* h_poll = nullptr;
     int* d_flags = nullptr;   // [0]: device-side error flag, [1..]: misc counters
+    // CUDA graph of `graph_iters` CG iterations, re-captured when the solve's
+    // pointers or scalars change (key); launched on `stream`
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t iter_exec = nullptr;
+    std::vector<uint64_t> iter_key;
+    int64_t iter_launches = 0;
     // per-kernel event timing (hd_profile_enable)
     bool prof = false;
     std::vector<cudaEvent_t> ev_pool;

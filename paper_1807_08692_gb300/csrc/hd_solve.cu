@@ -733,6 +733,76 @@ int engine_iteration(Engine& S_, int (*after_update)(void*), void* arg) {
     return HD_OK;
 }
 
+// Run `iters` CG iterations as one CUDA graph launch.  The graph is captured
+// on a private stream (the context's stream may be the legacy default stream,
+// which cannot be captured) and re-captured whenever anything the kernels take
+// as an argument differs from the cached capture.
+static uint64_t fbits(float f) {
+    uint32_t u;
+    memcpy(&u, &f, sizeof u);
+    return u;
+}
+
+static int run_iterations_graph(Engine& E, int iters) {
+    hd_ctx* ctx = E.ctx;
+    std::vector<uint64_t> key = {
+        (uint64_t)E.g, (uint64_t)E.g->row_ptr, (uint64_t)E.g->col, (uint64_t)E.g->val, (uint64_t)E.n, (uint64_t)E.lr.e,
+        (uint64_t)(E.has_lr ? E.lr.e->U : nullptr), (uint64_t)(E.has_lr ? E.lr.e->storage : -1), (uint64_t)E.R, (uint64_t)E.P, (uint64_t)E.Q, (uint64_t)E.X,
+        (uint64_t)E.part, (uint64_t)E.st, (uint64_t)E.num_active, (uint64_t)E.lr.part, (uint64_t)E.lr.C,
+        (uint64_t)E.lr.H, (uint64_t)E.lr.Hhi, (uint64_t)E.lr.Hlo, (uint64_t)E.dcoef, (uint64_t)E.opcoef,
+        (uint64_t)E.Bp, (uint64_t)E.vl.S, (uint64_t)E.vl.nblk, (uint64_t)E.vl.slabs, (uint64_t)E.lr.nchunk,
+        (uint64_t)E.lr.rpad, (uint64_t)E.lr.Bp16, (uint64_t)E.has_lr, (uint64_t)E.eff_mode, (uint64_t)E.r,
+        (uint64_t)E.max_iter, (uint64_t)iters, fbits(E.c1), fbits(E.c2),
+        fbits(E.xs), (uint64_t)ctx->stream};
+    if (!ctx->iter_exec || key != ctx->iter_key) {
+        if (ctx->iter_exec) {
+            cudaGraphExecDestroy(ctx->iter_exec);
+            ctx->iter_exec = nullptr;
+        }
+        if (!ctx->cap_stream) HD_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+        cudaStream_t user = ctx->stream;
+        // the capture stream starts after everything already queued on the user stream
+        HD_CUDA(ctx, cudaStreamSynchronize(user));
+        ctx->stream = ctx->cap_stream;
+        const int64_t l0 = ctx->launches;
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeRelaxed);
+        int rc = HD_OK;
+        if (e == cudaSuccess) {
+            for (int t = 0; t < iters && rc == HD_OK; ++t) rc = engine_iteration(E, nullptr, nullptr);
+            cudaError_t e2 = cudaStreamEndCapture(ctx->cap_stream, &graph);
+            if (rc == HD_OK && e2 != cudaSuccess) e = e2;
+        }
+        ctx->stream = user;
+        if (rc) return rc;
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return hd_fail(ctx, HD_ERR_CUDA, "iteration graph capture: %s", cudaGetErrorString(e));
+        }
+        e = cudaGraphInstantiate(&ctx->iter_exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            ctx->iter_exec = nullptr;
+            return hd_fail(ctx, HD_ERR_CUDA, "iteration graph instantiate: %s", cudaGetErrorString(e));
+        }
+        ctx->iter_launches = ctx->launches - l0;
+        ctx->launches = l0;
+        ctx->iter_key = key;
+    }
+    HD_CUDA(ctx, cudaGraphLaunch(ctx->iter_exec, ctx->stream));
+    ctx->launches += ctx->iter_launches;
+    return HD_OK;
+}
+
+static bool graphs_enabled(hd_ctx* ctx) {
+    static int off = -1;
+    if (off < 0) {
+        const char* s = getenv("HD_NO_GRAPH");
+        off = (s && atoi(s)) ? 1 : 0;
+    }
+    return !off && !ctx->prof;
+}
+
 extern "C" int hd_query_batch(hd_ctx* ctx, const hd_graph* g, const hd_eig* eig, int mode, int32_t B,
                               const int32_t* y_ptr, const int32_t* y_idx, const float* y_val, float alpha,
                               const float* tol, int32_t max_iter, float* X, int32_t ldx, int32_t* iters,
@@ -917,9 +987,14 @@ extern "C" int hd_query_batch(hd_ctx* ctx, const hd_graph* g, const hd_eig* eig,
     if (ctx->h_poll[1]) return hd_fail(ctx, HD_ERR_INVALID_ARG, "observation index out of range or bad y_ptr");
     int active = ctx->h_poll[0];
     while (active > 0 && it < max_iter) {
-        for (int t = 0; t < poll_every && it < max_iter; ++t, ++it) {
-            if ((rc = engine_iteration(S_, nullptr, nullptr))) return rc;
+        const int todo = std::min(poll_every, max_iter - it);
+        if (todo == poll_every && graphs_enabled(ctx)) {
+            if ((rc = run_iterations_graph(S_, todo))) return rc;
+        } else {
+            for (int t = 0; t < todo; ++t)
+                if ((rc = engine_iteration(S_, nullptr, nullptr))) return rc;
         }
+        it += todo;
         HD_CUDA(ctx, cudaMemcpyAsync(ctx->h_poll, S_.num_active, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
         HD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
         active = ctx->h_poll[0];

@@ -192,3 +192,29 @@ def test_r_equals_n_special_case(gpu_ctx):
     Y[5, 0], Y[40, 0] = 1.0, 0.5
     assert it[0] <= 2
     assert rel_l2_cols(Xg.cpu().numpy(), D.spectral(U, lam, Y, 0.99)).max() <= 1e-4
+
+
+def test_graph_replay_equals_eager_launches(gpu_ctx, g1, cfg1_data):
+    # Full poll intervals of CG iterations run as one captured CUDA graph;
+    # with per-kernel profiling on, the same iterations launch one by one.
+    # Both orders of work are identical, so the scores agree bit for bit, also
+    # when solves with other shapes and eigenpairs force a re-capture between.
+    import paper_1807_08692_gb300 as hd
+    lam, U = cfg1_data["lam"], cfg1_data["U"]
+    eigs = {r: hd.eig_from_host(gpu_ctx, g1, lam[:r], U[:, :r], "bf16") for r in (16, 48)}
+    yp, yi, yv = y_arrays(cfg1_data["yp"], cfg1_data["yi"], cfg1_data["yv"])
+    B = len(yp) - 1
+    half = B // 2
+    yp2 = yp[:half + 1].copy()
+    cases = [(None, "paper", (yp, yi, yv)), (eigs[16], "pcg", (yp, yi, yv)),
+             (eigs[48], "pcg", (yp2, yi, yv)), (eigs[48], "paper", (yp, yi, yv)),
+             (eigs[16], "proj", (yp2, yi, yv)), (eigs[16], "pcg", (yp, yi, yv))]
+    got = [hd.query_batch(gpu_ctx, g1, e, m, *a, 0.99, 1e-6, 400) for e, m, a in cases]
+    gpu_ctx.profile(True)
+    try:
+        ref = [hd.query_batch(gpu_ctx, g1, e, m, *a, 0.99, 1e-6, 400) for e, m, a in cases]
+    finally:
+        gpu_ctx.profile(False)
+    for (Xg, itg, _, stg), (Xr, itr, _, str_) in zip(got, ref):
+        assert np.array_equal(Xg.cpu().numpy().view(np.uint32), Xr.cpu().numpy().view(np.uint32))
+        assert np.array_equal(itg, itr) and np.array_equal(stg, str_)
