@@ -7,6 +7,11 @@
 // U is exact in bf16.  The fp32 operand (H or V) is split into bf16 high and
 // low parts (x = hi + lo + O(2^-16 |x|)) and both are multiplied, so the
 // products keep about 16 significant bits before the fp32 accumulation.
+// FP8 storage (e4m3 codes with a per-row fp32 scale): TMA brings the raw code
+// tiles in, four converter warps widen them to bf16 (exact: every e4m3 value
+// is a bf16 value) in the swizzled layout the MMA reads, and the row scale is
+// applied to the fp32 side (the expansion's output rows, the reduction's V
+// rows), so the MMAs are the same as for bf16 storage.
 // Both products are HBM-bound (arithmetic intensity ~B flop per byte of U):
 // the tensor cores only have to keep up with the U stream.
 #include <algorithm>
@@ -23,7 +28,31 @@ constexpr int RSTAGES = 3;
 constexpr int THREADS = 320;      // warp 0: TMA, warp 1: MMA, warps 2-9: epilogue / conversion
 constexpr int EPI = 256;          // epilogue threads: two warps per TMEM lane quarter, splitting the columns
 constexpr int TILE_BYTES = BM * BK * 2;  // 16 KB
+constexpr int CONV = 128;         // converter threads (warps 10-13) for FP8 storage
+constexpr int CSTAGES = 2;        // converted bf16 A stages for FP8 storage
+constexpr int RAW_X = BM * BK;    // raw fp8 expansion stage: 128 rows x 64 codes
+constexpr int RAW_R = BM * 128;   // raw fp8 reduction stage: 128 rows x 128 codes
 }  // namespace
+
+// 16 e4m3 codes -> 16 bf16 values (both exact), as two 16-byte chunks
+__device__ __forceinline__ void fp8x16_to_bf16(const uint4 raw, uint4& lo, uint4& hi) {
+    const uint32_t w[4] = {raw.x, raw.y, raw.z, raw.w};
+    uint32_t o[8];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const __half2_raw hr = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w[q] >> (16 * h)), __NV_E4M3);
+            __half2 hv;
+            memcpy(&hv, &hr, sizeof hv);
+            const float2 f = __half22float2(hv);
+            const __nv_bfloat162 b = __floats2bfloat162_rn(f.x, f.y);
+            memcpy(&o[2 * q + h], &b, sizeof(uint32_t));
+        }
+    }
+    lo = make_uint4(o[0], o[1], o[2], o[3]);
+    hi = make_uint4(o[4], o[5], o[6], o[7]);
+}
 
 bool lr_use_tensor_cores(const hd_eig* e) {
     static int off = -1;
@@ -31,7 +60,7 @@ bool lr_use_tensor_cores(const hd_eig* e) {
         const char* s = getenv("HD_LOWRANK_SIMT");
         off = (s && atoi(s)) ? 1 : 0;
     }
-    return e && e->storage == HD_BF16 && !off;
+    return e && !e->sparse && (e->storage == HD_BF16 || e->storage == HD_FP8) && !off;
 }
 
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
@@ -77,17 +106,23 @@ struct ExpandArgs {
     const float* P;
     const ColState* st;
     const int* gate;
+    const float* scale;  // per-row scale of FP8 storage
 };
 
-__global__ void __launch_bounds__(THREADS, 1)
+// SU = 0: bf16 storage (U tiles go straight from TMA to the MMA);
+// SU = 1: fp8 storage (raw code tiles, converter warps, row scale in the epilogue)
+template <int SU>
+__global__ void __launch_bounds__(THREADS + (SU ? CONV : 0), 1)
     k_lr_expand_tc(const __grid_constant__ CUtensorMap tmU, const __grid_constant__ CUtensorMap tmHhi,
                    const __grid_constant__ CUtensorMap tmHlo, ExpandArgs a, int* err) {
     if (a.gate && *a.gate == 0) return;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const uint32_t btile = (uint32_t)a.Nc * 128;  // one k-block of H^T (Nc rows x 128 B)
+    constexpr int NA = SU ? CSTAGES : XSTAGES;    // bf16 A stages the MMA reads
     uint8_t* As = smem;
-    uint8_t* Bhi = As + XSTAGES * TILE_BYTES;
+    uint8_t* Raw = As + NA * TILE_BYTES;          // raw fp8 stages (SU only)
+    uint8_t* Bhi = Raw + (SU ? XSTAGES * RAW_X : 0);
     uint8_t* Blo = Bhi + a.nkb * btile;
     uint64_t* bars = (uint64_t*)(Blo + a.nkb * btile);
     uint64_t* full = bars;
@@ -96,7 +131,9 @@ __global__ void __launch_bounds__(THREADS, 1)
     uint64_t* acc_full = bfull + 1;
     uint64_t* acc_empty = acc_full + 2;
     uint64_t* drain = acc_empty + 2;
-    uint32_t* tmem_slot = (uint32_t*)(drain + 1);
+    uint64_t* cfull = drain + 1;
+    uint64_t* cempty = cfull + CSTAGES;
+    uint32_t* tmem_slot = (uint32_t*)(cempty + CSTAGES);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -105,7 +142,11 @@ __global__ void __launch_bounds__(THREADS, 1)
     if (threadIdx.x == 0) {
         for (int s = 0; s < XSTAGES; ++s) {
             tc::mbar_init(&full[s], 1);
-            tc::mbar_init(&empty[s], 1);
+            tc::mbar_init(&empty[s], SU ? CONV : 1);
+        }
+        for (int s = 0; s < CSTAGES; ++s) {
+            tc::mbar_init(&cfull[s], CONV);
+            tc::mbar_init(&cempty[s], 1);
         }
         tc::mbar_init(bfull, 1);
         for (int b = 0; b < 2; ++b) {
@@ -138,8 +179,13 @@ __global__ void __launch_bounds__(THREADS, 1)
                         ok = false;
                         break;
                     }
-                    tc::mbar_arrive_expect_tx(&full[s], TILE_BYTES);
-                    tc::tma_load_2d(As + s * TILE_BYTES, &tmU, &full[s], kb * BK, t * BM);
+                    if (SU) {
+                        tc::mbar_arrive_expect_tx(&full[s], RAW_X);
+                        tc::tma_load_2d(Raw + s * RAW_X, &tmU, &full[s], kb * BK, t * BM);
+                    } else {
+                        tc::mbar_arrive_expect_tx(&full[s], TILE_BYTES);
+                        tc::tma_load_2d(As + s * TILE_BYTES, &tmU, &full[s], kb * BK, t * BM);
+                    }
                 }
             if (!ok) {
                 *abort_flag = 1;
@@ -165,8 +211,9 @@ __global__ void __launch_bounds__(THREADS, 1)
                 tc::fence_after_sync();
                 const uint32_t dt = tmem + ab * a.Nc;
                 for (int kb = 0; kb < a.nkb; ++kb, ++it) {
-                    const int s = it % XSTAGES;
-                    if (!tc::mbar_wait(&full[s], (it / XSTAGES) & 1, abort_flag)) {
+                    const int s = SU ? it % CSTAGES : it % XSTAGES;
+                    uint64_t* fb = SU ? &cfull[s] : &full[s];
+                    if (!tc::mbar_wait(fb, (SU ? it / CSTAGES : it / XSTAGES) & 1, abort_flag)) {
                         ok = false;
                         break;
                     }
@@ -181,7 +228,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                                      (kb | kk) ? 1u : 0u);
                         tc::mma_bf16(dt, ad, tc::smem_desc(bl + kk * 32, 16, 1024, tc::SWIZZLE_128B), idesc, 1u);
                     }
-                    tc::mma_commit(&empty[s]);
+                    tc::mma_commit(SU ? &cempty[s] : &empty[s]);
                 }
                 if (ok) tc::mma_commit(&acc_full[ab]);
             }
@@ -191,6 +238,38 @@ __global__ void __launch_bounds__(THREADS, 1)
                 tc::mma_commit(drain);
                 tc::mbar_wait(drain, 0, nullptr, 200000000ull);
             }
+        }
+    } else if (SU && warp >= THREADS / 32) {
+        // converters: raw 128 x 64 code tile -> bf16 128 x 128 B rows, 128-byte swizzle
+        const int ct = threadIdx.x - THREADS;
+        uint32_t it = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x)
+            for (int kb = 0; kb < a.nkb; ++kb, ++it) {
+                const int s = it % XSTAGES, s2 = it % CSTAGES;
+                if (!tc::mbar_wait(&full[s], (it / XSTAGES) & 1, abort_flag) ||
+                    !tc::mbar_wait(&cempty[s2], ((it / CSTAGES) & 1) ^ 1, abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                const uint8_t* src = Raw + s * RAW_X;
+                uint8_t* dst = As + s2 * TILE_BYTES;
+#pragma unroll
+                for (int p = 0; p < RAW_X / 16 / CONV; ++p) {
+                    const int ci = p * CONV + ct;   // 16-code chunk: row ci/4, codes 16*(ci%4) ..
+                    const int row = ci >> 2, lc = 2 * (ci & 3), sw = row & 7;
+                    uint4 lo, hi;
+                    fp8x16_to_bf16(*reinterpret_cast<const uint4*>(src + ci * 16), lo, hi);
+                    *reinterpret_cast<uint4*>(dst + row * 128 + ((lc ^ sw) << 4)) = lo;
+                    *reinterpret_cast<uint4*>(dst + row * 128 + (((lc + 1) ^ sw) << 4)) = hi;
+                }
+                tc::fence_proxy_async_smem();
+                tc::mbar_arrive(&cfull[s2]);
+                tc::mbar_arrive(&empty[s]);
+            }
+        if (!ok) {
+            *abort_flag = 1;
+            atomicExch(err, 14);
         }
     } else {
         // epilogue: warps 2-9; lane quarter (warp % 4) gives the TMEM lanes (rows),
@@ -225,13 +304,14 @@ __global__ void __launch_bounds__(THREADS, 1)
         bool ok = true;
         for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tcount) {
             const int ab = tcount & 1;
+            const int64_t row = (int64_t)t * BM + rloc;
+            const bool live = row < a.n;
+            const float rsc = (SU && live) ? __ldg(a.scale + row) : 1.0f;
             if (!tc::mbar_wait(&acc_full[ab], (tcount >> 1) & 1, abort_flag)) {
                 ok = false;
                 break;
             }
             tc::fence_after_sync();
-            const int64_t row = (int64_t)t * BM + rloc;
-            const bool live = row < a.n;
             for (int c0 = cb; c0 < ce; c0 += 2) {
                 if (c0 != cb) load_ops(row, c0);
 #pragma unroll
@@ -242,6 +322,10 @@ __global__ void __launch_bounds__(THREADS, 1)
                     tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + ab * a.Nc + c * 16, v);
                     tc::tmem_ld_wait();
                     if (!live) continue;
+                    if (SU) {
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) v[q] *= rsc;
+                    }
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
                         const int j = a.c0 + c * 16 + 4 * q;
@@ -302,17 +386,21 @@ struct ReduceArgs {
     const float* V;
     float* part;         // [gridDim.x][rpad][Bp]
     const int* gate;
+    const float* scale;  // per-row scale of FP8 storage
 };
 
-__global__ void __launch_bounds__(THREADS, 1)
+template <int SU>
+__global__ void __launch_bounds__(THREADS + (SU ? CONV : 0), 1)
     k_lr_reduce_tc(const __grid_constant__ CUtensorMap tmU, ReduceArgs a, int* err) {
     if (a.gate && *a.gate == 0) return;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const uint32_t astage = 2 * TILE_BYTES;                 // 128 rows x 128 eigen-indices
     const uint32_t bterm = (uint32_t)(a.Nc / 64) * TILE_BYTES;  // 128 rows x Nc, one bf16 part
+    constexpr int NA = SU ? CSTAGES : RSTAGES;
     uint8_t* As = smem;
-    uint8_t* Bs = As + RSTAGES * astage;                    // [2 buffers][hi, lo]
+    uint8_t* Raw = As + NA * astage;                        // raw fp8 stages (SU only)
+    uint8_t* Bs = Raw + (SU ? RSTAGES * RAW_R : 0);         // [2 buffers][hi, lo]
     uint64_t* bars = (uint64_t*)(Bs + 4 * bterm);
     uint64_t* full = bars;
     uint64_t* empty = full + RSTAGES;
@@ -320,7 +408,9 @@ __global__ void __launch_bounds__(THREADS, 1)
     uint64_t* bempty = bfull + 2;
     uint64_t* done = bempty + 2;
     uint64_t* drain = done + 1;
-    uint32_t* tmem_slot = (uint32_t*)(drain + 1);
+    uint64_t* cfull = drain + 1;
+    uint64_t* cempty = cfull + CSTAGES;
+    uint32_t* tmem_slot = (uint32_t*)(cempty + CSTAGES);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -332,7 +422,11 @@ __global__ void __launch_bounds__(THREADS, 1)
     if (threadIdx.x == 0) {
         for (int s = 0; s < RSTAGES; ++s) {
             tc::mbar_init(&full[s], 1);
-            tc::mbar_init(&empty[s], 1);
+            tc::mbar_init(&empty[s], SU ? CONV : 1);
+        }
+        for (int s = 0; s < CSTAGES; ++s) {
+            tc::mbar_init(&cfull[s], CONV);
+            tc::mbar_init(&cempty[s], 1);
         }
         for (int b = 0; b < 2; ++b) {
             tc::mbar_init(&bfull[b], EPI);
@@ -360,11 +454,16 @@ __global__ void __launch_bounds__(THREADS, 1)
                         ok = false;
                         break;
                     }
-                    uint8_t* dst = As + s * astage;
                     const int32_t rowc = (int32_t)((t0 + tl) * BM);
-                    tc::mbar_arrive_expect_tx(&full[s], astage);
-                    tc::tma_load_2d(dst, &tmU, &full[s], m * 128, rowc);
-                    tc::tma_load_2d(dst + TILE_BYTES, &tmU, &full[s], m * 128 + 64, rowc);
+                    if (SU) {
+                        tc::mbar_arrive_expect_tx(&full[s], RAW_R);
+                        tc::tma_load_2d(Raw + s * RAW_R, &tmU, &full[s], m * 128, rowc);
+                    } else {
+                        uint8_t* dst = As + s * astage;
+                        tc::mbar_arrive_expect_tx(&full[s], astage);
+                        tc::tma_load_2d(dst, &tmU, &full[s], m * 128, rowc);
+                        tc::tma_load_2d(dst + TILE_BYTES, &tmU, &full[s], m * 128 + 64, rowc);
+                    }
                 }
             if (!ok) {
                 *abort_flag = 1;
@@ -390,8 +489,9 @@ __global__ void __launch_bounds__(THREADS, 1)
                 const uint32_t bh = tc::smem_u32(Bs + (2 * buf) * bterm);
                 const uint32_t bl = tc::smem_u32(Bs + (2 * buf + 1) * bterm);
                 for (int m = 0; m < a.mt; ++m, ++it) {
-                    const int s = it % RSTAGES;
-                    if (!tc::mbar_wait(&full[s], (it / RSTAGES) & 1, abort_flag)) {
+                    const int s = SU ? it % CSTAGES : it % RSTAGES;
+                    uint64_t* fb = SU ? &cfull[s] : &full[s];
+                    if (!tc::mbar_wait(fb, (SU ? it / CSTAGES : it / RSTAGES) & 1, abort_flag)) {
                         ok = false;
                         break;
                     }
@@ -405,7 +505,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                                      (tl | kk) ? 1u : 0u);
                         tc::mma_bf16(dt, ad, tc::smem_desc(bl + kk * 2048, a.lbo, a.sbo, tc::SWIZZLE_128B), idesc, 1u);
                     }
-                    tc::mma_commit(&empty[s]);
+                    tc::mma_commit(SU ? &cempty[s] : &empty[s]);
                 }
                 if (ok) tc::mma_commit(&bempty[buf]);
             }
@@ -414,6 +514,41 @@ __global__ void __launch_bounds__(THREADS, 1)
                 *abort_flag = 1;
                 atomicExch(err, 22);
             }
+        }
+    } else if (SU && warp >= THREADS / 32) {
+        // converters: raw 128 rows x 128 codes -> two MN-major bf16 blocks of 64
+        // eigen-indices (128-byte rows, 128-byte swizzle)
+        const int ct = threadIdx.x - THREADS;
+        uint32_t it = 0;
+        bool ok = true;
+        for (int tl = 0; tl < ntl && ok; ++tl)
+            for (int m = 0; m < a.mt; ++m, ++it) {
+                const int s = it % RSTAGES, s2 = it % CSTAGES;
+                if (!tc::mbar_wait(&full[s], (it / RSTAGES) & 1, abort_flag) ||
+                    !tc::mbar_wait(&cempty[s2], ((it / CSTAGES) & 1) ^ 1, abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                const uint8_t* src = Raw + s * RAW_R;
+                uint8_t* dst = As + s2 * astage;
+#pragma unroll
+                for (int p = 0; p < RAW_R / 16 / CONV; ++p) {
+                    const int ci = p * CONV + ct;   // 16-code chunk: row ci/8, eigen-indices 16*(ci%8) ..
+                    const int rr = ci >> 3, c = ci & 7, sw = rr & 7;
+                    const int lc = 2 * (c & 3);
+                    uint8_t* blk = dst + (c >> 2) * TILE_BYTES + rr * 128;
+                    uint4 lo, hi;
+                    fp8x16_to_bf16(*reinterpret_cast<const uint4*>(src + ci * 16), lo, hi);
+                    *reinterpret_cast<uint4*>(blk + ((lc ^ sw) << 4)) = lo;
+                    *reinterpret_cast<uint4*>(blk + (((lc + 1) ^ sw) << 4)) = hi;
+                }
+                tc::fence_proxy_async_smem();
+                tc::mbar_arrive(&cfull[s2]);
+                tc::mbar_arrive(&empty[s]);
+            }
+        if (!ok) {
+            *abort_flag = 1;
+            atomicExch(err, 25);
         }
     } else {
         // conversion of V tiles into bf16 hi/lo, MN-major 128-byte swizzle, then the epilogue
@@ -427,16 +562,21 @@ __global__ void __launch_bounds__(THREADS, 1)
         // converted (one batch when a tile fits EPI x 8 float4, i.e. Nc <= 64)
         const bool one_batch = total <= EPI * 8;
         float4 v[8];
+        float vs[8];
         auto load_tile = [&](int tl_, int base_) {
             const int64_t row0_ = (t0 + tl_) * BM;
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
                 const int e = base_ + u * EPI;
                 v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                vs[u] = 1.0f;
                 if (e < total) {
                     const int rr = e / cq_n, j = a.c0 + 4 * (e % cq_n);
                     const int64_t i = row0_ + rr;
-                    if (i < a.n && j < a.Bp) v[u] = *reinterpret_cast<const float4*>(a.V + i * a.Bp + j);
+                    if (i < a.n && j < a.Bp) {
+                        v[u] = *reinterpret_cast<const float4*>(a.V + i * a.Bp + j);
+                        if (SU) vs[u] = __ldg(a.scale + i);
+                    }
                 }
             }
         };
@@ -453,7 +593,15 @@ __global__ void __launch_bounds__(THREADS, 1)
                 if (!one_batch) load_tile(tl, base);
                 float4 cur[8];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) cur[u] = v[u];
+                for (int u = 0; u < 8; ++u) {
+                    cur[u] = v[u];
+                    if (SU) {
+                        cur[u].x *= vs[u];
+                        cur[u].y *= vs[u];
+                        cur[u].z *= vs[u];
+                        cur[u].w *= vs[u];
+                    }
+                }
                 if (one_batch && tl + 1 < ntl) load_tile(tl + 1, tid);
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
@@ -536,19 +684,22 @@ int lr_tc_expand(hd_ctx* ctx, const LowRank& lr, int op, float* out, const float
                  int32_t Bp, const ColState* st, const int* gate) {
     const hd_eig* e = lr.e;
     const int nkb = lr.rpad / BK;
+    const int su = e->storage == HD_FP8 ? 1 : 0;
     CUtensorMap tu;
-    if (hd_make_tmap_2d(&tu, e->U, 2, n, e->ldu, e->ldu, BM, BK, 1))
+    if (hd_make_tmap_2d(&tu, e->U, su ? 1 : 2, n, e->ldu, e->ldu, BM, BK, su ? 0 : 1))
         return hd_fail(ctx, HD_ERR_CUDA, "tensor map for U failed");
     // column chunks so that H^T (hi + lo) fits next to the A pipeline
     const int max_smem = 227 * 1024 - 2048;
+    const int apipe = su ? CSTAGES * TILE_BYTES + XSTAGES * RAW_X : XSTAGES * TILE_BYTES;
     int Nc = lr.Bp16;
-    while (Nc > 16 && (XSTAGES * TILE_BYTES + 2 * nkb * Nc * 128 > max_smem || Nc > 256)) Nc = (Nc / 2 + 15) / 16 * 16;
-    if (XSTAGES * TILE_BYTES + 2 * nkb * Nc * 128 > max_smem)
+    while (Nc > 16 && (apipe + 2 * nkb * Nc * 128 > max_smem || Nc > 256)) Nc = (Nc / 2 + 15) / 16 * 16;
+    if (apipe + 2 * nkb * Nc * 128 > max_smem)
         return hd_fail(ctx, HD_ERR_INVALID_ARG, "rank %d too large for the tensor-core expansion", e->r);
-    static bool attr = false;
-    if (!attr) {
-        HD_CUDA(ctx, cudaFuncSetAttribute(k_lr_expand_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-        attr = true;
+    static bool attr[2] = {false, false};
+    if (!attr[su]) {
+        HD_CUDA(ctx, cudaFuncSetAttribute(su ? k_lr_expand_tc<1> : k_lr_expand_tc<0>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        attr[su] = true;
     }
     for (int c0 = 0; c0 < lr.Bp16; c0 += Nc) {
         const int nc = std::min(Nc, lr.Bp16 - c0);
@@ -569,10 +720,14 @@ int lr_tc_expand(hd_ctx* ctx, const LowRank& lr, int op, float* out, const float
         a.P = Pv;
         a.st = st;
         a.gate = gate;
-        const size_t smem = 1024 + XSTAGES * TILE_BYTES + 2 * (size_t)nkb * nc * 128 + 256;
+        a.scale = e->scale;
+        const size_t smem = 1024 + apipe + 2 * (size_t)nkb * nc * 128 + 256;
         const int tiles = (int)((n + BM - 1) / BM);
         const int grid = std::min(tiles, ctx->num_sms);
-        k_lr_expand_tc<<<grid, THREADS, smem, ctx->stream>>>(tu, th, tl, a, ctx->d_flags + 2);
+        if (su)
+            k_lr_expand_tc<1><<<grid, THREADS + CONV, smem, ctx->stream>>>(tu, th, tl, a, ctx->d_flags + 2);
+        else
+            k_lr_expand_tc<0><<<grid, THREADS, smem, ctx->stream>>>(tu, th, tl, a, ctx->d_flags + 2);
         HD_CHECK_LAUNCH(ctx);
     }
     return check_err(ctx, "expand");
@@ -581,20 +736,24 @@ int lr_tc_expand(hd_ctx* ctx, const LowRank& lr, int op, float* out, const float
 int lr_tc_reduce(hd_ctx* ctx, const LowRank& lr, const float* V, int64_t n, int32_t Bp, const int* gate) {
     const hd_eig* e = lr.e;
     const int mt = (e->r + 127) / 128;
+    const int su = e->storage == HD_FP8 ? 1 : 0;
     CUtensorMap tu;
-    if (hd_make_tmap_2d(&tu, e->U, 2, n, e->ldu, e->ldu, BM, BK, 1))
+    if (su ? hd_make_tmap_2d(&tu, e->U, 1, n, e->ldu, e->ldu, BM, 128, 0)
+           : hd_make_tmap_2d(&tu, e->U, 2, n, e->ldu, e->ldu, BM, BK, 1))
         return hd_fail(ctx, HD_ERR_CUDA, "tensor map for U failed");
     const int Bp64 = (Bp + 63) / 64 * 64;
     int Nc = Bp64;
     const int max_smem = 227 * 1024 - 2048;
-    auto smem_of = [&](int nc) { return (size_t)RSTAGES * 2 * TILE_BYTES + 4 * (size_t)(nc / 64) * TILE_BYTES; };
+    const size_t apipe = su ? (size_t)CSTAGES * 2 * TILE_BYTES + (size_t)RSTAGES * RAW_R : (size_t)RSTAGES * 2 * TILE_BYTES;
+    auto smem_of = [&](int nc) { return apipe + 4 * (size_t)(nc / 64) * TILE_BYTES; };
     while (Nc > 64 && (smem_of(Nc) > (size_t)max_smem || mt * Nc > 512 || Nc > 256)) Nc -= 64;
     if (mt * Nc > 512 || smem_of(Nc) > (size_t)max_smem)
         return hd_fail(ctx, HD_ERR_INVALID_ARG, "rank %d too large for the tensor-core reduction", e->r);
-    static bool attr = false;
-    if (!attr) {
-        HD_CUDA(ctx, cudaFuncSetAttribute(k_lr_reduce_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-        attr = true;
+    static bool attr[2] = {false, false};
+    if (!attr[su]) {
+        HD_CUDA(ctx, cudaFuncSetAttribute(su ? k_lr_reduce_tc<1> : k_lr_reduce_tc<0>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        attr[su] = true;
     }
     static int variant = -1;
     if (variant < 0) {
@@ -619,8 +778,12 @@ int lr_tc_reduce(hd_ctx* ctx, const LowRank& lr, const float* V, int64_t n, int3
         a.V = V;
         a.part = lr.part;
         a.gate = gate;
+        a.scale = e->scale;
         const size_t smem = 1024 + smem_of(nc) + 256;
-        k_lr_reduce_tc<<<grid, THREADS, smem, ctx->stream>>>(tu, a, ctx->d_flags + 3);
+        if (su)
+            k_lr_reduce_tc<1><<<grid, THREADS + CONV, smem, ctx->stream>>>(tu, a, ctx->d_flags + 3);
+        else
+            k_lr_reduce_tc<0><<<grid, THREADS, smem, ctx->stream>>>(tu, a, ctx->d_flags + 3);
         HD_CHECK_LAUNCH(ctx);
     }
     return HD_OK;

@@ -1,5 +1,5 @@
-"""Spectral products U^T V and U H on the device (tensor cores for bf16 U,
-CUDA cores for fp32 / fp8 U) against numpy on the dequantised U."""
+"""Spectral products U^T V and U H on the device (tensor cores for bf16 and
+fp8 U, CUDA cores for fp32 U) against numpy on the dequantised U."""
 import numpy as np
 import pytest
 
