@@ -363,10 +363,40 @@ def sweep_leg(ctx, wl, args, alpha):
         run(f"pcg r={r2} bf16", e, "pcg", args.batch, r=r2, storage="bf16")
         e.close()
         run(f"paper r={r} {args.storage}", wl["eig"], "paper", args.batch, r=r, storage=args.storage)
+        # SHybrid (Sec. 5.3): 99% of the embedding's entries dropped
+        es = wl["eig"].sparsify(0.99)
+        run(f"pcg r={r} {args.storage} sparse 0.99", es, "pcg", args.batch, r=r, storage=args.storage,
+            sparsity=0.99, u_nnz=es.nnz)
+        run(f"paper r={r} {args.storage} sparse 0.99", es, "paper", args.batch, r=r, storage=args.storage,
+            sparsity=0.99, u_nnz=es.nnz)
+        es.close()
     for b in [int(x) for x in args.sweep_batches.split(",") if x]:
         run(f"{args.mode} r={args.r} B={b}", wl["eig"], args.mode, b, r=args.r, storage=args.storage)
         run(f"cg r=0 B={b}", None, "paper", b, r=0, storage=None)
     return out
+
+
+def convergence_leg(ctx, wl, rows_in, alpha):
+    """Sec. 4.4 on the benchmark graph: lambda_n by Lanczos on -W, then the
+    Eq. 21-23 iteration bound for each measured (r, tol) leg.  lambda_{r+1} is
+    taken as lambda_r when only r eigenvalues are known (a larger kappa, so
+    the bound stays an upper bound)."""
+    import paper_1807_08692_gb300 as hd
+    t0 = time.perf_counter()
+    lam_min, conv = hd.spectrum_min(ctx, wl["g"], tol=1e-4, max_restarts=30)
+    t_min = time.perf_counter() - t0
+    lam = wl["lam"]
+    out = []
+    for r, mode, tol, measured in rows_in:
+        if r == 0:
+            lam_next = 1.0
+        else:
+            lam_next = float(lam[min(r, len(lam) - 1)])
+        kap, ia, ir = hd.cg_bound(mode if r > 0 else "paper", alpha, lam_next, min(lam_min, lam_next), tol)
+        out.append({"r": r, "mode": mode, "tol": tol, "lambda_next": round(lam_next, 5), "kappa": round(kap, 3),
+                    "bound_iters_anorm": ia, "bound_iters_resid": ir, "measured_iters": measured})
+    return {"lambda_min": round(lam_min, 5), "lambda_min_converged": conv, "lambda_min_s": round(t_min, 2),
+            "rows": out}
 
 
 # ------------------------------------------------------------------ serving (continuous batching)
@@ -491,6 +521,17 @@ def main():
                "d2h_bytes_per_step": int(d2h)}
     # ---- sweep over storage, rank and batch
     sweep = sweep_leg(ctx, wl, args, alpha) if (args.sweep and not args.quick) else None
+    # ---- convergence analysis (Eq. 21-23) against the measured iteration counts
+    conv = None
+    if not args.quick and wl["lam"] is not None:
+        rows_in = [(args.r, args.mode, tol_h, int(hyb["iters"].max()))]
+        if cg is not None:
+            rows_in.append((0, "paper", tol_0, cg["iters_max"]))
+        for sw in sweep or []:
+            if sw["mode"] == args.mode and sw.get("storage") == args.storage and sw["B"] == B \
+                    and "sparsity" not in sw and sw["r"] != args.r:
+                rows_in.append((sw["r"], sw["mode"], sw["tol"], sw["iters_max"]))
+        conv = convergence_leg(ctx, wl, rows_in, alpha)
     # ---- serving: continuous batching under Poisson load
     serving = None
     rates = [float(x) for x in args.serve_rates.split(",") if x.strip()]
@@ -551,7 +592,7 @@ def main():
                    "setup_s": {"gen": round(wl["t_gen"], 1), "graph": round(wl["t_graph"], 1),
                                "eig": round(wl["t_eig"], 1)}},
         "p50_ms": round(float(np.percentile(hyb["ms"], 50)), 4), "p99_ms": round(float(np.percentile(hyb["ms"], 99)), 4),
-        "cg_r0": cg, "sweep": sweep, "serving": serving, "e2e": e2e, "gpu_launches": int(hyb["launches"]), "roofline": roofline, "cpu_baseline": cpu,
+        "cg_r0": cg, "sweep": sweep, "convergence": conv, "serving": serving, "e2e": e2e, "gpu_launches": int(hyb["launches"]), "roofline": roofline, "cpu_baseline": cpu,
         "clocks": clocks, "wall_s_timed": round(t_wall, 3),
     }
     if rank == 0:

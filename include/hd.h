@@ -161,7 +161,51 @@ int hd_eigendecompose(hd_ctx* ctx, const hd_graph* g, int32_t r, int32_t block,
                       int32_t max_basis, double tol, int32_t max_restarts, int storage,
                       uint64_t seed, hd_eig** out, double* eigvals_out, double* resid_out);
 
+/* ---- convergence analysis (Sec. 4.4, Eq. 21-23) ---------------------------- */
+
+/* Smallest eigenvalue lambda_n of W, the other end of the spectrum that sets
+ * kappa in Eq. 22-23, by the same block Lanczos run on -W (block 4, basis 64
+ * columns).  *lam_min (host) receives the Ritz value; HD_ERR_NOT_CONVERGED
+ * (with the estimate written) if its residual ||W u - l u|| stays above tol
+ * after max_restarts restarts.  Needs n >= 32. */
+int hd_spectrum_min(hd_ctx* ctx, const hd_graph* g, double tol, int32_t max_restarts,
+                    uint64_t seed, double* lam_min);
+
+/* Host arithmetic, no device work.  For a solve in `mode` with the top r
+ * eigenpairs removed, lam_next = lambda_{r+1}(W) (lambda_1 = 1 for r = 0) and
+ * lam_min = lambda_n(W):
+ *  *kappa_out   = kappa of the operator CG iterates on, Eq. 23 (Eq. 22 at
+ *                 r = 0); the deflated operator's extremes are
+ *                 max(0, lambda_{r+1}) and min(0, lambda_n).  For HD_MODE_PCG
+ *                 the same number is kappa(M^-1 L_alpha(W)) with exact U.
+ *  *iters_anorm = smallest i with phi_i(kappa) <= tol (Eq. 21): A-norm error
+ *                 reduction by tol.
+ *  *iters_resid = smallest i with sqrt(kappa_A) phi_i(kappa) <= tol, an upper
+ *                 bound on the iterations the solver's stopping rule
+ *                 ||r|| <= tol ||b|| needs in exact arithmetic (kappa_A: the
+ *                 condition number of the matrix whose residual is measured,
+ *                 L_alpha(W) for HD_MODE_PCG, the deflated operator otherwise).
+ * Any output may be NULL.  HD_ERR_INVALID_ARG unless 0 <= alpha < 1, tol > 0
+ * and -1 <= lam_min <= lam_next <= 1. */
+int hd_cg_bound(int mode, double alpha, double lam_next, double lam_min, double tol,
+                double* kappa_out, int32_t* iters_anorm, int32_t* iters_resid);
+
 int hd_eig_info(const hd_eig* e, int32_t* r, int* storage);
+
+/* SHybrid (Sec. 5.3, Table 1, Fig. 2): a new eigenpair handle whose U keeps
+ * only the largest-magnitude entries of src's stored U.  The
+ * round(sparsity * n * r) entries of smallest |U_ij| over the whole n x r
+ * matrix are set to zero (round half to even); among equal magnitudes the
+ * later entry in row-major order is dropped first, so the kept set is unique.
+ * The kept entries keep their dequantised fp32 values and are stored twice,
+ * by rows and by columns (12 bytes per entry plus offsets); lambda is
+ * unchanged.  Every query mode and hd_eig_project / hd_eig_expand accept the
+ * result (their low-rank products then run on the sparse entries);
+ * hd_eig_export returns it densely with zeros.  sparsity in [0, 1]; src must
+ * be dense with r > 0.  src stays valid and independent. */
+int hd_eig_sparsify(hd_ctx* ctx, const hd_eig* src, double sparsity, hd_eig** out);
+/* Stored entries of U: nnz of a sparsified handle, n * r otherwise. */
+int hd_eig_nnz(const hd_eig* e, int64_t* nnz);
 /* lambda[r] (host), U n x r fp32 (host or device; dequantised). */
 int hd_eig_export(hd_ctx* ctx, const hd_eig* e, double* lambda, float* U);
 int hd_eig_destroy(hd_eig* e);
@@ -175,6 +219,23 @@ int hd_eig_destroy(hd_eig* e);
  * B must be a multiple of 4 and at most 256. */
 int hd_eig_project(hd_ctx* ctx, const hd_eig* e, const float* V, int32_t B, double* C_out);
 int hd_eig_expand(hd_ctx* ctx, const hd_eig* e, const double* H, int32_t B, float* X_out);
+
+/* ---- general transfer functions (Appendix A) ------------------------------ */
+
+/* x = h(W) y for a transfer function given by its series coefficients
+ * h(A) = sum_{i < ncoef} c_i A^i (Eq. 31, truncated by the caller), computed
+ * by Theorem 2 (Eq. 32-33): x = U g(Lambda) U^T y + h(W - U Lambda U^T) y with
+ * g(x) = h(x) - h(0); the second term by Horner's rule on the black box
+ * z -> W z - U (Lambda (U^T z)) (ncoef - 1 SpMMs and low-rank products).
+ *  eig      : NULL or r = 0 gives h(W) y by Horner's rule on W alone.
+ *  y_ptr[B+1], y_idx, y_val : sparse observations as for hd_query_batch.
+ *  coeffs[ncoef] : host, fp64, finite; 1 <= ncoef <= 100000.
+ *  X        : output n x B (leading dimension ldx >= B), host or device.
+ * Arithmetic is fp32 on the device (g(Lambda) in fp64 on the host).  With
+ * c_i = (1 - alpha) alpha^i the result is the truncated series of Eq. 3. */
+int hd_filter_poly(hd_ctx* ctx, const hd_graph* g, const hd_eig* eig, int32_t B,
+                   const int32_t* y_ptr, const int32_t* y_idx, const float* y_val,
+                   const double* coeffs, int32_t ncoef, float* X, int32_t ldx);
 
 /* ---- online query (Eq. 17-20) -------------------------------------------- */
 

@@ -49,6 +49,25 @@ def phi(kappa: float, i) -> np.ndarray:
     return 2.0 * ((s - 1.0) / (s + 1.0)) ** np.asarray(i, dtype=np.float64)
 
 
+def kappa_deflated(alpha: float, lam_next: float, lam_min: float) -> float:
+    """kappa of L_alpha(W_r) when W_r keeps r zero eigenvalues (Sec. 4.4): its
+    extremes are max(0, lambda_{r+1}) and min(0, lambda_n).  Equal to Eq. 23
+    whenever lambda_{r+1} >= 0 >= lambda_n, the case the paper states."""
+    return (1.0 - alpha * min(0.0, lam_min)) / (1.0 - alpha * max(0.0, lam_next))
+
+
+def cg_iterations_bound(kappa: float, tol: float, kappa_res: float = 1.0) -> int:
+    """Smallest i with sqrt(kappa_res) * phi_i(kappa) <= tol, by counting up
+    (Eq. 21; kappa_res = 1: A-norm error reduced by tol; kappa_res = kappa(A):
+    relative residual ||A e_i|| / ||A e_0|| <= tol, since that ratio is at most
+    sqrt(kappa(A)) times the A-norm ratio)."""
+    c = float(np.sqrt(kappa_res))
+    i = 0
+    while c * float(phi(kappa, i)) > tol:
+        i += 1
+    return i
+
+
 def components(A) -> tuple[int, np.ndarray]:
     """Connected components of the graph of A (count, label per node)."""
     return connected_components(sp.csr_matrix(A), directed=False)

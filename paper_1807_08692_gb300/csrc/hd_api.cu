@@ -394,7 +394,19 @@ static void eig_free(hd_eig* e) {
     cudaFree(e->U);
     cudaFree(e->scale);
     cudaFree(e->lambda_d);
+    cudaFree(e->sp_rp);
+    cudaFree(e->sp_col);
+    cudaFree(e->sp_val);
+    cudaFree(e->sp_cp);
+    cudaFree(e->sp_row);
+    cudaFree(e->sp_cval);
     delete e;
+}
+
+int hd_check_launch(hd_ctx* ctx, const char* file, int line) {
+    ctx->launches++;
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? 0 : hd_fail(ctx, HD_ERR_CUDA, "%s:%d launch: %s", file, line, cudaGetErrorString(e));
 }
 
 int hd_eig_alloc(hd_ctx* ctx, int64_t n, int32_t r, int storage, hd_eig** out) {
@@ -476,8 +488,16 @@ int hd_eig_export(hd_ctx* ctx, const hd_eig* e, double* lambda, float* U) {
             HD_CUDA(ctx, cudaMalloc(&tmp, (size_t)e->n * e->r * sizeof(float)));
             Ud = tmp;
         }
-        k_load_u<<<ceil_div(e->n, 256), 256, 0, ctx->stream>>>(e->U, e->scale, e->n, e->r, e->ldu, e->storage, Ud);
-        HD_CHECK_LAUNCH(ctx);
+        if (e->sparse) {
+            int rc = hd_eig_sparse_export(ctx, e, Ud);
+            if (rc) {
+                if (tmp) cudaFree(tmp);
+                return rc;
+            }
+        } else {
+            k_load_u<<<ceil_div(e->n, 256), 256, 0, ctx->stream>>>(e->U, e->scale, e->n, e->r, e->ldu, e->storage, Ud);
+            HD_CHECK_LAUNCH(ctx);
+        }
         if (tmp) {
             HD_CUDA(ctx, cudaMemcpyAsync(U, tmp, (size_t)e->n * e->r * 4, cudaMemcpyDeviceToHost, ctx->stream));
             HD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));

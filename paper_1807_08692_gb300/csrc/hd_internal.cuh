@@ -80,6 +80,15 @@ struct hd_eig {
     float* scale = nullptr;   // per-row fp8 scale (HD_FP8 only)
     double* lambda_d = nullptr;
     std::vector<double> lambda_h;
+    // sparsified embedding (hd_eig_sparsify): U is not stored densely then
+    bool sparse = false;
+    int64_t nnz = 0;
+    int64_t* sp_rp = nullptr;   // CSR row offsets [n + 1]
+    int32_t* sp_col = nullptr;  // CSR column (eigen-index) [nnz]
+    float* sp_val = nullptr;    // CSR values [nnz]
+    int64_t* sp_cp = nullptr;   // CSC column offsets [r + 1]
+    int32_t* sp_row = nullptr;  // CSC row [nnz]
+    float* sp_cval = nullptr;   // CSC values [nnz]
 };
 
 // ---------------------------------------------------------------- errors
@@ -91,6 +100,12 @@ int hd_fail(hd_ctx* ctx, int code, const char* fmt, ...);
             return hd_fail((ctx), HD_ERR_CUDA, "%s:%d %s: %s", __FILE__, __LINE__, #call, \
                            cudaGetErrorString(e_));                                   \
     } while (0)
+// Function forms of the two checks, for code that must release resources
+// before returning: 0 or the error code (the message is recorded).
+inline int hd_check_cuda(hd_ctx* ctx, cudaError_t e, const char* what, const char* file, int line) {
+    return e == cudaSuccess ? 0 : hd_fail(ctx, HD_ERR_CUDA, "%s:%d %s: %s", file, line, what, cudaGetErrorString(e));
+}
+int hd_check_launch(hd_ctx* ctx, const char* file, int line);
 #define HD_CHECK_LAUNCH(ctx)                                                          \
     do {                                                                              \
         (ctx)->launches++;                                                            \
@@ -162,6 +177,7 @@ int hd_graph_from_lists(hd_ctx* ctx, int64_t n, int32_t k, const int32_t* idx_d,
 int hd_normalize_graph(hd_ctx* ctx, hd_graph* g);
 int hd_eig_alloc(hd_ctx* ctx, int64_t n, int32_t r, int storage, hd_eig** out);
 int hd_eig_store_from_device_f32(hd_ctx* ctx, hd_eig* e, const float* U_d, int32_t ldsrc);
+int hd_eig_sparse_export(hd_ctx* ctx, const hd_eig* e, float* dst);
 int hd_spmm_apply(hd_ctx* ctx, const hd_graph* g, const float* P, float* Q, int32_t ld, int32_t B,
                   float c1, float c2);
 int hd_rank_impl(hd_ctx* ctx, const float* Xd, int64_t n, int32_t B, int32_t ldx, const int32_t* K_h,

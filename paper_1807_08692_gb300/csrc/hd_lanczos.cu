@@ -137,6 +137,7 @@ struct Lanczos {
     double* work;
     int lwork = 0;
     int bp;
+    float c2 = -1.0f;  // SpMM coefficient: -1 multiplies by W, +1 by -W (smallest end)
 };
 
 static int spmm_block(Lanczos& L, const double* V, int cols, double* out) {
@@ -147,7 +148,7 @@ static int spmm_block(Lanczos& L, const double* V, int cols, double* out) {
         int bp = (c + 3) / 4 * 4;
         k_cm64_to_rm32<<<ceil_div(L.n * bp, 256), 256, 0, ctx->stream>>>(V + (int64_t)c0 * L.n, L.n, c, L.n, L.f_in, bp);
         HD_CHECK_LAUNCH(ctx);
-        int rc = hd_spmm_apply(ctx, L.g, L.f_in, L.f_out, bp, c, 0.0f, -1.0f);
+        int rc = hd_spmm_apply(ctx, L.g, L.f_in, L.f_out, bp, c, 0.0f, L.c2);
         if (rc) return rc;
         k_rm32_to_cm64<<<ceil_div(L.n * c, 256), 256, 0, ctx->stream>>>(L.f_out, L.n, c, bp, out + (int64_t)c0 * L.n, L.n);
         HD_CHECK_LAUNCH(ctx);
@@ -221,17 +222,17 @@ static int new_block(Lanczos& L, int cols, double* Wb, uint64_t seed, int salt) 
     return hd_fail(ctx, HD_ERR_NOT_CONVERGED, "could not extend the Krylov basis (n=%lld too small?)", (long long)L.n);
 }
 
-extern "C" int hd_eigendecompose(hd_ctx* ctx, const hd_graph* g, int32_t r, int32_t block, int32_t max_basis,
-                                 double tol, int32_t max_restarts, int storage, uint64_t seed, hd_eig** out,
-                                 double* eigvals_out, double* resid_out) {
-    if (!ctx || !g || !out || r <= 0 || r > 1024) return HD_ERR_INVALID_ARG;
-    if (storage != HD_F32 && storage != HD_BF16 && storage != HD_FP8)
-        return hd_fail(ctx, HD_ERR_INVALID_ARG, "storage %d", storage);
-    *out = nullptr;
+// Top-r eigenpairs of sign * W (sign = +1: W; -1: the smallest end of W).  With
+// out == nullptr only the Ritz values and residuals are returned.
+static int lanczos_top(hd_ctx* ctx, const hd_graph* g, int32_t r, int32_t block, int32_t max_basis, double tol,
+                       int32_t max_restarts, int storage, uint64_t seed, int sign, hd_eig** out, double* eigvals_out,
+                       double* resid_out) {
+    if (out) *out = nullptr;
     HD_CUDA(ctx, cudaSetDevice(ctx->device));
     Lanczos L;
     L.ctx = ctx;
     L.g = g;
+    L.c2 = sign > 0 ? -1.0f : 1.0f;
     L.n = g->n;
     L.b = block > 0 ? block : 32;
     if (L.b > 128) L.b = 128;
@@ -365,6 +366,10 @@ extern "C" int hd_eigendecompose(hd_ctx* ctx, const hd_graph* g, int32_t r, int3
                 if (eigvals_out) eigvals_out[t] = thk[t];
                 if (resid_out) resid_out[t] = std::sqrt(res[t]);
             }
+            if (!out) {
+                cleanup();
+                return converged ? HD_OK : hd_fail(ctx, HD_ERR_NOT_CONVERGED, "max residual %.3e > tol %.1e", worst, tol);
+            }
             hd_eig* e;
             TRY(hd_eig_alloc(ctx, n, r, storage, &e));
             e->lambda_h.assign(thk.begin(), thk.begin() + r);
@@ -396,4 +401,56 @@ extern "C" int hd_eigendecompose(hd_ctx* ctx, const hd_graph* g, int32_t r, int3
         BL(cublasDgeam(L.h.blas, CUBLAS_OP_T, CUBLAS_OP_N, k, cols, &one, P, cols, &zero, P, k, L.T, m));
     }
 #undef TRY
+}
+
+extern "C" int hd_eigendecompose(hd_ctx* ctx, const hd_graph* g, int32_t r, int32_t block, int32_t max_basis,
+                                 double tol, int32_t max_restarts, int storage, uint64_t seed, hd_eig** out,
+                                 double* eigvals_out, double* resid_out) {
+    if (!ctx || !g || !out || r <= 0 || r > 1024) return HD_ERR_INVALID_ARG;
+    if (storage != HD_F32 && storage != HD_BF16 && storage != HD_FP8)
+        return hd_fail(ctx, HD_ERR_INVALID_ARG, "storage %d", storage);
+    return lanczos_top(ctx, g, r, block, max_basis, tol, max_restarts, storage, seed, +1, out, eigvals_out, resid_out);
+}
+
+extern "C" int hd_spectrum_min(hd_ctx* ctx, const hd_graph* g, double tol, int32_t max_restarts, uint64_t seed,
+                               double* lam_min) {
+    if (!ctx || !g || !lam_min) return HD_ERR_INVALID_ARG;
+    if (g->n < 32) return hd_fail(ctx, HD_ERR_INVALID_ARG, "n=%lld too small for the Lanczos estimate", (long long)g->n);
+    double th = 0.0, rs = 0.0;
+    // one Ritz value of -W with a block of 4 and a basis of 64 columns
+    const int rc = lanczos_top(ctx, g, 1, 4, 64, tol, max_restarts, HD_F32, seed, -1, nullptr, &th, &rs);
+    *lam_min = -th;
+    return rc;
+}
+
+// Eq. 21-23: kappa of the system CG runs on and the iterations the bound needs.
+extern "C" int hd_cg_bound(int mode, double alpha, double lam_next, double lam_min, double tol, double* kappa_out,
+                           int32_t* iters_anorm, int32_t* iters_resid) {
+    if (!(alpha >= 0.0 && alpha < 1.0) || !(tol > 0.0) || !(lam_next <= 1.0) || !(lam_min >= -1.0) ||
+        lam_min > lam_next || (mode != HD_MODE_PAPER && mode != HD_MODE_PROJ && mode != HD_MODE_PCG))
+        return HD_ERR_INVALID_ARG;
+    // the deflated operator keeps r zero eigenvalues, so its extremes are
+    // max(0, lambda_{r+1}) and min(0, lambda_n)
+    const double top = std::max(0.0, lam_next), bot = std::min(0.0, lam_min);
+    const double kappa = (1.0 - alpha * bot) / (1.0 - alpha * top);
+    // the residual criterion ||r|| <= tol ||b|| follows from the A-norm bound
+    // through sqrt(kappa(A)) of the matrix the residual belongs to: the deflated
+    // operator for Forms P and N, L_alpha(W) itself (Eq. 22) for the
+    // preconditioned solve
+    const double kappa_a = mode == HD_MODE_PCG ? (1.0 - alpha * bot) / (1.0 - alpha) : kappa;
+    const double sk = std::sqrt(kappa);
+    const double q = (sk - 1.0) / (sk + 1.0);
+    auto first = [&](double target) -> int32_t {
+        if (q <= 0.0) return 1;
+        const double need = std::log(target / 2.0) / std::log(q);
+        int32_t i = need <= 0.0 ? 0 : (int32_t)std::ceil(need);
+        // settle rounding of the logarithms against the bound itself
+        while (i > 0 && 2.0 * std::pow(q, i - 1) <= target) --i;
+        while (2.0 * std::pow(q, i) > target) ++i;
+        return i;
+    };
+    if (kappa_out) *kappa_out = kappa;
+    if (iters_anorm) *iters_anorm = first(tol);
+    if (iters_resid) *iters_resid = first(tol / std::sqrt(kappa_a));
+    return HD_OK;
 }

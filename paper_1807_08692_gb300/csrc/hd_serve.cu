@@ -170,7 +170,7 @@ int hd_serve_open(hd_ctx* ctx, const hd_graph* g, const hd_eig* eig, int mode, f
     const int rpad = lr_on ? (eig->r + 63) / 64 * 64 : 0;
     const int Bp16 = (Bp + 15) / 16 * 16;
     int nchunk = 0;
-    if (lr_on) nchunk = lr_use_tensor_cores(eig) ? lr_tc_nchunk(ctx, n) : simt_nchunk(ctx, n, rpad, Bp);
+    if (lr_on) nchunk = lr_nchunk(ctx, eig, Bp);
     s->cap_nnz = Bp * 512;
     const size_t vec = (size_t)n * Bp * 4;
     size_t bytes = 4 * ws_size(vec) + ws_size((size_t)ctx->num_sms * 8 * Bp * 8) + ws_size(Bp * sizeof(ColState)) +

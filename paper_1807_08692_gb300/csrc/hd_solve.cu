@@ -526,8 +526,14 @@ int simt_nchunk(hd_ctx* ctx, int64_t n, int rpad, int Bp) {
     return (int)std::max<int64_t>(1, std::min<int64_t>(nc, maxc));
 }
 
+int lr_nchunk(hd_ctx* ctx, const hd_eig* e, int32_t Bp) {
+    if (e->sparse) return lr_sparse_nchunk(ctx, e);
+    return lr_use_tensor_cores(e) ? lr_tc_nchunk(ctx, e->n) : simt_nchunk(ctx, e->n, (e->r + 63) / 64 * 64, Bp);
+}
+
 int lr_reduce(hd_ctx* ctx, const LowRank& lr, const float* V, int64_t n, int32_t Bp, const int* gate) {
     HD_PROF(ctx, "lr_reduce");
+    if (lr.e->sparse) return lr_sparse_reduce(ctx, lr, V, n, Bp, gate);
     if (lr_use_tensor_cores(lr.e)) return lr_tc_reduce(ctx, lr, V, n, Bp, gate);
     const hd_eig* e = lr.e;
     int64_t rpc = (n + lr.nchunk - 1) / lr.nchunk;
@@ -557,6 +563,7 @@ int lr_finish(hd_ctx* ctx, const LowRank& lr, int32_t Bp, const double* coef) {
 int lr_expand(hd_ctx* ctx, const LowRank& lr, int op, float* out, const float* Rv, const float* Pv, int64_t n,
               int32_t Bp, const ColState* st, const int* gate) {
     HD_PROF(ctx, "lr_expand");
+    if (lr.e->sparse) return lr_sparse_expand(ctx, lr, op, out, Rv, Pv, n, Bp, st, gate);
     if (lr_use_tensor_cores(lr.e)) return lr_tc_expand(ctx, lr, op, out, Rv, Pv, n, Bp, st, gate);
     const hd_eig* e = lr.e;
     size_t smem = (size_t)e->r * 16 * sizeof(float);
@@ -747,7 +754,8 @@ static int run_iterations_graph(Engine& E, int iters) {
     hd_ctx* ctx = E.ctx;
     std::vector<uint64_t> key = {
         (uint64_t)E.g, (uint64_t)E.g->row_ptr, (uint64_t)E.g->col, (uint64_t)E.g->val, (uint64_t)E.n, (uint64_t)E.lr.e,
-        (uint64_t)(E.has_lr ? E.lr.e->U : nullptr), (uint64_t)(E.has_lr ? E.lr.e->storage : -1), (uint64_t)E.R, (uint64_t)E.P, (uint64_t)E.Q, (uint64_t)E.X,
+        (uint64_t)(E.has_lr ? E.lr.e->U : nullptr), (uint64_t)(E.has_lr ? E.lr.e->storage : -1),
+        (uint64_t)(E.has_lr ? E.lr.e->sp_rp : nullptr), (uint64_t)(E.has_lr ? E.lr.e->sp_cp : nullptr), (uint64_t)E.R, (uint64_t)E.P, (uint64_t)E.Q, (uint64_t)E.X,
         (uint64_t)E.part, (uint64_t)E.st, (uint64_t)E.num_active, (uint64_t)E.lr.part, (uint64_t)E.lr.C,
         (uint64_t)E.lr.H, (uint64_t)E.lr.Hhi, (uint64_t)E.lr.Hlo, (uint64_t)E.dcoef, (uint64_t)E.opcoef,
         (uint64_t)E.Bp, (uint64_t)E.vl.S, (uint64_t)E.vl.nblk, (uint64_t)E.vl.slabs, (uint64_t)E.lr.nchunk,
@@ -847,7 +855,7 @@ extern "C" int hd_query_batch(hd_ctx* ctx, const hd_graph* g, const hd_eig* eig,
     }
     const bool x_direct = hd_is_device_ptr(X) && ldx == Bp;
     int nchunk = 0;
-    if (lr_on) nchunk = lr_use_tensor_cores(eig) ? lr_tc_nchunk(ctx, n) : simt_nchunk(ctx, n, rpad, Bp);
+    if (lr_on) nchunk = lr_nchunk(ctx, eig, Bp);
 
     size_t vec = (size_t)n * Bp * sizeof(float);
     size_t bytes = 3 * ws_size(vec) + (x_direct ? 0 : ws_size(vec)) + ws_size((size_t)ctx->num_sms * 8 * Bp * sizeof(float2)) +
@@ -1034,7 +1042,7 @@ static int lowrank_setup(hd_ctx* ctx, const hd_eig* e, int32_t Bp, LowRank& lr, 
     lr.e = e;
     lr.rpad = (e->r + 63) / 64 * 64;
     lr.Bp16 = (Bp + 15) / 16 * 16;
-    lr.nchunk = lr_use_tensor_cores(e) ? lr_tc_nchunk(ctx, e->n) : simt_nchunk(ctx, e->n, lr.rpad, Bp);
+    lr.nchunk = lr_nchunk(ctx, e, Bp);
     lr.part = cv.take<float>((size_t)lr.nchunk * lr.rpad * Bp);
     lr.C = cv.take<double>((size_t)lr.rpad * Bp);
     lr.H = cv.take<float>((size_t)lr.rpad * Bp);
@@ -1051,7 +1059,7 @@ static int lowrank_setup(hd_ctx* ctx, const hd_eig* e, int32_t Bp, LowRank& lr, 
 
 static size_t lowrank_bytes(hd_ctx* ctx, const hd_eig* e, int32_t Bp) {
     int rpad = (e->r + 63) / 64 * 64;
-    int nch = std::max(lr_tc_nchunk(ctx, e->n), simt_nchunk(ctx, e->n, rpad, Bp));
+    int nch = lr_nchunk(ctx, e, Bp);
     return ws_size((size_t)nch * rpad * Bp * 4) + ws_size((size_t)rpad * Bp * 8) + ws_size((size_t)rpad * Bp * 4) +
            2 * ws_size((size_t)((Bp + 15) / 16 * 16) * rpad * 2) + ws_size(rpad * 8);
 }
@@ -1102,6 +1110,121 @@ extern "C" int hd_eig_expand(hd_ctx* ctx, const hd_eig* e, const double* H, int3
     HD_CHECK_LAUNCH(ctx);
     if ((rc = lr_finish(ctx, lr, B, ones))) return rc;
     if ((rc = lr_expand(ctx, lr, EXP_SET_X, X_out, nullptr, nullptr, e->n, B, nullptr))) return rc;
+    HD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return HD_OK;
+}
+
+// ------------------------------------------------------------------ general transfer functions (Appendix A)
+
+// out = (accumulate ? out : 0) + c * Y over n x Bp
+__global__ void k_axpy_dense(float* __restrict__ out, const float* __restrict__ Y, float c, int64_t count4,
+                             int accumulate) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= count4) return;
+    const float4 y = reinterpret_cast<const float4*>(Y)[e];
+    float4 o = accumulate ? reinterpret_cast<const float4*>(out)[e] : make_float4(0.f, 0.f, 0.f, 0.f);
+    o.x = fmaf(c, y.x, o.x);
+    o.y = fmaf(c, y.y, o.y);
+    o.z = fmaf(c, y.z, o.z);
+    o.w = fmaf(c, y.w, o.w);
+    reinterpret_cast<float4*>(out)[e] = o;
+}
+
+extern "C" int hd_filter_poly(hd_ctx* ctx, const hd_graph* g, const hd_eig* eig, int32_t B, const int32_t* y_ptr,
+                              const int32_t* y_idx, const float* y_val, const double* coeffs, int32_t ncoef,
+                              float* X, int32_t ldx) {
+    if (!ctx || !g || !y_ptr || !coeffs || !X) return HD_ERR_INVALID_ARG;
+    if (B <= 0 || B > 4096 || ldx < B) return hd_fail(ctx, HD_ERR_INVALID_ARG, "B=%d ldx=%d", B, ldx);
+    if (ncoef < 1 || ncoef > 100000) return hd_fail(ctx, HD_ERR_INVALID_ARG, "ncoef=%d", ncoef);
+    for (int i = 0; i < ncoef; ++i)
+        if (!std::isfinite(coeffs[i])) return hd_fail(ctx, HD_ERR_INVALID_ARG, "coefficient %d not finite", i);
+    if (eig && eig->n != g->n) return hd_fail(ctx, HD_ERR_INVALID_ARG, "eigenpairs for n=%lld, graph n=%lld",
+                                              (long long)eig->n, (long long)g->n);
+    HD_CUDA(ctx, cudaSetDevice(ctx->device));
+    const int64_t n = g->n;
+    const int32_t Bp = (B + 3) / 4 * 4;
+    const bool lr_on = eig && eig->r > 0;
+    int32_t nnz_y;
+    if (hd_is_device_ptr(y_ptr)) {
+        HD_CUDA(ctx, cudaMemcpy(&nnz_y, y_ptr + B, 4, cudaMemcpyDeviceToHost));
+    } else {
+        nnz_y = y_ptr[B];
+    }
+    if (nnz_y < 0) return hd_fail(ctx, HD_ERR_INVALID_ARG, "y_ptr[B] = %d", nnz_y);
+    if (nnz_y > 0 && (!y_idx || !y_val)) return HD_ERR_INVALID_ARG;
+    const size_t vec = (size_t)n * Bp * 4;
+    size_t bytes = 3 * ws_size(vec) + ws_size(64) + ws_size((B + 1) * 4) + 2 * ws_size((size_t)nnz_y * 4 + 4);
+    if (lr_on) bytes += lowrank_bytes(ctx, eig, Bp) + 2 * ws_size((size_t)((eig->r + 63) / 64 * 64) * 8);
+    void* ws;
+    int rc = hd_ws_reserve(ctx, bytes, &ws);
+    if (rc) return rc;
+    WsCarver cv(ws);
+    float* Yd = cv.take<float>((size_t)n * Bp);
+    float* acc = cv.take<float>((size_t)n * Bp);
+    float* Q = cv.take<float>((size_t)n * Bp);
+    int* err = cv.take<int>(16);
+    int32_t* d_yptr = cv.take<int32_t>(B + 1);
+    int32_t* d_yidx = cv.take<int32_t>(nnz_y + 1);
+    float* d_yval = cv.take<float>(nnz_y + 1);
+    const void *yp, *yi, *yv;
+    if ((rc = hd_stage_in(ctx, y_ptr, (B + 1) * 4, d_yptr, &yp))) return rc;
+    if ((rc = hd_stage_in(ctx, y_idx, (size_t)nnz_y * 4, d_yidx, &yi))) return rc;
+    if ((rc = hd_stage_in(ctx, y_val, (size_t)nnz_y * 4, d_yval, &yv))) return rc;
+    LowRank lr{};
+    double *ones = nullptr, *lamc = nullptr, *gc = nullptr;
+    if (lr_on) {
+        if ((rc = lowrank_setup(ctx, eig, Bp, lr, &ones, cv))) return rc;
+        lamc = cv.take<double>(lr.rpad);
+        gc = cv.take<double>(lr.rpad);
+        // g(lambda) = h(lambda) - h(0) = sum_{i >= 1} c_i lambda^i (Eq. 33), Horner in fp64
+        std::vector<double> lh(lr.rpad, 0.0), gh(lr.rpad, 0.0);
+        for (int k = 0; k < eig->r; ++k) {
+            const double l = eig->lambda_h[k];
+            double s = 0.0;
+            for (int i = ncoef - 1; i >= 1; --i) s = s * l + coeffs[i];
+            lh[k] = l;
+            gh[k] = s * l;
+        }
+        HD_CUDA(ctx, cudaMemcpyAsync(lamc, lh.data(), lr.rpad * 8, cudaMemcpyHostToDevice, ctx->stream));
+        HD_CUDA(ctx, cudaMemcpyAsync(gc, gh.data(), lr.rpad * 8, cudaMemcpyHostToDevice, ctx->stream));
+    }
+    HD_CUDA(ctx, cudaMemsetAsync(Yd, 0, vec, ctx->stream));
+    HD_CUDA(ctx, cudaMemsetAsync(err, 0, sizeof(int), ctx->stream));
+    k_scatter_y<<<ceil_div(B, 128), 128, 0, ctx->stream>>>((const int32_t*)yp, (const int32_t*)yi, (const float*)yv, B,
+                                                           n, Bp, Yd, err);
+    HD_CHECK_LAUNCH(ctx);
+    const int64_t c4 = (int64_t)n * Bp / 4;
+    // h(W_r) y by Horner's rule on the black box W_r z = W z - U (Lambda (U^T z)) (Eq. 32)
+    k_axpy_dense<<<ceil_div(c4, 256), 256, 0, ctx->stream>>>(acc, Yd, (float)coeffs[ncoef - 1], c4, 0);
+    HD_CHECK_LAUNCH(ctx);
+    for (int i = ncoef - 2; i >= 0; --i) {
+        { HD_PROF(ctx, "spmm");
+          if ((rc = hd_spmm_apply(ctx, g, acc, Q, Bp, B, 0.0f, -1.0f))) return rc; }
+        if (lr_on) {
+            if ((rc = lr_reduce(ctx, lr, acc, n, Bp))) return rc;
+            if ((rc = lr_finish(ctx, lr, Bp, lamc))) return rc;
+            if ((rc = lr_expand(ctx, lr, EXP_SUB_R, Q, nullptr, nullptr, n, Bp, nullptr))) return rc;
+        }
+        k_axpy_dense<<<ceil_div(c4, 256), 256, 0, ctx->stream>>>(Q, Yd, (float)coeffs[i], c4, 1);
+        HD_CHECK_LAUNCH(ctx);
+        std::swap(acc, Q);
+    }
+    // + U g(Lambda) U^T y (Eq. 32)
+    if (lr_on) {
+        if ((rc = lr_reduce(ctx, lr, Yd, n, Bp))) return rc;
+        if ((rc = lr_finish(ctx, lr, Bp, gc))) return rc;
+        if ((rc = lr_expand(ctx, lr, EXP_ADD_Q, acc, nullptr, nullptr, n, Bp, nullptr))) return rc;
+    }
+    HD_CUDA(ctx, cudaMemcpyAsync(ctx->h_poll, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    HD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (ctx->h_poll[0]) return hd_fail(ctx, HD_ERR_INVALID_ARG, "observation index out of range or bad y_ptr");
+    if (hd_is_device_ptr(X)) {
+        k_copy_out<<<ceil_div(n * B, 256), 256, 0, ctx->stream>>>(acc, Bp, X, ldx, B, n);
+        HD_CHECK_LAUNCH(ctx);
+    } else {
+        HD_CUDA(ctx, cudaMemcpy2DAsync(X, (size_t)ldx * 4, acc, (size_t)Bp * 4, (size_t)B * 4, n,
+                                       cudaMemcpyDeviceToHost, ctx->stream));
+    }
     HD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     return HD_OK;
 }

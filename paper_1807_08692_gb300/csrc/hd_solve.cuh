@@ -47,6 +47,12 @@ int lr_finish(hd_ctx* ctx, const LowRank& lr, int32_t Bp, const double* coef);
 int lr_expand(hd_ctx* ctx, const LowRank& lr, int op, float* out, const float* Rv, const float* Pv, int64_t n,
               int32_t Bp, const ColState* st, const int* gate = nullptr);
 bool lr_use_tensor_cores(const hd_eig* e);
+// partial-sum chunks of the reduction for this embedding and batch width
+int lr_nchunk(hd_ctx* ctx, const hd_eig* e, int32_t Bp);
+int lr_sparse_nchunk(hd_ctx* ctx, const hd_eig* e);
+int lr_sparse_reduce(hd_ctx* ctx, const LowRank& lr, const float* V, int64_t n, int32_t Bp, const int* gate);
+int lr_sparse_expand(hd_ctx* ctx, const LowRank& lr, int op, float* out, const float* Rv, const float* Pv, int64_t n,
+                     int32_t Bp, const ColState* st, const int* gate);
 int lr_tc_reduce(hd_ctx* ctx, const LowRank& lr, const float* V, int64_t n, int32_t Bp, const int* gate);
 int lr_tc_expand(hd_ctx* ctx, const LowRank& lr, int op, float* out, const float* Rv, const float* Pv, int64_t n,
                  int32_t Bp, const ColState* st, const int* gate);

@@ -52,7 +52,12 @@ _SIGS = {
     "hd_graph_destroy": (C.c_int, [vp]),
     "hd_eig_from_host": (C.c_int, [vp, vp, i32, vp, vp, C.c_int, C.POINTER(vp)]),
     "hd_eigendecompose": (C.c_int, [vp, vp, i32, i32, i32, f64, i32, C.c_int, u64, C.POINTER(vp), vp, vp]),
+    "hd_spectrum_min": (C.c_int, [vp, vp, f64, i32, u64, C.POINTER(f64)]),
+    "hd_cg_bound": (C.c_int, [C.c_int, f64, f64, f64, f64, C.POINTER(f64), C.POINTER(i32), C.POINTER(i32)]),
     "hd_eig_info": (C.c_int, [vp, C.POINTER(i32), C.POINTER(C.c_int)]),
+    "hd_eig_sparsify": (C.c_int, [vp, vp, f64, C.POINTER(vp)]),
+    "hd_filter_poly": (C.c_int, [vp, vp, vp, i32, vp, vp, vp, vp, i32, vp, i32]),
+    "hd_eig_nnz": (C.c_int, [vp, C.POINTER(C.c_int64)]),
     "hd_eig_export": (C.c_int, [vp, vp, vp, vp]),
     "hd_eig_destroy": (C.c_int, [vp]),
     "hd_query_batch": (C.c_int, [vp, vp, vp, C.c_int, i32, vp, vp, vp, f32, vp, i32, vp, i32, vp, vp, vp]),
@@ -214,6 +219,21 @@ class Eig:
     def handle(self):
         return self._h
 
+    @property
+    def nnz(self) -> int:
+        """Stored entries of U (n * r unless sparsified)."""
+        v = C.c_int64()
+        lib().hd_eig_nnz(self._h, C.byref(v))
+        return v.value
+
+    def sparsify(self, sparsity: float) -> "Eig":
+        """SHybrid (Sec. 5.3): a new handle keeping the largest-magnitude
+        entries of U, round(sparsity * n * r) of them set to zero."""
+        h = vp()
+        self.ctx.check(lib().hd_eig_sparsify(self.ctx.handle, self._h, float(sparsity), C.byref(h)),
+                       "hd_eig_sparsify")
+        return Eig(self.ctx, h, self.n)
+
     def export(self):
         lam = np.empty(self.r, np.float64)
         U = np.empty((self.n, self.r), np.float32)
@@ -315,6 +335,55 @@ def eigendecompose(ctx: Context, g: Graph, r: int, block: int = 32, max_basis: i
     if rc not in (OK, ERR_NOT_CONVERGED):
         ctx.check(rc, "hd_eigendecompose")
     return Eig(ctx, h, g.n), lam, res, rc == OK
+
+
+def spectrum_min(ctx: Context, g: Graph, tol: float = 1e-6, max_restarts: int = 50, seed: int = 7):
+    """lambda_n(W) by Lanczos on -W: (estimate, converged)."""
+    lam = f64()
+    rc = lib().hd_spectrum_min(ctx.handle, g.handle, tol, max_restarts, seed, C.byref(lam))
+    if rc not in (OK, ERR_NOT_CONVERGED):
+        ctx.check(rc, "hd_spectrum_min")
+    return lam.value, rc == OK
+
+
+def cg_bound(mode, alpha: float, lam_next: float, lam_min: float, tol: float):
+    """(kappa, iterations for an A-norm reduction by tol, iterations bounding
+    the residual stopping rule) from Eq. 21-23."""
+    if isinstance(mode, str):
+        mode = MODES[mode]
+    k, ia, ir = f64(), i32(), i32()
+    rc = lib().hd_cg_bound(mode, alpha, lam_next, lam_min, tol, C.byref(k), C.byref(ia), C.byref(ir))
+    if rc != OK:
+        raise HDError(rc, "hd_cg_bound: invalid arguments")
+    return k.value, ia.value, ir.value
+
+
+def convergence_table(lam, lam_min: float, alpha: float, tol: float, ranks, mode="pcg"):
+    """Predicted iterations against r (the analysis behind Fig. 1b): for each r
+    in `ranks`, lambda_{r+1} is taken from the descending spectrum `lam`."""
+    rows = []
+    for r in ranks:
+        lam_next = 1.0 if r == 0 else float(lam[r])
+        kap, ia, ir = cg_bound(mode if r > 0 else "paper", alpha, lam_next, lam_min, tol)
+        rows.append({"r": int(r), "lambda_next": lam_next, "kappa": kap, "iters_anorm": ia, "iters_resid": ir})
+    return rows
+
+
+def filter_poly(ctx: Context, g: Graph, eig, y_ptr, y_idx, y_val, coeffs, X=None, ldx=None):
+    """x = h(W) y for h(A) = sum_i coeffs[i] A^i via Theorem 2 (Eq. 32);
+    X defaults to a new (n x B) device tensor."""
+    import torch
+    B = len(y_ptr) - 1
+    co = np.ascontiguousarray(coeffs, dtype=np.float64)
+    yp, yi, yv = (np.ascontiguousarray(y_ptr, np.int32) if isinstance(y_ptr, np.ndarray) else y_ptr,
+                  np.ascontiguousarray(y_idx, np.int32) if isinstance(y_idx, np.ndarray) else y_idx,
+                  np.ascontiguousarray(y_val, np.float32) if isinstance(y_val, np.ndarray) else y_val)
+    if X is None:
+        X = torch.empty((g.n, B), dtype=torch.float32, device="cuda")
+    ld = ldx if ldx is not None else (X.shape[1] if hasattr(X, "shape") else B)
+    ctx.check(lib().hd_filter_poly(ctx.handle, g.handle, eig.handle if eig is not None else None, B, _ptr(yp),
+                                   _ptr(yi), _ptr(yv), _ptr(co), len(co), _ptr(X), ld), "hd_filter_poly")
+    return X
 
 
 def query_batch(ctx: Context, g: Graph, eig, mode, y_ptr, y_idx, y_val, alpha: float, tol, max_iter: int,

@@ -156,3 +156,58 @@ def test_pooled_and_rank_match():
     ref = np.array([1.0, 1.0 + 1e-9, 0.5])
     assert rank.ranks_match([1, 0, 2], [0, 1, 2], ref, 1e-6)
     assert not rank.ranks_match([2, 0, 1], [0, 1, 2], ref, 1e-6)
+
+
+def test_kappa_deflated_against_dense(small_graph):
+    # Sec. 4.4: W_r keeps r zero eigenvalues; for every r (including r with
+    # lambda_{r+1} < 0, where Eq. 23 alone would not apply) the condition
+    # number of the dense L_alpha(W_r) is the clamped formula.
+    W = small_graph["W"].toarray()
+    lam, U = S.eigh_desc(W)
+    a = 0.99
+    seen_negative = False
+    for r in (0, 1, 4, 20, 45, 58):
+        Wr = S.deflated(W, U[:, :r], lam[:r])
+        Lr = (np.eye(60) - a * Wr) / (1 - a)
+        lam_next = lam[r] if r > 0 else 1.0
+        seen_negative |= lam_next < 0
+        assert S.kappa_of(Lr) == pytest.approx(S.kappa_deflated(a, lam_next, lam[-1]), rel=1e-9)
+    assert seen_negative
+
+
+@pytest.mark.parametrize("tol", [1e-2, 1e-4, 1e-6])
+def test_iteration_bound_holds_for_cg_and_pcg(small_graph, tol):
+    # Eq. 21 turned into an iteration count: CG on the deflated operator (Form P)
+    # and PCG with exact eigenpairs (Form S) never need more iterations than the
+    # bound for the residual stopping rule, and the A-norm error is below tol
+    # after iters_anorm iterations.
+    W = small_graph["W"]
+    Wd = W.toarray()
+    a = 0.99
+    lam, U = S.eigh_desc(Wd)
+    Y = np.zeros((60, 3))
+    Y[[3, 17, 40], 0] = [1.0, 0.5, 0.25]
+    Y[[5, 6], 1] = [1.0, 1.0]
+    Y[:, 2] = np.random.default_rng(4).random(60)
+    L = (np.eye(60) - a * Wd) / (1 - a)
+    kap_L = S.kappa_of(L)
+    for r in (0, 3, 12):
+        lam_next = lam[r] if r > 0 else 1.0
+        kap = S.kappa_deflated(a, lam_next, lam[-1])
+        Lr = (np.eye(60) - a * S.deflated(Wd, U[:, :r], lam[:r])) / (1 - a)
+        i_res = S.cg_iterations_bound(kap, tol, kap)
+        i_a = S.cg_iterations_bound(kap, tol)
+        # minimality of both counts
+        assert np.sqrt(kap) * S.phi(kap, i_res) <= tol < np.sqrt(kap) * S.phi(kap, i_res - 1) if i_res > 0 else True
+        assert S.phi(kap, i_a) <= tol < (S.phi(kap, i_a - 1) if i_a > 0 else np.inf)
+        for j in range(3):
+            y = Y[:, j]
+            xstar = np.linalg.solve(Lr, y)
+            errs = []
+            res = D.cg(lambda z: Lr @ z, y, tol, 500, callback=lambda i, x: errs.append(S.a_norm(Lr, xstar - x)))
+            assert res.converged and res.iters <= i_res
+            if len(errs) > i_a:
+                assert errs[i_a] / errs[0] <= tol
+            if r > 0:
+                _, it = D.hybrid_pcg(W, U[:, :r], lam[:r], y, a, tol, 500)
+                assert it[0] <= S.cg_iterations_bound(kap, tol, kap_L)
