@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--serve-slots", type=int, default=128)
     ap.add_argument("--sweep", type=int, default=1, help="run the storage / rank / batch sweep")
     ap.add_argument("--sweep-batches", default="1,16,256")
+    ap.add_argument("--shortlist", type=int, default=75000, help="Temporal† shortlist size (0: skip the leg)")
+    ap.add_argument("--trunc-iters", type=int, default=20, help="Temporal† CG iterations (Table 1: 20)")
     return ap.parse_args()
 
 
@@ -121,7 +123,14 @@ def build_workload(args, ctx, rank):
     n = args.n or c.n
     d = args.d or c.d
     t0 = time.time()
-    X, _ = synth.database(c.seed, n, d, c.ncl, c.kappa_lo, c.kappa_hi, c.sizes, c.zipf_s)
+    R = c.regions
+    if R > 1:
+        # regional workload: images of R region descriptors, image-major rows
+        n = n // R * R
+        X, _ = synth.regional_database(c.seed, n // R, R, d, c.ncl, c.kappa_lo, c.kappa_hi,
+                                       c.extra.get("p_stay", 0.8))
+    else:
+        X, _ = synth.database(c.seed, n, d, c.ncl, c.kappa_lo, c.kappa_hi, c.sizes, c.zipf_s)
     Xt = torch.from_numpy(X).to(torch.bfloat16 if c.dtype == "bf16" else torch.float32).cuda()
     del X
     t_gen = time.time() - t0
@@ -133,10 +142,16 @@ def build_workload(args, ctx, rank):
     # for the largest batch of the sweep
     bmax = max([args.batch] + ([int(b) for b in args.sweep_batches.split(",") if b] if args.sweep else []))
     nq = 2 * bmax
-    Qv = synth.queries(c.seed + 1000 * rank, nq, d, c.ncl, c.kappa_lo, c.kappa_hi, c.sizes, c.zipf_s)
-    Qt = torch.from_numpy(Qv).to(Xt.dtype).cuda()
-    yp, yi, yv = hd.observe(ctx, Xt, Qt, c.k_y, c.gamma)
-    del Qt
+    if R > 1:
+        # query images drawn like the database's (own seed), one observation per image
+        Qv, _ = synth.regional_database(c.seed + 7000 + 1000 * rank, nq, R, d, c.ncl, c.kappa_lo, c.kappa_hi,
+                                        c.extra.get("p_stay", 0.8))
+        Qt = torch.from_numpy(Qv).to(Xt.dtype).cuda()
+        yp, yi, yv = hd.observe_regional(ctx, Xt, Qt, R, c.k_y, c.gamma)
+    else:
+        Qv = synth.queries(c.seed + 1000 * rank, nq, d, c.ncl, c.kappa_lo, c.kappa_hi, c.sizes, c.zipf_s)
+        Qt = torch.from_numpy(Qv).to(Xt.dtype).cuda()
+        yp, yi, yv = hd.observe(ctx, Xt, Qt, c.k_y, c.gamma)
     yall = (yp, yi, yv)
     B = args.batch
     cal, tim = split_batches(yall, B, bmax)
@@ -151,7 +166,8 @@ def build_workload(args, ctx, rank):
         eig = hd.eig_from_host(ctx, g, lam, U32, args.storage)
     torch.cuda.synchronize()
     t_eig = time.time() - t0
-    return {"cfg": c, "n": n, "d": d, "g": g, "Xt": Xt, "cal": cal, "tim": tim, "yall": yall, "bmax": bmax,
+    return {"cfg": c, "n": n, "d": d, "g": g, "Xt": Xt, "Qt": Qt, "pool": R if R > 1 else 0, "cal": cal, "tim": tim,
+            "yall": yall, "bmax": bmax,
             "eig": eig, "lam": lam, "U32": U32, "res": res, "conv": conv, "t_gen": t_gen, "t_graph": t_graph,
             "t_eig": t_eig}
 
@@ -209,7 +225,7 @@ def time_leg(ctx, wl, eig, mode, tol, alpha, K, W, B, topk, profile, tim=None):
     def step():
         hd.query_batch(ctx, g, eig, mode, ypd, yid, yvd, alpha, told, 2000, X=X, ldx=X.shape[1], iters=itd,
                        relres=rrd, status=std)
-        hd.rank(ctx, X[:, :B], Kh, topk, idx=idx, score=sc)
+        hd.rank(ctx, X[:, :B], Kh, topk, pool=wl["pool"], idx=idx, score=sc)
 
     for _ in range(W):
         step()
@@ -259,7 +275,7 @@ def e2e_leg(ctx, wl, eig, mode, tol, alpha, K, B, topk):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         hd.query_batch(ctx, g, eig, mode, yp, yi, yv, alpha, tolh, 2000, X=X, ldx=X.shape[1])
-        hd.rank(ctx, X[:, :B], Kh, topk, idx=idx, score=sc)
+        hd.rank(ctx, X[:, :B], Kh, topk, pool=wl["pool"], idx=idx, score=sc)
         torch.cuda.synchronize()
         if k:
             times.append(time.perf_counter() - t0)
@@ -374,6 +390,45 @@ def sweep_leg(ctx, wl, args, alpha):
         run(f"{args.mode} r={args.r} B={b}", wl["eig"], args.mode, b, r=args.r, storage=args.storage)
         run(f"cg r=0 B={b}", None, "paper", b, r=0, storage=None)
     return out
+
+
+def truncated_leg(ctx, wl, args, alpha, tol_ref):
+    """Temporal† (Sec. 3.1; Table 1: 20 iterations, 75k shortlist): CG on each
+    query's shortlist subgraph.  The shortlists (top-s database items by
+    descriptor similarity, the paper's excluded NN search) are prepared
+    outside the timed region.  Reported with its truncation error against the
+    full-graph solution on the shortlist."""
+    import torch
+    import paper_1807_08692_gb300 as hd
+    B, s = args.batch, min(args.shortlist, wl["n"])
+    bmax = wl["bmax"]
+    Q = wl["Qt"][bmax:bmax + B]
+    sims = (Q.float() @ wl["Xt"].float().T) if wl["Xt"].dtype == torch.float32 else (Q @ wl["Xt"].T).float()
+    sl = torch.topk(sims, s, dim=1).indices.to(torch.int32)
+    del sims
+    sl_idx = sl.reshape(-1).contiguous()
+    sl_ptr = np.arange(B + 1, dtype=np.int32) * s
+    yp, yi, yv = wl["tim"]
+    ypd, yid, yvd = (torch.from_numpy(a).cuda() for a in (yp, yi, yv))
+    X = torch.empty((s, B), dtype=torch.float32, device="cuda")
+    for _ in range(2):
+        hd.temporal_truncated(ctx, wl["g"], sl_ptr, sl_idx, ypd, yid, yvd, alpha, 1e-12, args.trunc_iters, X=X)
+    torch.cuda.synchronize()
+    steps = 5
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        _, it, _, st = hd.temporal_truncated(ctx, wl["g"], sl_ptr, sl_idx, ypd, yid, yvd, alpha, 1e-12,
+                                             args.trunc_iters, X=X)
+    torch.cuda.synchronize()
+    ms = (time.perf_counter() - t0) / steps * 1e3
+    # truncation error: the full solution restricted to each shortlist
+    ref, *_ = hd.query_batch(ctx, wl["g"], wl["eig"], "pcg", yp, yi, yv, alpha, tol_ref, 2000)
+    full = torch.gather(ref, 0, sl.T.long())
+    err = (torch.linalg.norm(full - X, dim=0) / torch.linalg.norm(full, dim=0)).cpu().numpy()
+    return {"shortlist": s, "B": B, "iters": int(np.max(it)), "ms_per_batch": round(ms, 3),
+            "qps": round(B / ms * 1e3, 1), "truncation_rel_err_median": float(np.median(err)),
+            "truncation_rel_err_max": float(np.max(err)),
+            "timing": "host wall clock around the call (subsystem build + CG), inputs resident"}
 
 
 def convergence_leg(ctx, wl, rows_in, alpha):
@@ -521,6 +576,10 @@ def main():
                "d2h_bytes_per_step": int(d2h)}
     # ---- sweep over storage, rank and batch
     sweep = sweep_leg(ctx, wl, args, alpha) if (args.sweep and not args.quick) else None
+    # ---- Temporal† baseline (truncated temporal filtering)
+    trunc = None
+    if not args.quick and args.shortlist > 0 and not wl["pool"]:
+        trunc = truncated_leg(ctx, wl, args, alpha, 1e-7)
     # ---- convergence analysis (Eq. 21-23) against the measured iteration counts
     conv = None
     if not args.quick and wl["lam"] is not None:
@@ -534,7 +593,7 @@ def main():
         conv = convergence_leg(ctx, wl, rows_in, alpha)
     # ---- serving: continuous batching under Poisson load
     serving = None
-    rates = [float(x) for x in args.serve_rates.split(",") if x.strip()]
+    rates = [float(x) for x in args.serve_rates.split(",") if x.strip()] if not wl["pool"] else []
     if rates:
         serving = serve_leg(ctx, wl, eig, args, rates, alpha)
     # ---- roofline of the dominant kernel
@@ -581,7 +640,9 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 (U bf16)" if args.storage == "bf16" else "f32",
         "data": "synthetic vMF mixture (seeded), built on the device",
         "config": {"workload": f"{wl['cfg'].name}: n={wl['n']}, d={wl['d']}, k={wl['cfg'].k}, nnz={wl['g'].nnz}, "
-                               f"B={B} queries/step, k_y={wl['cfg'].k_y}, top-{args.topk}",
+                               f"B={B} queries/step, k_y={wl['cfg'].k_y}, top-{args.topk}"
+                               + (f", regional: {wl['pool']} regions per image, pooled ranking of "
+                                  f"{wl['n'] // wl['pool']} images" if wl["pool"] else ""),
                    "mode": args.mode, "r": args.r, "storage": args.storage, "alpha": alpha, "tol": tol_h,
                    "calib_rel_err": err_h, "iters_max": int(hyb["iters"].max()),
                    "l2": "inputs larger than L2 (graph + U + vectors per step > 129 MB)",
@@ -592,7 +653,7 @@ def main():
                    "setup_s": {"gen": round(wl["t_gen"], 1), "graph": round(wl["t_graph"], 1),
                                "eig": round(wl["t_eig"], 1)}},
         "p50_ms": round(float(np.percentile(hyb["ms"], 50)), 4), "p99_ms": round(float(np.percentile(hyb["ms"], 99)), 4),
-        "cg_r0": cg, "sweep": sweep, "convergence": conv, "serving": serving, "e2e": e2e, "gpu_launches": int(hyb["launches"]), "roofline": roofline, "cpu_baseline": cpu,
+        "cg_r0": cg, "sweep": sweep, "temporal_truncated": trunc, "convergence": conv, "serving": serving, "e2e": e2e, "gpu_launches": int(hyb["launches"]), "roofline": roofline, "cpu_baseline": cpu,
         "clocks": clocks, "wall_s_timed": round(t_wall, 3),
     }
     if rank == 0:

@@ -220,6 +220,32 @@ int hd_eig_destroy(hd_eig* e);
 int hd_eig_project(hd_ctx* ctx, const hd_eig* e, const float* V, int32_t B, double* C_out);
 int hd_eig_expand(hd_ctx* ctx, const hd_eig* e, const double* H, int32_t B, float* X_out);
 
+/* ---- truncated temporal filtering, "Temporal†" (Sec. 3.1, Sec. 5.1) ------- */
+
+/* The baseline the paper compares against at large scale: for query j only
+ * the shortlist S_j (its nearest database items, chosen by the caller) is
+ * kept; the affinity restricted to S_j x S_j is normalised again by its own
+ * degrees, W_j = D_j^-1/2 A_{S_j S_j} D_j^-1/2, and L_alpha(W_j) x_j = y_j
+ * (Eq. 2 on the subgraph) is solved by CG, one system per column.  A is
+ * recovered from the stored graph as W_ik / (d_i^-1/2 d_k^-1/2) (for a graph
+ * given already normalised, A = W).
+ *  sl_ptr[B+1], sl_idx : shortlists (host or device), ids in [0, n), no
+ *             duplicate within a shortlist; s_j = sl_ptr[j+1] - sl_ptr[j] >= 0,
+ *             s_max = max_j s_j >= 1.
+ *  y_ptr, y_idx, y_val : observations as for hd_query_batch, by database id;
+ *             entries outside S_j are dropped.
+ *  X        : output s_max x B (leading dimension ldx >= B), host or device:
+ *             X[t][j] is the score of sl_idx[sl_ptr[j] + t]; rows t >= s_j
+ *             are 0.
+ *  tol, max_iter, iters, relres, status : as for hd_query_batch.
+ * Temporary device memory of about B n 4 bytes (the position maps) plus the B
+ * subsystems is allocated for the call.  Errors: HD_ERR_INVALID_ARG for a bad
+ * or duplicated shortlist id or observation index, HD_ERR_OOM. */
+int hd_temporal_truncated(hd_ctx* ctx, const hd_graph* g, int32_t B, const int32_t* sl_ptr,
+                          const int32_t* sl_idx, const int32_t* y_ptr, const int32_t* y_idx,
+                          const float* y_val, float alpha, const float* tol, int32_t max_iter,
+                          float* X, int32_t ldx, int32_t* iters, float* relres, int32_t* status);
+
 /* ---- general transfer functions (Appendix A) ------------------------------ */
 
 /* x = h(W) y for a transfer function given by its series coefficients

@@ -33,6 +33,18 @@ def observe(Xdb: np.ndarray, Q: np.ndarray, k_y: int, gamma: float = 3.0):
             np.concatenate(val_all) if val_all else np.zeros(0))
 
 
+def observe_regional(Xdb: np.ndarray, Q: np.ndarray, regions: int, k_y: int, gamma: float = 3.0):
+    """Regional queries (reading: one observation per query image): the
+    image's `regions` consecutive rows of Q each contribute their own top-k_y
+    (observe above); the lists are concatenated, so a database item found by
+    several regions carries the sum of their values.  (y_ptr, y_idx, y_val)
+    with one segment per image."""
+    p, i, v = observe(Xdb, Q, k_y, gamma)
+    nimg = (len(p) - 1) // regions
+    ptr = np.asarray([p[j * regions] for j in range(nimg)] + [p[nimg * regions]], dtype=np.int64)
+    return ptr, i, v
+
+
 def dense(n: int, y_ptr, y_idx, y_val) -> np.ndarray:
     """Scatter the sparse columns into a dense n x B float64 array."""
     B = len(y_ptr) - 1

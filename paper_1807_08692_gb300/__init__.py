@@ -6,7 +6,7 @@ Manifold Ranking" (Eq. 17-20), behind the C ABI of include/hd.h.
 """
 from . import hd  # noqa: F401
 from .hd import (  # noqa: F401
-    Context, Graph, Eig, HDError, build_graph, graph_from_csr, knn, observe, eig_from_host,
+    Context, Graph, Eig, HDError, build_graph, graph_from_csr, knn, observe, observe_regional, eig_from_host,
     eigendecompose, query_batch, rank, Server, spectrum_min, cg_bound, convergence_table,
-    filter_poly,
+    filter_poly, temporal_truncated, rank_shortlists,
 )

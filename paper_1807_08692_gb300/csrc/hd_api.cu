@@ -246,6 +246,7 @@ static void graph_free(hd_graph* g) {
     cudaFree(g->col);
     cudaFree(g->val);
     cudaFree(g->dinv);
+    for (auto& kv : g->seg_bounds) cudaFree(kv.second);
     delete g;
 }
 

@@ -69,6 +69,12 @@ struct hd_graph {
     float* dinv = nullptr;    // D^-1/2
     // autotuned SpMM column-slab width per padded batch width (Bp -> S)
     mutable std::map<int, int> slab_cache;
+    // node-range segments of the SpMM: per segment count K, the entry bounds
+    // [K + 1][n] of every row's part in each range of ceil(n / K) columns
+    // (rows are sorted by column, so each part is contiguous); and the K
+    // chosen per padded batch width
+    mutable std::map<int, int32_t*> seg_bounds;
+    mutable std::map<int, int> seg_cache;
 };
 
 struct hd_eig {

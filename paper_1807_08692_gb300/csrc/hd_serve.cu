@@ -195,6 +195,13 @@ int hd_serve_open(hd_ctx* ctx, const hd_graph* g, const hd_eig* eig, int mode, f
     E.num_active = cv.take<int>(16);
     E.err = E.num_active + 1;
     E.vl = vec_launch(ctx, n, Bp, tune_slab(ctx, g, Bp, E.P, E.Q));
+    {
+        const int trc = tune_segments(ctx, E);
+        if (trc) {
+            server_free(s);
+            return trc;
+        }
+    }
     s->d_rec = cv.take<AdmitRec>(Bp);
     s->d_yidx = cv.take<int32_t>(s->cap_nnz);
     s->d_yval = cv.take<float>(s->cap_nnz);

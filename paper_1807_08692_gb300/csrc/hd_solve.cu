@@ -152,6 +152,145 @@ __global__ void __launch_bounds__(256) k_spmm(const int32_t* __restrict__ rp, co
     if (part) block_reduce_cols<S>(acc, part + (int64_t)blockIdx.x * ld + blockIdx.y * S);
 }
 
+// Per-column operators (truncated systems): column j's row t holds the entries
+// off[j * n + t] .. off[j * n + t + 1] of (ci, wv); columns j >= B are empty.
+// Q = c1 P - c2 W_j P column by column; optional partials of P^T Q.
+template <int S>
+__global__ void __launch_bounds__(256) k_spmm_cols(const int64_t* __restrict__ off, const int32_t* __restrict__ ci,
+                                                   const float* __restrict__ wv, int32_t B, const float* __restrict__ P,
+                                                   float* __restrict__ Q, int64_t n, int32_t ld, float c1, float c2,
+                                                   float2* __restrict__ part, const ColState* __restrict__ st) {
+    constexpr int L = S / 4;
+    constexpr int RPB = 256 / L;
+    if (!slab_has_work<S>(st, false)) return;
+    const int g = (threadIdx.x & 31) % L;
+    const int col = blockIdx.y * S + 4 * g;
+    KSum acc[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+    for (int64_t row = (int64_t)blockIdx.x * RPB + threadIdx.x / L; row < n; row += (int64_t)gridDim.x * RPB) {
+        float s[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int j = col + c;
+            if (j >= B) continue;
+            const int64_t f = (int64_t)j * n + row;
+            const int64_t b = __ldg(off + f), e = __ldg(off + f + 1);
+            float s0 = 0.f, s1 = 0.f;
+            int64_t t = b;
+            for (; t + 2 <= e; t += 2) {
+                s0 = fmaf(__ldg(wv + t), __ldg(P + (int64_t)__ldg(ci + t) * ld + j), s0);
+                s1 = fmaf(__ldg(wv + t + 1), __ldg(P + (int64_t)__ldg(ci + t + 1) * ld + j), s1);
+            }
+            if (t < e) s0 = fmaf(__ldg(wv + t), __ldg(P + (int64_t)__ldg(ci + t) * ld + j), s0);
+            s[c] = s0 + s1;
+        }
+        const float4 own = ld4(P + row * ld + col);
+        float4 q;
+        q.x = c1 * own.x - c2 * s[0];
+        q.y = c1 * own.y - c2 * s[1];
+        q.z = c1 * own.z - c2 * s[2];
+        q.w = c1 * own.w - c2 * s[3];
+        st4(Q + row * ld + col, q);
+        if (part) {
+            ksum_add(acc[0], own.x * q.x);
+            ksum_add(acc[1], own.y * q.y);
+            ksum_add(acc[2], own.z * q.z);
+            ksum_add(acc[3], own.w * q.w);
+        }
+    }
+    if (part) block_reduce_cols<S>(acc, part + (int64_t)blockIdx.x * ld + blockIdx.y * S);
+}
+
+// Row i's entries in segment s (columns [s w, (s + 1) w)) are
+// bounds[s n + i] .. bounds[(s + 1) n + i] (rows sorted by column).
+__global__ void k_seg_bounds(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, int64_t n, int K,
+                             int64_t w, int32_t* __restrict__ bounds) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int32_t t = rp[i];
+    const int32_t e = rp[i + 1];
+    bounds[i] = t;
+    for (int s = 1; s < K; ++s) {
+        const int64_t lim = (int64_t)s * w;
+        while (t < e && ci[t] < lim) ++t;
+        bounds[(int64_t)s * n + i] = t;
+    }
+    bounds[(int64_t)K * n + i] = e;
+}
+
+// One node-range segment of Q = c1 P - c2 W P: the gathered rows of P all lie
+// in one range of the nodes, so that range stays in L2 for the pass.  The
+// first segment writes Q, the others subtract into it; the last one also
+// forms the P^T Q partials.
+template <int S>
+__global__ void __launch_bounds__(256) k_spmm_seg(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
+                                                  const int32_t* __restrict__ ci, const float* __restrict__ wv,
+                                                  const float* __restrict__ P, float* __restrict__ Q, int64_t n,
+                                                  int32_t ld, float c1, float c2, float2* __restrict__ part,
+                                                  const ColState* __restrict__ st, int first, int last) {
+    constexpr int L = S / 4;
+    constexpr int RPB = 256 / L;
+    if (!slab_has_work<S>(st, false)) return;
+    const int g = (threadIdx.x & 31) % L;
+    const int col = blockIdx.y * S + 4 * g;
+    KSum acc[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+    for (int64_t row = (int64_t)blockIdx.x * RPB + threadIdx.x / L; row < n; row += (int64_t)gridDim.x * RPB) {
+        const int32_t b = __ldg(lo + row), e = __ldg(hi + row);
+        float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 s2 = make_float4(0.f, 0.f, 0.f, 0.f);
+        int32_t t = b;
+        for (; t + 8 <= e; t += 8) {
+            int32_t j[8];
+            float w[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                j[u] = __ldg(ci + t + u);
+                w[u] = __ldg(wv + t + u);
+            }
+            float4 v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = ld4(P + (int64_t)j[u] * ld + col);
+#pragma unroll
+            for (int u = 0; u < 8; u += 2) {
+                FMA4(s, w[u], v[u]);
+                FMA4(s2, w[u + 1], v[u + 1]);
+            }
+        }
+        for (; t < e; ++t) {
+            const int32_t j0 = __ldg(ci + t);
+            const float w0 = __ldg(wv + t);
+            const float4 v0 = ld4(P + (int64_t)j0 * ld + col);
+            FMA4(s, w0, v0);
+        }
+        s.x += s2.x;
+        s.y += s2.y;
+        s.z += s2.z;
+        s.w += s2.w;
+        float4 q;
+        if (first) {
+            const float4 own = ld4(P + row * ld + col);
+            q.x = c1 * own.x - c2 * s.x;
+            q.y = c1 * own.y - c2 * s.y;
+            q.z = c1 * own.z - c2 * s.z;
+            q.w = c1 * own.w - c2 * s.w;
+        } else {
+            q = ld4v(Q + row * ld + col);
+            q.x -= c2 * s.x;
+            q.y -= c2 * s.y;
+            q.z -= c2 * s.z;
+            q.w -= c2 * s.w;
+        }
+        st4(Q + row * ld + col, q);
+        if (part && last) {
+            const float4 own = ld4(P + row * ld + col);
+            ksum_add(acc[0], own.x * q.x);
+            ksum_add(acc[1], own.y * q.y);
+            ksum_add(acc[2], own.z * q.z);
+            ksum_add(acc[3], own.w * q.w);
+        }
+    }
+    if (part && last) block_reduce_cols<S>(acc, part + (int64_t)blockIdx.x * ld + blockIdx.y * S);
+}
+
 // Partials of sum_i V_ij^2.
 template <int S>
 __global__ void __launch_bounds__(256) k_colsq(const float* __restrict__ V, int64_t n, int32_t ld, float2* part) {
@@ -671,6 +810,104 @@ int hd_spmm_apply(hd_ctx* ctx, const hd_graph* g, const float* P, float* Q, int3
     return HD_OK;
 }
 
+// Q = c1 P - c2 W P with the engine's slab width and segments (+ P^T Q partials)
+static int launch_spmm(Engine& E, float c1, float c2, float2* part, const ColState* st) {
+    hd_ctx* ctx = E.ctx;
+    const hd_graph* g = E.g;
+    dim3 grid(E.vl.nblk, E.vl.slabs);
+    HD_PROF(ctx, "spmm");
+    if (E.segK <= 1) {
+        HD_DISPATCH_S(E.vl.S, (k_spmm<SS><<<grid, 256, 0, ctx->stream>>>(g->row_ptr, g->col, g->val, E.P, E.Q, E.n,
+                                                                          E.Bp, c1, c2, part, st)));
+        HD_CHECK_LAUNCH(ctx);
+        return HD_OK;
+    }
+    for (int s = 0; s < E.segK; ++s) {
+        const int32_t* lo = E.seg + (int64_t)s * E.n;
+        HD_DISPATCH_S(E.vl.S, (k_spmm_seg<SS><<<grid, 256, 0, ctx->stream>>>(
+                                  lo, lo + E.n, g->col, g->val, E.P, E.Q, E.n, E.Bp, c1, c2, part, st, s == 0,
+                                  s == E.segK - 1)));
+        HD_CHECK_LAUNCH(ctx);
+    }
+    return HD_OK;
+}
+
+static const int32_t* seg_bounds_for(hd_ctx* ctx, const hd_graph* g, int K) {
+    auto it = g->seg_bounds.find(K);
+    if (it != g->seg_bounds.end()) return it->second;
+    int32_t* b = nullptr;
+    if (cudaMalloc(&b, (size_t)(K + 1) * g->n * 4) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    const int64_t w = (g->n + K - 1) / K;
+    k_seg_bounds<<<ceil_div(g->n, 256), 256, 0, ctx->stream>>>(g->row_ptr, g->col, g->n, K, w, b);
+    ctx->launches++;
+    if (cudaGetLastError() != cudaSuccess) {
+        cudaFree(b);
+        return nullptr;
+    }
+    g->seg_bounds[K] = b;
+    return b;
+}
+
+int tune_segments(hd_ctx* ctx, Engine& E) {
+    const hd_graph* g = E.g;
+    E.segK = 1;
+    E.seg = nullptr;
+    static int forced = -2;
+    if (forced == -2) {
+        const char* s = getenv("HD_SEGMENTS");
+        forced = s ? atoi(s) : -1;
+    }
+    int K = 1;
+    auto it = g->seg_cache.find(E.Bp);
+    if (forced >= 1) {
+        K = forced;
+    } else if (it != g->seg_cache.end()) {
+        K = it->second;
+    } else if ((int64_t)g->n * E.Bp * 4 > (int64_t)64 << 20) {
+        // gathered block larger than about half of L2: time the candidates
+        float best_ms = 1e30f;
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        for (int k : {1, 2, 4, 8}) {
+            if (k > 1 && !seg_bounds_for(ctx, g, k)) continue;
+            E.segK = k;
+            E.seg = k > 1 ? g->seg_bounds[k] : nullptr;
+            float tot = 0.f;
+            for (int rep = 0; rep < 3; ++rep) {
+                cudaEventRecord(e0, ctx->stream);
+                launch_spmm(E, 1.f, 1.f, nullptr, nullptr);
+                cudaEventRecord(e1, ctx->stream);
+                cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep) tot += ms;
+            }
+            if (tot < best_ms * 0.97f) {
+                best_ms = tot;
+                K = k;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        cudaGetLastError();
+        g->seg_cache[E.Bp] = K;
+    }
+    if (K > 1) {
+        const int32_t* b = seg_bounds_for(ctx, g, K);
+        if (!b) return hd_fail(ctx, HD_ERR_OOM, "SpMM segment bounds");
+        E.segK = K;
+        E.seg = b;
+    } else {
+        E.segK = 1;
+        E.seg = nullptr;
+    }
+    return HD_OK;
+}
+
 // ------------------------------------------------------------------ the solve
 
 
@@ -689,7 +926,6 @@ int hd_spmm_apply(hd_ctx* ctx, const hd_graph* g, const float* P, float* Q, int3
 // scatters newly admitted observations there).
 int engine_iteration(Engine& S_, int (*after_update)(void*), void* arg) {
     hd_ctx* ctx = S_.ctx;
-    const hd_graph* g = S_.g;
     const int64_t n = S_.n;
     const int32_t Bp = S_.Bp;
     const int r = S_.r;
@@ -700,7 +936,7 @@ int engine_iteration(Engine& S_, int (*after_update)(void*), void* arg) {
     const double* Cd = lr_on ? S_.lr.C : nullptr;
     int rc;
     if (eff_mode == HD_MODE_PCG) {
-        LAUNCH_VEC(k_spmm, g->row_ptr, g->col, g->val, S_.P, S_.Q, n, Bp, c1, c2, S_.part, S_.st);
+        if ((rc = launch_spmm(S_, c1, c2, S_.part, S_.st))) return rc;
         { HD_PROF(ctx, "scalar");
         k_fin_sigma<<<Bp, 128, 0, ctx->stream>>>(S_.part, S_.vl.nblk, Bp, S_.st, nullptr, nullptr, 0); }
         HD_CHECK_LAUNCH(ctx);
@@ -715,7 +951,11 @@ int engine_iteration(Engine& S_, int (*after_update)(void*), void* arg) {
         HD_CHECK_LAUNCH(ctx);
         if ((rc = lr_expand(ctx, S_.lr, EXP_DIRECTION, S_.P, S_.R, S_.P, n, Bp, S_.st, S_.num_active))) return rc;
     } else {
-        LAUNCH_VEC(k_spmm, g->row_ptr, g->col, g->val, S_.P, S_.Q, n, Bp, c1, c2, S_.part, S_.st);
+        if (S_.ts)
+            LAUNCH_VEC(k_spmm_cols, S_.ts->off, S_.ts->ci, S_.ts->wv, S_.ts->B, S_.P, S_.Q, n, Bp, c1, c2, S_.part,
+                       S_.st);
+        else if ((rc = launch_spmm(S_, c1, c2, S_.part, S_.st)))
+            return rc;
         if (lr_on) {
             if ((rc = lr_expand(ctx, S_.lr, EXP_ADD_Q, S_.Q, nullptr, nullptr, n, Bp, S_.st, S_.num_active)))
                 return rc;
@@ -753,12 +993,13 @@ static uint64_t fbits(float f) {
 static int run_iterations_graph(Engine& E, int iters) {
     hd_ctx* ctx = E.ctx;
     std::vector<uint64_t> key = {
-        (uint64_t)E.g, (uint64_t)E.g->row_ptr, (uint64_t)E.g->col, (uint64_t)E.g->val, (uint64_t)E.n, (uint64_t)E.lr.e,
+        (uint64_t)E.g, (uint64_t)E.ts, (uint64_t)(E.ts ? E.ts->off : nullptr), (uint64_t)(E.ts ? E.ts->ci : nullptr),
+        (uint64_t)(E.ts ? E.ts->wv : nullptr), (uint64_t)(E.ts ? E.ts->B : 0), (uint64_t)E.g->row_ptr, (uint64_t)E.g->col, (uint64_t)E.g->val, (uint64_t)E.n, (uint64_t)E.lr.e,
         (uint64_t)(E.has_lr ? E.lr.e->U : nullptr), (uint64_t)(E.has_lr ? E.lr.e->storage : -1),
         (uint64_t)(E.has_lr ? E.lr.e->sp_rp : nullptr), (uint64_t)(E.has_lr ? E.lr.e->sp_cp : nullptr), (uint64_t)E.R, (uint64_t)E.P, (uint64_t)E.Q, (uint64_t)E.X,
         (uint64_t)E.part, (uint64_t)E.st, (uint64_t)E.num_active, (uint64_t)E.lr.part, (uint64_t)E.lr.C,
         (uint64_t)E.lr.H, (uint64_t)E.lr.Hhi, (uint64_t)E.lr.Hlo, (uint64_t)E.dcoef, (uint64_t)E.opcoef,
-        (uint64_t)E.Bp, (uint64_t)E.vl.S, (uint64_t)E.vl.nblk, (uint64_t)E.vl.slabs, (uint64_t)E.lr.nchunk,
+        (uint64_t)E.segK, (uint64_t)E.seg, (uint64_t)E.Bp, (uint64_t)E.vl.S, (uint64_t)E.vl.nblk, (uint64_t)E.vl.slabs, (uint64_t)E.lr.nchunk,
         (uint64_t)E.lr.rpad, (uint64_t)E.lr.Bp16, (uint64_t)E.has_lr, (uint64_t)E.eff_mode, (uint64_t)E.r,
         (uint64_t)E.max_iter, (uint64_t)iters, fbits(E.c1), fbits(E.c2),
         fbits(E.xs), (uint64_t)ctx->stream};
@@ -815,7 +1056,17 @@ extern "C" int hd_query_batch(hd_ctx* ctx, const hd_graph* g, const hd_eig* eig,
                               const int32_t* y_ptr, const int32_t* y_idx, const float* y_val, float alpha,
                               const float* tol, int32_t max_iter, float* X, int32_t ldx, int32_t* iters,
                               float* relres, int32_t* status) {
+    return hd_query_impl(ctx, g, nullptr, eig, mode, B, y_ptr, y_idx, y_val, alpha, tol, max_iter, X, ldx, iters,
+                         relres, status);
+}
+
+// The solve behind hd_query_batch; with `ts` the operator is the per-column
+// truncated system (rows = shortlist positions) instead of the graph.
+int hd_query_impl(hd_ctx* ctx, const hd_graph* g, const TruncSys* ts, const hd_eig* eig, int mode, int32_t B,
+                  const int32_t* y_ptr, const int32_t* y_idx, const float* y_val, float alpha, const float* tol,
+                  int32_t max_iter, float* X, int32_t ldx, int32_t* iters, float* relres, int32_t* status) {
     if (!ctx || !g || !y_ptr || !tol || !X) return HD_ERR_INVALID_ARG;
+    if (ts && eig) return hd_fail(ctx, HD_ERR_INVALID_ARG, "truncated systems take no eigenpairs");
     if (B <= 0 || ldx < B) return hd_fail(ctx, HD_ERR_INVALID_ARG, "B=%d ldx=%d", B, ldx);
     if (!(alpha >= 0.0f && alpha < 1.0f)) return hd_fail(ctx, HD_ERR_INVALID_ARG, "alpha=%g not in [0,1)", alpha);
     if (mode != HD_MODE_PAPER && mode != HD_MODE_PROJ && mode != HD_MODE_PCG)
@@ -827,7 +1078,8 @@ extern "C" int hd_query_batch(hd_ctx* ctx, const hd_graph* g, const hd_eig* eig,
     Engine S_;
     S_.ctx = ctx;
     S_.g = g;
-    S_.n = g->n;
+    S_.ts = ts;
+    S_.n = ts ? ts->smax : g->n;
     S_.B = B;
     S_.Bp = (B + 3) / 4 * 4;
     S_.vl = vec_launch(ctx, S_.n, S_.Bp, pick_slab(S_.Bp));
@@ -922,7 +1174,8 @@ extern "C" int hd_query_batch(hd_ctx* ctx, const hd_graph* g, const hd_eig* eig,
     }
 
     // ---------------- setup
-    S_.vl = vec_launch(ctx, n, Bp, tune_slab(ctx, g, Bp, S_.P, S_.Q));
+    S_.vl = vec_launch(ctx, n, Bp, ts ? pick_slab(Bp) : tune_slab(ctx, g, Bp, S_.P, S_.Q));
+    if (!ts && (rc = tune_segments(ctx, S_))) return rc;
     const int eff_mode = lr_on ? mode : HD_MODE_PAPER;
     const double a = alpha;
     float c1, c2, xs = 1.0f;

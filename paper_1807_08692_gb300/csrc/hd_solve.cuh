@@ -65,12 +65,26 @@ struct VecLaunch {
     int slabs;   // grid.y
 };
 
+// Truncated temporal systems (one per column): row t of column j has the
+// entries off[j * smax + t] .. off[j * smax + t + 1] of (ci, wv), ci a row
+// index of the same column's system; columns j >= B are empty.
+struct TruncSys {
+    const int64_t* off = nullptr;
+    const int32_t* ci = nullptr;
+    const float* wv = nullptr;
+    int32_t B = 0;
+    int64_t smax = 0;
+};
+
 struct Engine {
     hd_ctx* ctx = nullptr;
     const hd_graph* g = nullptr;
+    const TruncSys* ts = nullptr;   // per-column operators instead of g (truncated temporal)
     int64_t n = 0;
     int32_t B = 0, Bp = 0;
     VecLaunch vl{};
+    int segK = 1;                      // SpMM node-range segments (1: one pass)
+    const int32_t* seg = nullptr;      // their row bounds [segK + 1][n]
     float *R = nullptr, *P = nullptr, *Q = nullptr, *X = nullptr;
     float2* part = nullptr;
     ColState* st = nullptr;
@@ -90,4 +104,10 @@ VecLaunch vec_launch(hd_ctx* ctx, int64_t n, int32_t Bp, int S = 0);
 // per (graph, Bp) over the widths dividing Bp (HD_SLAB overrides).
 int tune_slab(hd_ctx* ctx, const hd_graph* g, int32_t Bp, const float* P, float* Q);
 int simt_nchunk(hd_ctx* ctx, int64_t n, int rpad, int Bp);
+// Node-range segments for the SpMM with slab width S: measured once per
+// (graph, Bp) over K in {1, 2, 4, 8} (HD_SEGMENTS overrides); sets E.segK / E.seg.
+int tune_segments(hd_ctx* ctx, Engine& E);
 int engine_iteration(Engine& E, int (*after_update)(void*), void* arg);
+int hd_query_impl(hd_ctx* ctx, const hd_graph* g, const TruncSys* ts, const hd_eig* eig, int mode, int32_t B,
+                  const int32_t* y_ptr, const int32_t* y_idx, const float* y_val, float alpha, const float* tol,
+                  int32_t max_iter, float* X, int32_t ldx, int32_t* iters, float* relres, int32_t* status);

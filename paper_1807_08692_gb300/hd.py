@@ -57,6 +57,7 @@ _SIGS = {
     "hd_eig_info": (C.c_int, [vp, C.POINTER(i32), C.POINTER(C.c_int)]),
     "hd_eig_sparsify": (C.c_int, [vp, vp, f64, C.POINTER(vp)]),
     "hd_filter_poly": (C.c_int, [vp, vp, vp, i32, vp, vp, vp, vp, i32, vp, i32]),
+    "hd_temporal_truncated": (C.c_int, [vp, vp, i32, vp, vp, vp, vp, vp, f32, vp, i32, vp, i32, vp, vp, vp]),
     "hd_eig_nnz": (C.c_int, [vp, C.POINTER(C.c_int64)]),
     "hd_eig_export": (C.c_int, [vp, vp, vp, vp]),
     "hd_eig_destroy": (C.c_int, [vp]),
@@ -313,6 +314,15 @@ def observe(ctx: Context, X, Q, k_y: int, gamma: float = 3.0):
     return ptr, idx[:m].copy(), val[:m].copy()
 
 
+def observe_regional(ctx: Context, X, Q, regions: int, k_y: int, gamma: float = 3.0):
+    """Regional queries: each image's `regions` consecutive rows of Q observe
+    their own top-k_y and the image's observation is the concatenation (the
+    solver sums duplicate ids).  (y_ptr, y_idx, y_val), one segment per image."""
+    p, i, v = observe(ctx, X, Q, k_y, gamma)
+    nimg = (len(p) - 1) // regions
+    return np.ascontiguousarray(p[::regions][:nimg + 1], np.int32), i, v
+
+
 def eig_from_host(ctx: Context, g: Graph, lam, U, storage="bf16") -> Eig:
     lam = np.ascontiguousarray(lam, dtype=np.float64)
     r = lam.size
@@ -413,6 +423,44 @@ def query_batch(ctx: Context, g: Graph, eig, mode, y_ptr, y_idx, y_val, alpha: f
                               _ptr(relres), _ptr(status))
     ctx.check(rc, "hd_query_batch")
     return X, iters, relres, status
+
+
+def temporal_truncated(ctx: Context, g: Graph, sl_ptr, sl_idx, y_ptr, y_idx, y_val, alpha: float, tol,
+                       max_iter: int, X=None):
+    """Temporal† (Sec. 3.1): CG on each query's shortlist subgraph.  Returns
+    (X, iters, relres, status) with X (s_max x B) holding shortlist-position
+    scores: X[t, j] belongs to sl_idx[sl_ptr[j] + t]."""
+    import torch
+    B = len(sl_ptr) - 1
+    slp = np.ascontiguousarray(sl_ptr, np.int32)
+    smax = int(np.max(np.diff(slp)))
+    if np.isscalar(tol):
+        tol = np.full(B, tol, np.float32)
+    tol = np.ascontiguousarray(tol, dtype=np.float32)
+    if X is None:
+        X = torch.empty((smax, B), dtype=torch.float32, device=f"cuda:{ctx.device}")
+    iters = np.zeros(B, np.int32)
+    relres = np.zeros(B, np.float32)
+    status = np.zeros(B, np.int32)
+    sli = np.ascontiguousarray(sl_idx, np.int32) if isinstance(sl_idx, np.ndarray) else sl_idx
+    ctx.check(lib().hd_temporal_truncated(ctx.handle, g.handle, B, _ptr(slp), _ptr(sli), _ptr(y_ptr), _ptr(y_idx),
+                                          _ptr(y_val), alpha, _ptr(tol), max_iter, _ptr(X), X.shape[1], _ptr(iters),
+                                          _ptr(relres), _ptr(status)), "hd_temporal_truncated")
+    return X, iters, relres, status
+
+
+def rank_shortlists(ctx: Context, X, sl_ptr, sl_idx, K: int):
+    """Top-K of truncated scores (s_max x B), mapped back to database ids:
+    (ids, scores), each B x K; ids are -1 past a shortlist's end."""
+    slp = np.asarray(sl_ptr, np.int64)
+    sli = np.asarray(sl_idx)
+    pos, sc = rank(ctx, X, K)
+    ids = np.full(pos.shape, -1, np.int64)
+    for j in range(pos.shape[0]):
+        s = slp[j + 1] - slp[j]
+        ok = (pos[j] >= 0) & (pos[j] < s)
+        ids[j, ok] = sli[slp[j] + pos[j, ok]]
+    return ids, sc
 
 
 def rank(ctx: Context, X, K, Kmax: int | None = None, pool: int = 0, n: int | None = None, idx=None, score=None):

@@ -60,7 +60,7 @@ def test_poly_edge_cases(gpu_ctx, cfg1_data):
     import paper_1807_08692_gb300 as hd
     g, args = _setup(gpu_ctx, cfg1_data)
     X = hd.filter_poly(gpu_ctx, g, None, *args, [2.5]).cpu().numpy()
-    assert np.array_equal(X, (2.5 * cfg1_data["Y"]).astype(np.float32))
+    assert np.array_equal(X, np.float32(2.5) * cfg1_data["Y"].astype(np.float32))
     # host output buffer, sparse eigenpairs
     eig = hd.eig_from_host(gpu_ctx, g, cfg1_data["lam"][:20], cfg1_data["U"][:, :20], "bf16").sparsify(0.9)
     n, B = cfg1_data["Y"].shape

@@ -218,3 +218,43 @@ def test_graph_replay_equals_eager_launches(gpu_ctx, g1, cfg1_data):
     for (Xg, itg, _, stg), (Xr, itr, _, str_) in zip(got, ref):
         assert np.array_equal(Xg.cpu().numpy().view(np.uint32), Xr.cpu().numpy().view(np.uint32))
         assert np.array_equal(itg, itr) and np.array_equal(stg, str_)
+
+
+def test_segmented_spmm_matches_single_pass(gpu_ctx, g1, cfg1_data, tmp_path):
+    # Large graphs run the SpMM as K node-range passes (the gathered rows of
+    # each pass stay in L2); a fresh process with HD_SEGMENTS forces K on this
+    # small graph.  Every K reaches the closed form; iteration counts agree.
+    import os
+    import subprocess
+    import sys
+    here = os.path.dirname(os.path.abspath(__file__))
+    np.savez(tmp_path / "case.npz", rp=csr_of(cfg1_data["A"])[0], col=csr_of(cfg1_data["A"])[1],
+             val=csr_of(cfg1_data["A"])[2], yp=cfg1_data["yp"], yi=cfg1_data["yi"], yv=cfg1_data["yv"],
+             lam=cfg1_data["lam"][:30], U=cfg1_data["U"][:, :30])
+    script = (
+        "import sys, numpy as np\n"
+        f"sys.path.insert(0, {os.path.dirname(here)!r}); sys.path.insert(0, {here!r})\n"
+        "import paper_1807_08692_gb300 as hd\n"
+        "from _helpers import y_arrays\n"
+        f"z = np.load({str(tmp_path / 'case.npz')!r})\n"
+        "ctx = hd.Context(0)\n"
+        "g = hd.graph_from_csr(ctx, z['rp'], z['col'], z['val'])\n"
+        "eig = hd.eig_from_host(ctx, g, z['lam'], z['U'], 'bf16')\n"
+        "args = y_arrays(z['yp'], z['yi'], z['yv'])\n"
+        "out = {}\n"
+        "for m, e in (('paper', None), ('pcg', eig)):\n"
+        "    X, it, rr, st = hd.query_batch(ctx, g, e, m, *args, 0.99, 1e-6, 500)\n"
+        "    out[m + '_X'] = X.cpu().numpy(); out[m + '_it'] = it; out[m + '_st'] = st\n"
+        f"np.savez(sys.argv[1], **out)\n")
+    res = {}
+    for K in (1, 3, 8):
+        env = dict(os.environ, HD_SEGMENTS=str(K))
+        outp = tmp_path / f"out{K}.npz"
+        subprocess.run([sys.executable, "-c", script, str(outp)], env=env, check=True, timeout=300)
+        res[K] = np.load(outp)
+    for K in (1, 3, 8):
+        for m in ("paper", "pcg"):
+            assert np.all(res[K][m + "_st"] == 0)
+            err = rel_l2_cols(res[K][m + "_X"].astype(np.float64), cfg1_data["xstar"])
+            assert err.max() <= TOL_REL, (K, m, err.max())
+            assert np.all(np.abs(res[K][m + "_it"] - res[1][m + "_it"]) <= 1)

@@ -136,3 +136,61 @@ def test_1m_workload_properties(gpu_ctx):
     for j in range(c.batch):
         ref, rs = ORank.topk(x[:, j].astype(np.float32), 100)
         assert np.array_equal(ids[j], ref)
+
+
+@pytest.mark.slow
+def test_5m_regional_workload_properties(gpu_ctx):
+    """cfg5: 240,000 images x 21 regions (n = 5.04M), d=512 bf16, k=50,
+    r=100 fp8 eigenpairs, B=128 regional queries pooled per image."""
+    import torch
+    import paper_1807_08692_gb300 as hd
+    c = synth.get_config("cfg5")
+    R = c.regions
+    n_img = c.extra["images"]
+    X, img = synth.regional_database(c.seed, n_img, R, c.d, c.ncl, c.kappa_lo, c.kappa_hi, c.extra["p_stay"])
+    Xb = synth.round_bf16(X)
+    del X
+    Xt = torch.from_numpy(Xb).to(torch.bfloat16).cuda()
+    g = hd.build_graph(gpu_ctx, Xt, c.k, c.gamma)
+    n = g.n
+    assert n == n_img * R
+    rp, col, val, dinv = g.export()
+    # graph rows sampled against the oracle's brute force
+    rng = np.random.default_rng(5)
+    rows = rng.choice(n, 8, replace=False)
+    ridx, rsim = graph.knn_rows(Xb, rows, c.k)
+    for t, i in enumerate(rows):
+        got = set(col[rp[i]:rp[i + 1]].tolist())
+        for jpos, j in enumerate(ridx[t]):
+            if j not in got:
+                assert rsim[t, jpos] - rsim[t, -1] <= 2e-5
+    Qv, _ = synth.regional_database(c.seed + 7000, c.batch, R, c.d, c.ncl, c.kappa_lo, c.kappa_hi,
+                                    c.extra["p_stay"])
+    Qt = torch.from_numpy(Qv).to(torch.bfloat16).cuda()
+    yp, yi, yv = hd.observe_regional(gpu_ctx, Xt, Qt, R, c.k_y, c.gamma)
+    assert len(yp) == c.batch + 1
+    # the regional observations are the sum of the regions' own observations
+    p1, i1, v1 = hd.observe(gpu_ctx, Xt, Qt[:R], c.k_y, c.gamma)
+    assert np.array_equal(np.sort(yi[:yp[1]]), np.sort(i1))
+    del Xt, Qt
+    eig, lam, res, conv = hd.eigendecompose(gpu_ctx, g, 100, block=32, tol=1e-5, max_restarts=2, storage="fp8")
+    Xg, it, rr, st = hd.query_batch(gpu_ctx, g, eig, "pcg", yp, yi, yv, c.alpha, 1e-6, 1000)
+    assert np.all(st == 0)
+    x = Xg.cpu().numpy()
+    # true residual of L_a(W) x = y on sampled rows (each entry is bounded by ||res||)
+    colj = np.repeat(np.arange(c.batch), np.diff(yp))
+    Ysp = sp.csr_matrix((yv.astype(np.float64), (yi, colj)), shape=(n, c.batch))  # duplicates summed
+    ynorm = np.sqrt(np.asarray(Ysp.multiply(Ysp).sum(axis=0)).ravel())
+    W = sp.csr_matrix((val.astype(np.float64), col, rp), shape=(n, n))
+    sample = np.sort(rng.choice(n, 2000, replace=False))
+    Ws = W[sample]
+    touched = np.unique(Ws.indices)
+    Wx = Ws[:, touched] @ x[touched].astype(np.float64)
+    res_rows = Ysp[sample].toarray() - (x[sample].astype(np.float64) - c.alpha * Wx) / (1.0 - c.alpha)
+    assert np.max(np.abs(res_rows) / ynorm) <= 2e-5
+    # pooled ranking: per-image sums of the 21 region scores, exact top-100
+    ids, scores = hd.rank(gpu_ctx, Xg, 100, pool=R)
+    pooled = x.reshape(n_img, R, c.batch).astype(np.float64).sum(axis=1)
+    for j in range(c.batch):
+        ref, _ = ORank.topk(pooled[:, j], 100)
+        assert ORank.ranks_match(ids[j], ref, pooled[:, j], 1e-5 * pooled[:, j].max()), j

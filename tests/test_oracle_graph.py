@@ -101,3 +101,19 @@ def test_observe_dense_scatter():
     Y = observe.dense(5, ptr, np.array([1, 4, 0]), np.array([0.5, 0.25, 2.0]))
     assert Y.shape == (5, 2)
     assert Y[1, 0] == 0.5 and Y[4, 0] == 0.25 and Y[0, 1] == 2.0 and Y.sum() == 2.75
+
+
+def test_observe_regional_is_the_sum_of_region_observations():
+    # reading for regional queries: an image's observation vector is the sum of
+    # its regions' observation vectors (computed one region at a time here)
+    X, _ = synth.database(6, 50, 5, 3, 10.0, 10.0)
+    Q = synth.queries(6, 3 * 4, 5, 3, 10.0, 10.0)
+    ptr, idx, val = observe.observe_regional(X, Q, 4, 5, 3.0)
+    Y = observe.dense(50, ptr, idx, val)
+    assert Y.shape == (50, 3)
+    for img in range(3):
+        want = np.zeros(50)
+        for reg in range(4):
+            p1, i1, v1 = observe.observe(X, Q[img * 4 + reg], 5, 3.0)
+            want += observe.dense(50, p1, i1, v1)[:, 0]
+        assert np.allclose(Y[:, img], want, rtol=0, atol=0)

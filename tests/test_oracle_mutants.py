@@ -10,9 +10,14 @@ import pytest
 import test_oracle_diffusion as TD
 import test_oracle_graph as TG
 import test_oracle_spectral as TS
+import test_oracle_truncated as TT
 from oracle import diffusion as D
 from oracle import graph as G
+from oracle import observe as O
 from oracle import rank as R
+from oracle import shybrid as SH
+from oracle import spectral as SP
+from oracle import truncated as T
 
 
 def _g_no_one_minus_alpha(lam, alpha):
@@ -63,6 +68,38 @@ def _g_transposed_basis(U1, lam1, Y, alpha):
     return U1 @ (D.g_alpha(lam1, alpha)[:, None] * (U1.T @ Y))[::-1]
 
 
+def _subsystem_not_renormalised(A, S):
+    W, dinv = G.normalize(A)
+    S = np.asarray(S, dtype=np.int64)
+    return W[S][:, S].tocsr(), dinv[S]
+
+
+def _kappa_unclamped(alpha, lam_next, lam_min):
+    return (1.0 - alpha * lam_min) / (1.0 - alpha * lam_next)
+
+
+def _bound_one_short(kappa, tol, kappa_res=1.0):
+    i = 0
+    while np.sqrt(kappa_res) * float(SP.phi(kappa, i)) > tol:
+        i += 1
+    return max(i - 1, 0)
+
+
+def _sparsify_earlier_first(U1, sparsity):
+    U = np.asarray(U1, dtype=np.float64)
+    flat = U.ravel()
+    drop = int(round(sparsity * flat.size))
+    order = np.lexsort((np.arange(flat.size), np.abs(flat)))
+    out = flat.copy()
+    out[order[:drop]] = 0.0
+    return out.reshape(U.shape)
+
+
+def _regional_first_region_only(Xdb, Q, regions, k_y, gamma=3.0):
+    p, i, v = O.observe(Xdb, Q[::regions], k_y, gamma)
+    return p, i, v
+
+
 MUTANTS = [
     ("g drops (1-alpha)", D, "g_alpha", _g_no_one_minus_alpha,
      lambda g: TD.test_hybrid_every_rank_equals_closed_form(g, 5)),
@@ -80,6 +117,16 @@ MUTANTS = [
      lambda g: TG.test_adjacency_matches_loops("union")),
     ("spectral term rows permuted", D, "spectral_term", _g_transposed_basis,
      lambda g: TD.test_hybrid_every_rank_equals_closed_form(g, 17)),
+    ("truncated subgraph not renormalised", T, "subsystem", _subsystem_not_renormalised,
+     lambda g: TT.test_matches_dense_solve_built_by_loops(TT.make_g80())),
+    ("deflated kappa unclamped", SP, "kappa_deflated", _kappa_unclamped,
+     lambda g: TS.test_kappa_deflated_against_dense(g)),
+    ("iteration bound one short", SP, "cg_iterations_bound", _bound_one_short,
+     lambda g: TS.test_iteration_bound_holds_for_cg_and_pcg(g, 1e-4)),
+    ("sparsify drops the earlier tie", SH, "sparsify", _sparsify_earlier_first,
+     lambda g: TS.test_sparsify_keeps_largest_magnitudes()),
+    ("regional observation from one region", O, "observe_regional", _regional_first_region_only,
+     lambda g: TG.test_observe_regional_is_the_sum_of_region_observations()),
 ]
 
 

@@ -8,11 +8,15 @@ from oracle import diffusion as D
 from oracle import graph, truncated as T
 
 
-@pytest.fixture(scope="module")
-def g80():
+def make_g80():
     X, _ = synth.database(41, 80, 12, 4, 30.0, 30.0)
     A = graph.adjacency(X, 7)
     return X, A
+
+
+@pytest.fixture(scope="module")
+def g80():
+    return make_g80()
 
 
 def test_full_shortlist_is_temporal(g80):
