@@ -201,7 +201,7 @@ def calibrate(ctx, wl, eig, mode, alpha, cal=None):
 
 
 # ------------------------------------------------------------------ timed legs
-FAMILIES = ["spmm", "update", "direction", "lr_reduce", "lr_expand", "scalar", "rank"]
+FAMILIES = ["spmm", "dot", "update", "direction", "lr_reduce", "lr_expand", "scalar", "rank"]
 
 
 def time_leg(ctx, wl, eig, mode, tol, alpha, K, W, B, topk, profile, tim=None):
@@ -295,7 +295,7 @@ SPMM_NCU = {"dram_bytes": 11657710000, "nnz": 62097728, "n": 1000000, "B": 64,
 def spmm_source_sha1():
     import hashlib
     src = open(os.path.join(ROOT, "paper_1807_08692_gb300", "csrc", "hd_solve.cu")).read()
-    a = src.index("__global__ void __launch_bounds__(256) k_spmm(")
+    a = src.index("k_spmm(const int32_t* rp,")
     b = src.index("\n}\n", a)
     return hashlib.sha1(src[a:b].encode()).hexdigest()
 
@@ -319,6 +319,7 @@ def algorithmic_bytes(wl, B, eig):
         ub = n * ldu * su[{0: "f32", 1: "bf16", 2: "fp8"}[eig.storage]]
     return {
         "spmm": 8 * nnz + 4 * (n + 1) + 2 * vec,      # W (col + val), row_ptr, P once, Q
+        "dot": 2 * vec,                                 # read P, Q (P^T Q partials)
         "update": 6 * vec,                              # read X, R, P, Q; write X, R
         "direction": 3 * vec,                           # read R, P; write P
         "lr_reduce": ub + vec,                          # U and R once
