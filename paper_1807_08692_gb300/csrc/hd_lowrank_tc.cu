@@ -32,6 +32,7 @@ constexpr int CONV = 128;         // converter threads (warps 10-13) for FP8 sto
 constexpr int CSTAGES = 2;        // converted bf16 A stages for FP8 storage
 constexpr int RAW_X = BM * BK;    // raw fp8 expansion stage: 128 rows x 64 codes
 constexpr int RAW_R = BM * 128;   // raw fp8 reduction stage: 128 rows x 128 codes
+constexpr int STAGE_BYTES = (EPI / 32) * 32 * 32 * 4;  // expansion epilogue: 32 x 32 fp32 per warp
 }  // namespace
 
 // 16 e4m3 codes -> 16 bf16 values (both exact), as two 16-byte chunks
@@ -124,7 +125,8 @@ __global__ void __launch_bounds__(THREADS + (SU ? CONV : 0), 1)
     uint8_t* Raw = As + NA * TILE_BYTES;          // raw fp8 stages (SU only)
     uint8_t* Bhi = Raw + (SU ? XSTAGES * RAW_X : 0);
     uint8_t* Blo = Bhi + a.nkb * btile;
-    uint64_t* bars = (uint64_t*)(Blo + a.nkb * btile);
+    float* stage = reinterpret_cast<float*>(Blo + a.nkb * btile);  // epilogue transposition, 4 KB per warp
+    uint64_t* bars = (uint64_t*)(reinterpret_cast<uint8_t*>(stage) + STAGE_BYTES);
     uint64_t* full = bars;
     uint64_t* empty = full + XSTAGES;
     uint64_t* bfull = empty + XSTAGES;
@@ -273,89 +275,111 @@ __global__ void __launch_bounds__(THREADS + (SU ? CONV : 0), 1)
         }
     } else {
         // epilogue: warps 2-9; lane quarter (warp % 4) gives the TMEM lanes (rows),
-        // the two warps of a quarter split the 16-column chunks.  The global
-        // operands of a tile's first two chunks are loaded one tile ahead, so
-        // their latency overlaps the MMAs of that tile.
+        // the two warps of a quarter split the 16-column chunks, 32 columns at a
+        // time.  Each thread reads its row's accumulators from TMEM and parks
+        // them in a per-warp shared tile (16-byte chunks XOR-swizzled by row, so
+        // both the row-wise writes and the column-wise reads are conflict-free);
+        // the global side then runs with lanes across columns, 8 rows x 4
+        // columns per thread, so every warp access covers 4 rows x 128 bytes.
+        // The global operands of a tile's first 32 columns are loaded one tile
+        // ahead, overlapping the MMAs of that tile.
         const int quarter = warp & 3;
         const int half = (warp - 2) >> 2;
         const int rloc = quarter * 32 + lane;
         const int nch = a.Nc / 16;
         const int nh = (nch + 1) / 2;
         const int cb = half ? nh : 0, ce = half ? nch : nh;
-        float4 g1[2][4], g2[2][4];
-        auto load_ops = [&](int64_t row_, int c0_) {
+        const int sr = lane >> 3, ch = lane & 7;  // global-side mapping: row offset, 16-byte column chunk
+        float4* stg = reinterpret_cast<float4*>(stage) + (warp - 2) * 256;  // 32 rows x 8 chunks
+        float4 g1[8], g2[8];
+        auto load_ops = [&](int t_, int c0_) {
+            const int j = a.c0 + c0_ * 16 + 4 * ch;
+            const bool colok = c0_ + (ch >> 2) < ce && j < a.Bp && a.op != EXP_SET_X;
 #pragma unroll
-            for (int u = 0; u < 2; ++u)
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int j = a.c0 + (c0_ + u) * 16 + 4 * q;
-                    g1[u][q] = g2[u][q] = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (row_ >= a.n || c0_ + u >= ce || j >= a.Bp || a.op == EXP_SET_X) continue;
-                    if (a.op == EXP_DIRECTION) {
-                        g1[u][q] = *reinterpret_cast<const float4*>(a.R + row_ * a.Bp + j);
-                        g2[u][q] = *reinterpret_cast<const float4*>(a.P + row_ * a.Bp + j);
-                    } else {
-                        g1[u][q] = *reinterpret_cast<const float4*>(a.out + row_ * a.Bp + j);
-                    }
+            for (int k = 0; k < 8; ++k) {
+                const int64_t row_ = (int64_t)t_ * BM + quarter * 32 + sr + 4 * k;
+                g1[k] = g2[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (!colok || row_ >= a.n) continue;
+                if (a.op == EXP_DIRECTION) {
+                    g1[k] = *reinterpret_cast<const float4*>(a.R + row_ * a.Bp + j);
+                    g2[k] = *reinterpret_cast<const float4*>(a.P + row_ * a.Bp + j);
+                } else {
+                    g1[k] = *reinterpret_cast<const float4*>(a.out + row_ * a.Bp + j);
                 }
+            }
         };
-        if ((int)blockIdx.x < ntiles && cb < ce) load_ops((int64_t)blockIdx.x * BM + rloc, cb);
+        if ((int)blockIdx.x < ntiles && cb < ce) load_ops(blockIdx.x, cb);
         uint32_t tcount = 0;
         bool ok = true;
         for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tcount) {
             const int ab = tcount & 1;
             const int64_t row = (int64_t)t * BM + rloc;
-            const bool live = row < a.n;
-            const float rsc = (SU && live) ? __ldg(a.scale + row) : 1.0f;
+            const float rsc = (SU && row < a.n) ? __ldg(a.scale + row) : 1.0f;
             if (!tc::mbar_wait(&acc_full[ab], (tcount >> 1) & 1, abort_flag)) {
                 ok = false;
                 break;
             }
             tc::fence_after_sync();
             for (int c0 = cb; c0 < ce; c0 += 2) {
-                if (c0 != cb) load_ops(row, c0);
+                if (c0 != cb) load_ops(t, c0);
 #pragma unroll
                 for (int u = 0; u < 2; ++u) {
                     if (c0 + u >= ce) break;
-                    const int c = c0 + u;
                     float v[16];
-                    tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + ab * a.Nc + c * 16, v);
+                    tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + ab * a.Nc + (c0 + u) * 16, v);
                     tc::tmem_ld_wait();
-                    if (!live) continue;
-                    if (SU) {
-#pragma unroll
-                        for (int q = 0; q < 16; ++q) v[q] *= rsc;
-                    }
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
-                        const int j = a.c0 + c * 16 + 4 * q;
-                        if (j >= a.Bp) break;
-                        float4 w;
-                        if (a.op == EXP_SET_X) {
-                            w = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-                        } else if (a.op == EXP_SUB_R) {
-                            w = g1[u][q];
-                            w.x -= v[4 * q]; w.y -= v[4 * q + 1]; w.z -= v[4 * q + 2]; w.w -= v[4 * q + 3];
-                        } else if (a.op == EXP_ADD_Q) {
-                            w = g1[u][q];
-                            w.x += v[4 * q]; w.y += v[4 * q + 1]; w.z += v[4 * q + 2]; w.w += v[4 * q + 3];
-                        } else {
-                            const float4 rr = g1[u][q], pp = g2[u][q];
-                            const float b0 = (float)a.st[j].beta, b1 = (float)a.st[j + 1].beta;
-                            const float b2 = (float)a.st[j + 2].beta, b3 = (float)a.st[j + 3].beta;
-                            w.x = rr.x + v[4 * q] + (b0 == 0.0f ? 0.0f : b0 * pp.x);
-                            w.y = rr.y + v[4 * q + 1] + (b1 == 0.0f ? 0.0f : b1 * pp.y);
-                            w.z = rr.z + v[4 * q + 2] + (b2 == 0.0f ? 0.0f : b2 * pp.z);
-                            w.w = rr.w + v[4 * q + 3] + (b3 == 0.0f ? 0.0f : b3 * pp.w);
+                        float4 w4 = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                        if (SU) {
+                            w4.x *= rsc;
+                            w4.y *= rsc;
+                            w4.z *= rsc;
+                            w4.w *= rsc;
                         }
-                        *reinterpret_cast<float4*>(a.out + row * a.Bp + j) = w;
+                        stg[lane * 8 + ((u * 4 + q) ^ (lane & 7))] = w4;
                     }
                 }
+                __syncwarp();
+                const int j = a.c0 + c0 * 16 + 4 * ch;
+                const bool colok = c0 + (ch >> 2) < ce && j < a.Bp;
+                float b0 = 0.f, b1 = 0.f, b2 = 0.f, b3 = 0.f;
+                if (colok && a.op == EXP_DIRECTION) {
+                    b0 = (float)a.st[j].beta;
+                    b1 = (float)a.st[j + 1].beta;
+                    b2 = (float)a.st[j + 2].beta;
+                    b3 = (float)a.st[j + 3].beta;
+                }
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const int rr = sr + 4 * k;
+                    const int64_t row_g = (int64_t)t * BM + quarter * 32 + rr;
+                    if (!colok || row_g >= a.n) continue;
+                    const float4 acc = stg[rr * 8 + (ch ^ (rr & 7))];
+                    float4 w;
+                    if (a.op == EXP_SET_X) {
+                        w = acc;
+                    } else if (a.op == EXP_SUB_R) {
+                        w = g1[k];
+                        w.x -= acc.x; w.y -= acc.y; w.z -= acc.z; w.w -= acc.w;
+                    } else if (a.op == EXP_ADD_Q) {
+                        w = g1[k];
+                        w.x += acc.x; w.y += acc.y; w.z += acc.z; w.w += acc.w;
+                    } else {
+                        const float4 r4 = g1[k], p4 = g2[k];
+                        w.x = r4.x + acc.x + (b0 == 0.0f ? 0.0f : b0 * p4.x);
+                        w.y = r4.y + acc.y + (b1 == 0.0f ? 0.0f : b1 * p4.y);
+                        w.z = r4.z + acc.z + (b2 == 0.0f ? 0.0f : b2 * p4.z);
+                        w.w = r4.w + acc.w + (b3 == 0.0f ? 0.0f : b3 * p4.w);
+                    }
+                    *reinterpret_cast<float4*>(a.out + row_g * a.Bp + j) = w;
+                }
+                __syncwarp();
             }
             tc::fence_before_sync();
             tc::mbar_arrive(&acc_empty[ab]);
             const int tn = t + gridDim.x;
-            if (tn < ntiles && cb < ce) load_ops((int64_t)tn * BM + rloc, cb);
+            if (tn < ntiles && cb < ce) load_ops(tn, cb);
         }
         if (!ok) {
             *abort_flag = 1;
@@ -692,8 +716,8 @@ int lr_tc_expand(hd_ctx* ctx, const LowRank& lr, int op, float* out, const float
     const int max_smem = 227 * 1024 - 2048;
     const int apipe = su ? CSTAGES * TILE_BYTES + XSTAGES * RAW_X : XSTAGES * TILE_BYTES;
     int Nc = lr.Bp16;
-    while (Nc > 16 && (apipe + 2 * nkb * Nc * 128 > max_smem || Nc > 256)) Nc = (Nc / 2 + 15) / 16 * 16;
-    if (apipe + 2 * nkb * Nc * 128 > max_smem)
+    while (Nc > 16 && (apipe + STAGE_BYTES + 2 * nkb * Nc * 128 > max_smem || Nc > 256)) Nc = (Nc / 2 + 15) / 16 * 16;
+    if (apipe + STAGE_BYTES + 2 * nkb * Nc * 128 > max_smem)
         return hd_fail(ctx, HD_ERR_INVALID_ARG, "rank %d too large for the tensor-core expansion", e->r);
     static bool attr[2] = {false, false};
     if (!attr[su]) {
@@ -721,7 +745,7 @@ int lr_tc_expand(hd_ctx* ctx, const LowRank& lr, int op, float* out, const float
         a.st = st;
         a.gate = gate;
         a.scale = e->scale;
-        const size_t smem = 1024 + apipe + 2 * (size_t)nkb * nc * 128 + 256;
+        const size_t smem = 1024 + apipe + STAGE_BYTES + 2 * (size_t)nkb * nc * 128 + 256;
         const int tiles = (int)((n + BM - 1) / BM);
         const int grid = std::min(tiles, ctx->num_sms);
         if (su)
