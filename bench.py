@@ -288,8 +288,8 @@ def e2e_leg(ctx, wl, eig, mode, tol, alpha, K, B, topk):
 # k_spmm<64> on a 1M-node k=50 graph (d=256 descriptors, nnz 62,097,728), B=64.
 # Scaled to another graph by nnz (the gathered rows dominate); reported only
 # while the kernel source still hashes to the value the counters were taken on.
-SPMM_NCU = {"dram_bytes": 11657710000, "nnz": 62097728, "n": 1000000, "B": 64,
-            "src_sha1": "08002631e21e21b2a047d6aa0ee97372ea9f741d"}
+SPMM_NCU = {"dram_bytes": 11916185088, "nnz": 62097728, "n": 1000000, "B": 64, "slab": 64,
+            "src_sha1": "e4ecb596fff14fe64d25174f3a2c8cf177800a3d"}
 
 
 def spmm_source_sha1():
@@ -301,7 +301,9 @@ def spmm_source_sha1():
 
 
 def spmm_traffic(wl, B):
-    if SPMM_NCU["dram_bytes"] is None or SPMM_NCU["src_sha1"] != spmm_source_sha1() or B != SPMM_NCU["B"]:
+    tun = wl["g"].tuning(B)
+    if SPMM_NCU["dram_bytes"] is None or SPMM_NCU["src_sha1"] != spmm_source_sha1() or B != SPMM_NCU["B"] \
+            or tun is None or tun[0] != SPMM_NCU["slab"] or tun[1] != 1:
         return None
     return int(SPMM_NCU["dram_bytes"] * wl["g"].nnz / SPMM_NCU["nnz"])
 
@@ -645,6 +647,7 @@ def main():
                                + (f", regional: {wl['pool']} regions per image, pooled ranking of "
                                   f"{wl['n'] // wl['pool']} images" if wl["pool"] else ""),
                    "mode": args.mode, "r": args.r, "storage": args.storage, "alpha": alpha, "tol": tol_h,
+                   "spmm_tuning": dict(zip(("slab", "segments"), wl["g"].tuning(B) or (None, None))),
                    "calib_rel_err": err_h, "iters_max": int(hyb["iters"].max()),
                    "l2": "inputs larger than L2 (graph + U + vectors per step > 129 MB)",
                    "parallelism": f"replicas x{world}",

@@ -135,6 +135,11 @@ int hd_observe(hd_ctx* ctx, const void* X, int64_t n, int32_t d, int dtype, cons
                float* y_val);
 
 int hd_graph_info(const hd_graph* g, int64_t* n, int64_t* nnz);
+/* The SpMM launch shape the library measured for this graph at padded batch
+ * width Bp (B rounded up to 4) during an earlier solve: *slab = columns per
+ * row group (4..128), *segments = node-range passes.  HD_ERR_INVALID_ARG if no
+ * solve with that width has run on the graph yet. */
+int hd_graph_tuning(const hd_graph* g, int32_t Bp, int32_t* slab, int32_t* segments);
 /* Copy the normalised graph out (any pointer may be NULL; host or device):
  * row_ptr[n+1], col[nnz], val[nnz] = W, dinv[n] = D^-1/2. Rows sorted by column. */
 int hd_graph_export(hd_ctx* ctx, const hd_graph* g, int32_t* row_ptr, int32_t* col, float* val,
@@ -146,7 +151,10 @@ int hd_graph_destroy(hd_graph* g);
 /* Eigenpairs supplied by the caller: lambda[r] (host, descending), U
  * (n x r row-major fp32, host or device), stored on the device as `storage`
  * (HD_F32, HD_BF16 round-to-nearest-even, or HD_FP8 e4m3 with per-row scale
- * max_k |U_ik| / 448).  r may be 0. */
+ * max_k |U_ik| / 448).  HD_F32 keeps, besides the fp32 values, a bf16
+ * [hi | lo] copy (4 more bytes per entry) that the tensor-core products read;
+ * their results carry about 16 significant bits of U and of the fp32 operand.
+ * r may be 0. */
 int hd_eig_from_host(hd_ctx* ctx, const hd_graph* g, int32_t r, const double* lambda,
                      const float* U, int storage, hd_eig** out);
 

@@ -329,6 +329,16 @@ int hd_graph_from_csr(hd_ctx* ctx, int64_t n, int64_t nnz, const int32_t* row_pt
     return HD_OK;
 }
 
+int hd_graph_tuning(const hd_graph* g, int32_t Bp, int32_t* slab, int32_t* segments) {
+    if (!g) return HD_ERR_INVALID_ARG;
+    auto it = g->slab_cache.find(Bp);
+    if (it == g->slab_cache.end()) return HD_ERR_INVALID_ARG;
+    if (slab) *slab = it->second;
+    auto is = g->seg_cache.find(Bp);
+    if (segments) *segments = is == g->seg_cache.end() ? 1 : is->second;
+    return HD_OK;
+}
+
 int hd_graph_info(const hd_graph* g, int64_t* n, int64_t* nnz) {
     if (!g) return HD_ERR_INVALID_ARG;
     if (n) *n = g->n;
@@ -357,13 +367,23 @@ int hd_graph_destroy(hd_graph* g) {
 // ------------------------------------------------------------------ eigenpairs
 
 __global__ void k_store_u(const float* src, int32_t lds, int64_t n, int32_t r, int32_t ldu, int storage,
-                          void* dst, float* scale) {
+                          void* dst, float* scale, __nv_bfloat16* split, int32_t ldsplit) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float* s = src + i * lds;
     if (storage == HD_F32) {
         float* d = (float*)dst + i * ldu;
         for (int k = 0; k < ldu; ++k) d[k] = k < r ? s[k] : 0.0f;
+        if (split) {
+            const int half = ldsplit / 2;
+            __nv_bfloat16* h = split + i * ldsplit;
+            for (int k = 0; k < half; ++k) {
+                const float v = k < r ? s[k] : 0.0f;
+                const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+                h[k] = hi;
+                h[half + k] = __float2bfloat16_rn(v - __bfloat162float(hi));
+            }
+        }
     } else if (storage == HD_BF16) {
         __nv_bfloat16* d = (__nv_bfloat16*)dst + i * ldu;
         for (int k = 0; k < ldu; ++k) d[k] = __float2bfloat16_rn(k < r ? s[k] : 0.0f);
@@ -393,6 +413,7 @@ __global__ void k_load_u(const void* U, const float* scale, int64_t n, int32_t r
 static void eig_free(hd_eig* e) {
     if (!e) return;
     cudaFree(e->U);
+    cudaFree(e->Usplit);
     cudaFree(e->scale);
     cudaFree(e->lambda_d);
     cudaFree(e->sp_rp);
@@ -421,7 +442,12 @@ int hd_eig_alloc(hd_ctx* ctx, int64_t n, int32_t r, int storage, hd_eig** out) {
     cudaError_t a = cudaMalloc(&e->U, (size_t)n * e->ldu * es);
     cudaError_t b = cudaMalloc(&e->scale, n * sizeof(float));
     cudaError_t c = cudaMalloc(&e->lambda_d, (r > 0 ? r : 1) * sizeof(double));
-    if (a || b || c) {
+    cudaError_t d = cudaSuccess;
+    if (storage == HD_F32 && r > 0) {
+        e->lds = 2 * ((r + 127) / 128 * 128);
+        d = cudaMalloc(&e->Usplit, (size_t)n * e->lds * 2);
+    }
+    if (a || b || c || d) {
         cudaGetLastError();
         eig_free(e);
         return hd_fail(ctx, HD_ERR_OOM, "eigenpairs n=%lld r=%d", (long long)n, r);
@@ -432,7 +458,7 @@ int hd_eig_alloc(hd_ctx* ctx, int64_t n, int32_t r, int storage, hd_eig** out) {
 
 int hd_eig_store_from_device_f32(hd_ctx* ctx, hd_eig* e, const float* U_d, int32_t ldsrc) {
     k_store_u<<<ceil_div(e->n, 256), 256, 0, ctx->stream>>>(U_d, ldsrc, e->n, e->r, e->ldu, e->storage, e->U,
-                                                            e->scale);
+                                                            e->scale, (__nv_bfloat16*)e->Usplit, e->lds);
     HD_CHECK_LAUNCH(ctx);
     return HD_OK;
 }

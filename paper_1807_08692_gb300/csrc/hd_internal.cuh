@@ -84,6 +84,11 @@ struct hd_eig {
     int storage = HD_F32;
     void* U = nullptr;        // n x ldu, storage type
     float* scale = nullptr;   // per-row fp8 scale (HD_FP8 only)
+    // HD_F32 only: bf16 copy of U split as [hi | lo] per row (each half
+    // r rounded up to 128 wide, zero padded), hi = bf16(U), lo = bf16(U - hi),
+    // read by the tensor-core products; lds = row length in elements
+    void* Usplit = nullptr;
+    int32_t lds = 0;
     double* lambda_d = nullptr;
     std::vector<double> lambda_h;
     // sparsified embedding (hd_eig_sparsify): U is not stored densely then

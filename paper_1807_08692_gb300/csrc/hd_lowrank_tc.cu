@@ -7,6 +7,10 @@
 // U is exact in bf16.  The fp32 operand (H or V) is split into bf16 high and
 // low parts (x = hi + lo + O(2^-16 |x|)) and both are multiplied, so the
 // products keep about 16 significant bits before the fp32 accumulation.
+// FP32 storage: U is also kept as a bf16 [hi | lo] copy (lo = bf16(U - hi));
+// the expansion runs twice the k-blocks (the lo half meets the same H blocks)
+// and the reduction twice the M tiles, adding the lo tile into the hi tile in
+// the epilogue, so all four hi/lo products are formed.
 // FP8 storage (e4m3 codes with a per-row fp32 scale): TMA brings the raw code
 // tiles in, four converter warps widen them to bf16 (exact: every e4m3 value
 // is a bf16 value) in the swizzled layout the MMA reads, and the row scale is
@@ -61,7 +65,8 @@ bool lr_use_tensor_cores(const hd_eig* e) {
         const char* s = getenv("HD_LOWRANK_SIMT");
         off = (s && atoi(s)) ? 1 : 0;
     }
-    return e && !e->sparse && (e->storage == HD_BF16 || e->storage == HD_FP8) && !off;
+    return e && !e->sparse && (e->storage == HD_BF16 || e->storage == HD_FP8 || (e->storage == HD_F32 && e->Usplit)) &&
+           !off;
 }
 
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
@@ -99,7 +104,10 @@ struct ExpandArgs {
     int32_t Bp;
     int32_t c0;     // first column of this launch
     int32_t Nc;     // columns of this launch (multiple of 16, <= 256)
-    int32_t nkb;    // k-blocks of 64
+    int32_t nkb;    // k-block iterations per tile (64 eigen-indices each)
+    int32_t nkb_b;  // k-blocks of H; with U stored as [hi | lo] there are 2 nkb_b iterations: iteration kb
+                    // reads U block kb (kb < nkb_b) or kb + a_off (the lo half) and H block kb mod nkb_b
+    int32_t a_off;
     int32_t op;
     uint32_t tmem_cols;
     float* out;
@@ -124,8 +132,8 @@ __global__ void __launch_bounds__(THREADS + (SU ? CONV : 0), 1)
     uint8_t* As = smem;
     uint8_t* Raw = As + NA * TILE_BYTES;          // raw fp8 stages (SU only)
     uint8_t* Bhi = Raw + (SU ? XSTAGES * RAW_X : 0);
-    uint8_t* Blo = Bhi + a.nkb * btile;
-    float* stage = reinterpret_cast<float*>(Blo + a.nkb * btile);  // epilogue transposition, 4 KB per warp
+    uint8_t* Blo = Bhi + a.nkb_b * btile;
+    float* stage = reinterpret_cast<float*>(Blo + a.nkb_b * btile);  // epilogue transposition, 4 KB per warp
     uint64_t* bars = (uint64_t*)(reinterpret_cast<uint8_t*>(stage) + STAGE_BYTES);
     uint64_t* full = bars;
     uint64_t* empty = full + XSTAGES;
@@ -169,8 +177,8 @@ __global__ void __launch_bounds__(THREADS + (SU ? CONV : 0), 1)
         if (lane == 0) {
             uint32_t it = 0;
             bool ok = true;
-            tc::mbar_arrive_expect_tx(bfull, 2u * a.nkb * btile);
-            for (int kb = 0; kb < a.nkb; ++kb) {
+            tc::mbar_arrive_expect_tx(bfull, 2u * a.nkb_b * btile);
+            for (int kb = 0; kb < a.nkb_b; ++kb) {
                 tc::tma_load_2d(Bhi + kb * btile, &tmHhi, bfull, kb * BK, a.c0);
                 tc::tma_load_2d(Blo + kb * btile, &tmHlo, bfull, kb * BK, a.c0);
             }
@@ -186,7 +194,8 @@ __global__ void __launch_bounds__(THREADS + (SU ? CONV : 0), 1)
                         tc::tma_load_2d(Raw + s * RAW_X, &tmU, &full[s], kb * BK, t * BM);
                     } else {
                         tc::mbar_arrive_expect_tx(&full[s], TILE_BYTES);
-                        tc::tma_load_2d(As + s * TILE_BYTES, &tmU, &full[s], kb * BK, t * BM);
+                        tc::tma_load_2d(As + s * TILE_BYTES, &tmU, &full[s], (kb < a.nkb_b ? kb : kb + a.a_off) * BK,
+                                        t * BM);
                     }
                 }
             if (!ok) {
@@ -221,8 +230,9 @@ __global__ void __launch_bounds__(THREADS + (SU ? CONV : 0), 1)
                     }
                     tc::fence_after_sync();
                     const uint32_t aa = tc::smem_u32(As + s * TILE_BYTES);
-                    const uint32_t bh = tc::smem_u32(Bhi + kb * btile);
-                    const uint32_t bl = tc::smem_u32(Blo + kb * btile);
+                    const int kbb = kb < a.nkb_b ? kb : kb - a.nkb_b;
+                    const uint32_t bh = tc::smem_u32(Bhi + kbb * btile);
+                    const uint32_t bl = tc::smem_u32(Blo + kbb * btile);
 #pragma unroll
                     for (int kk = 0; kk < BK / 16; ++kk) {
                         const uint64_t ad = tc::smem_desc(aa + kk * 32, 16, 1024, tc::SWIZZLE_128B);
@@ -405,6 +415,7 @@ struct ReduceArgs {
     int32_t mt;          // M tiles of 128 eigen-indices
     int32_t rpad;
     int64_t tiles_per_cta;
+    int32_t fold;        // U stored as [hi | lo]: M tiles m and m + fold add into output rows of tile m (0: none)
     uint32_t lbo, sbo;   // MN-major descriptor strides (bytes)
     uint32_t tmem_cols;
     const float* V;
@@ -660,13 +671,21 @@ __global__ void __launch_bounds__(THREADS + (SU ? CONV : 0), 1)
         const int nch = a.Nc / 16;
         const int nh = (nch + 1) / 2;
         const int cb = half ? nh : 0, ce = half ? nch : nh;
-        for (int m = 0; m < a.mt; ++m) {
+        const int mt_out = a.fold ? a.fold : a.mt;
+        for (int m = 0; m < mt_out; ++m) {
             const int k = m * 128 + quarter * 32 + lane;
             for (int c = cb; c < ce; ++c) {
                 float v[16];
                 if (have) {
                     tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + m * a.Nc + c * 16, v);
                     tc::tmem_ld_wait();
+                    if (a.fold) {
+                        float v2[16];
+                        tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (m + a.fold) * a.Nc + c * 16, v2);
+                        tc::tmem_ld_wait();
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) v[q] += v2[q];
+                    }
                 } else {
 #pragma unroll
                     for (int q = 0; q < 16; ++q) v[q] = 0.0f;
@@ -707,17 +726,21 @@ static int check_err(hd_ctx* ctx, const char* what) {
 int lr_tc_expand(hd_ctx* ctx, const LowRank& lr, int op, float* out, const float* Rv, const float* Pv, int64_t n,
                  int32_t Bp, const ColState* st, const int* gate) {
     const hd_eig* e = lr.e;
-    const int nkb = lr.rpad / BK;
     const int su = e->storage == HD_FP8 ? 1 : 0;
+    const bool split = e->storage == HD_F32;  // [hi | lo] bf16 copy of the fp32 U
+    const int nkb_b = lr.rpad / BK;
+    const int nkb = split ? 2 * nkb_b : nkb_b;
+    const int a_off = split ? e->lds / 2 / BK - nkb_b : 0;
     CUtensorMap tu;
-    if (hd_make_tmap_2d(&tu, e->U, su ? 1 : 2, n, e->ldu, e->ldu, BM, BK, su ? 0 : 1))
+    if (split ? hd_make_tmap_2d(&tu, e->Usplit, 2, n, e->lds, e->lds, BM, BK, 1)
+              : hd_make_tmap_2d(&tu, e->U, su ? 1 : 2, n, e->ldu, e->ldu, BM, BK, su ? 0 : 1))
         return hd_fail(ctx, HD_ERR_CUDA, "tensor map for U failed");
     // column chunks so that H^T (hi + lo) fits next to the A pipeline
     const int max_smem = 227 * 1024 - 2048;
     const int apipe = su ? CSTAGES * TILE_BYTES + XSTAGES * RAW_X : XSTAGES * TILE_BYTES;
     int Nc = lr.Bp16;
-    while (Nc > 16 && (apipe + STAGE_BYTES + 2 * nkb * Nc * 128 > max_smem || Nc > 256)) Nc = (Nc / 2 + 15) / 16 * 16;
-    if (apipe + STAGE_BYTES + 2 * nkb * Nc * 128 > max_smem)
+    while (Nc > 16 && (apipe + STAGE_BYTES + 2 * nkb_b * Nc * 128 > max_smem || Nc > 256)) Nc = (Nc / 2 + 15) / 16 * 16;
+    if (apipe + STAGE_BYTES + 2 * nkb_b * Nc * 128 > max_smem)
         return hd_fail(ctx, HD_ERR_INVALID_ARG, "rank %d too large for the tensor-core expansion", e->r);
     static bool attr[2] = {false, false};
     if (!attr[su]) {
@@ -737,6 +760,8 @@ int lr_tc_expand(hd_ctx* ctx, const LowRank& lr, int op, float* out, const float
         a.c0 = c0;
         a.Nc = nc;
         a.nkb = nkb;
+        a.nkb_b = nkb_b;
+        a.a_off = a_off;
         a.op = op;
         a.tmem_cols = tmem_cols_for(2 * nc);
         a.out = out;
@@ -745,7 +770,7 @@ int lr_tc_expand(hd_ctx* ctx, const LowRank& lr, int op, float* out, const float
         a.st = st;
         a.gate = gate;
         a.scale = e->scale;
-        const size_t smem = 1024 + apipe + STAGE_BYTES + 2 * (size_t)nkb * nc * 128 + 256;
+        const size_t smem = 1024 + apipe + STAGE_BYTES + 2 * (size_t)nkb_b * nc * 128 + 256;
         const int tiles = (int)((n + BM - 1) / BM);
         const int grid = std::min(tiles, ctx->num_sms);
         if (su)
@@ -759,12 +784,17 @@ int lr_tc_expand(hd_ctx* ctx, const LowRank& lr, int op, float* out, const float
 
 int lr_tc_reduce(hd_ctx* ctx, const LowRank& lr, const float* V, int64_t n, int32_t Bp, const int* gate) {
     const hd_eig* e = lr.e;
-    const int mt = (e->r + 127) / 128;
     const int su = e->storage == HD_FP8 ? 1 : 0;
+    const bool split = e->storage == HD_F32;
+    // with the [hi | lo] copy the M tiles cover both halves (lds / 2 is a multiple of 64)
+    const int fold = split ? e->lds / 256 : 0;
+    const int mt = split ? 2 * fold : (e->r + 127) / 128;
     CUtensorMap tu;
-    if (su ? hd_make_tmap_2d(&tu, e->U, 1, n, e->ldu, e->ldu, BM, 128, 0)
-           : hd_make_tmap_2d(&tu, e->U, 2, n, e->ldu, e->ldu, BM, BK, 1))
-        return hd_fail(ctx, HD_ERR_CUDA, "tensor map for U failed");
+    int tmrc;
+    if (split) tmrc = hd_make_tmap_2d(&tu, e->Usplit, 2, n, e->lds, e->lds, BM, BK, 1);
+    else if (su) tmrc = hd_make_tmap_2d(&tu, e->U, 1, n, e->ldu, e->ldu, BM, 128, 0);
+    else tmrc = hd_make_tmap_2d(&tu, e->U, 2, n, e->ldu, e->ldu, BM, BK, 1);
+    if (tmrc) return hd_fail(ctx, HD_ERR_CUDA, "tensor map for U failed");
     const int Bp64 = (Bp + 63) / 64 * 64;
     int Nc = Bp64;
     const int max_smem = 227 * 1024 - 2048;
@@ -794,6 +824,7 @@ int lr_tc_reduce(hd_ctx* ctx, const LowRank& lr, const float* V, int64_t n, int3
         a.c0 = c0;
         a.Nc = nc;
         a.mt = mt;
+        a.fold = fold;
         a.rpad = lr.rpad;
         a.tiles_per_cta = (tiles + grid - 1) / grid;
         a.lbo = variant == 1 ? 1024 : TILE_BYTES;

@@ -48,6 +48,7 @@ _SIGS = {
     "hd_knn": (C.c_int, [vp, vp, i64, i32, C.c_int, vp, i64, i32, C.c_int, vp, vp]),
     "hd_observe": (C.c_int, [vp, vp, i64, i32, C.c_int, vp, i32, i32, f32, vp, vp, vp]),
     "hd_graph_info": (C.c_int, [vp, C.POINTER(i64), C.POINTER(i64)]),
+    "hd_graph_tuning": (C.c_int, [vp, i32, C.POINTER(i32), C.POINTER(i32)]),
     "hd_graph_export": (C.c_int, [vp, vp, vp, vp, vp, vp]),
     "hd_graph_destroy": (C.c_int, [vp]),
     "hd_eig_from_host": (C.c_int, [vp, vp, i32, vp, vp, C.c_int, C.POINTER(vp)]),
@@ -186,6 +187,13 @@ class Graph:
     @property
     def handle(self):
         return self._h
+
+    def tuning(self, B: int):
+        """(slab, segments) the SpMM measured for batch width B, or None before any solve at that width."""
+        sl, sg = i32(), i32()
+        if lib().hd_graph_tuning(self._h, (B + 3) // 4 * 4, C.byref(sl), C.byref(sg)) != OK:
+            return None
+        return sl.value, sg.value
 
     def export(self):
         """(row_ptr, col, val, dinv) as numpy arrays (host copies)."""

@@ -1,5 +1,6 @@
-"""Spectral products U^T V and U H on the device (tensor cores for bf16 and
-fp8 U, CUDA cores for fp32 U) against numpy on the dequantised U."""
+"""Spectral products U^T V and U H on the device (tensor cores for every
+storage: bf16 directly, fp8 through converter warps, fp32 through its bf16
+[hi | lo] split) against numpy on the dequantised U."""
 import numpy as np
 import pytest
 

@@ -258,3 +258,13 @@ def test_segmented_spmm_matches_single_pass(gpu_ctx, g1, cfg1_data, tmp_path):
             err = rel_l2_cols(res[K][m + "_X"].astype(np.float64), cfg1_data["xstar"])
             assert err.max() <= TOL_REL, (K, m, err.max())
             assert np.all(np.abs(res[K][m + "_it"] - res[1][m + "_it"]) <= 1)
+
+
+def test_graph_tuning_reported(gpu_ctx, cfg1_data):
+    import paper_1807_08692_gb300 as hd
+    g = hd.graph_from_csr(gpu_ctx, *csr_of(cfg1_data["A"]))
+    assert g.tuning(16) is None
+    hd.query_batch(gpu_ctx, g, None, "paper", *y_arrays(cfg1_data["yp"], cfg1_data["yi"], cfg1_data["yv"]), 0.99,
+                   1e-4, 100)
+    slab, segs = g.tuning(16)
+    assert slab in (4, 8, 16) and segs == 1
