@@ -366,6 +366,11 @@ int hd_serve_step(hd_server* s, int32_t iters, int32_t* busy);
  * unknown ticket. */
 int hd_serve_poll(hd_server* s, uint64_t ticket, int32_t* idx_out, float* score_out,
                   hd_req_stats* st);
+/* Tickets retired by hd_serve_step since the last call, in retirement order
+ * (at most max_tickets; the rest stay for the next call): lets a caller with
+ * many requests in flight poll only the finished ones.  *count receives the
+ * number written to tickets[] (host). */
+int hd_serve_completed(hd_server* s, uint64_t* tickets, int32_t max_tickets, int32_t* count);
 int hd_serve_close(hd_server* s);
 
 #ifdef __cplusplus

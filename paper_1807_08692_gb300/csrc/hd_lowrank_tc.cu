@@ -27,7 +27,7 @@
 namespace {
 constexpr int BM = 128;           // rows of U per tile
 constexpr int BK = 64;            // bf16 elements per 128-byte swizzle row
-constexpr int XSTAGES = 4;
+constexpr int XSTAGES = 6;
 constexpr int RSTAGES = 3;
 constexpr int THREADS = 320;      // warp 0: TMA, warp 1: MMA, warps 2-9: epilogue / conversion
 constexpr int EPI = 256;          // epilogue threads: two warps per TMEM lane quarter, splitting the columns
@@ -591,7 +591,10 @@ __global__ void __launch_bounds__(THREADS + (SU ? CONV : 0), 1)
         const int quarter = warp & 3;
         const int half = (warp - 2) >> 2;
         bool ok = true;
-        const int cq_n = a.Nc / 4;
+        // only the columns below Bp are converted: the MMA output columns beyond
+        // them are never stored, so their operand bytes in shared memory do not matter
+        const int live4 = (a.Bp - a.c0 + 3) / 4;
+        const int cq_n = live4 < a.Nc / 4 ? (live4 > 0 ? live4 : 1) : a.Nc / 4;
         const int total = BM * cq_n;
         // V of the next tile is loaded into registers while the current one is
         // converted (one batch when a tile fits EPI x 8 float4, i.e. Nc <= 64)
@@ -738,7 +741,9 @@ int lr_tc_expand(hd_ctx* ctx, const LowRank& lr, int op, float* out, const float
     // column chunks so that H^T (hi + lo) fits next to the A pipeline
     const int max_smem = 227 * 1024 - 2048;
     const int apipe = su ? CSTAGES * TILE_BYTES + XSTAGES * RAW_X : XSTAGES * TILE_BYTES;
-    int Nc = lr.Bp16;
+    // columns that can be active (the server's occupied slots); the rest keep their values
+    const int cols = lr.live > 0 ? std::min(lr.Bp16, (lr.live + 15) / 16 * 16) : lr.Bp16;
+    int Nc = cols;
     while (Nc > 16 && (apipe + STAGE_BYTES + 2 * nkb_b * Nc * 128 > max_smem || Nc > 256)) Nc = (Nc / 2 + 15) / 16 * 16;
     if (apipe + STAGE_BYTES + 2 * nkb_b * Nc * 128 > max_smem)
         return hd_fail(ctx, HD_ERR_INVALID_ARG, "rank %d too large for the tensor-core expansion", e->r);
@@ -748,8 +753,8 @@ int lr_tc_expand(hd_ctx* ctx, const LowRank& lr, int op, float* out, const float
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
         attr[su] = true;
     }
-    for (int c0 = 0; c0 < lr.Bp16; c0 += Nc) {
-        const int nc = std::min(Nc, lr.Bp16 - c0);
+    for (int c0 = 0; c0 < cols; c0 += Nc) {
+        const int nc = std::min(Nc, cols - c0);
         CUtensorMap th, tl;
         if (hd_make_tmap_2d(&th, lr.Hhi, 2, lr.Bp16, lr.rpad, lr.rpad, nc, BK, 1) ||
             hd_make_tmap_2d(&tl, lr.Hlo, 2, lr.Bp16, lr.rpad, lr.rpad, nc, BK, 1))
@@ -795,7 +800,7 @@ int lr_tc_reduce(hd_ctx* ctx, const LowRank& lr, const float* V, int64_t n, int3
     else if (su) tmrc = hd_make_tmap_2d(&tu, e->U, 1, n, e->ldu, e->ldu, BM, 128, 0);
     else tmrc = hd_make_tmap_2d(&tu, e->U, 2, n, e->ldu, e->ldu, BM, BK, 1);
     if (tmrc) return hd_fail(ctx, HD_ERR_CUDA, "tensor map for U failed");
-    const int Bp64 = (Bp + 63) / 64 * 64;
+    const int Bp64 = lr.live > 0 ? std::min((Bp + 63) / 64 * 64, (lr.live + 63) / 64 * 64) : (Bp + 63) / 64 * 64;
     int Nc = Bp64;
     const int max_smem = 227 * 1024 - 2048;
     const size_t apipe = su ? (size_t)CSTAGES * 2 * TILE_BYTES + (size_t)RSTAGES * RAW_R : (size_t)RSTAGES * 2 * TILE_BYTES;
@@ -808,11 +813,6 @@ int lr_tc_reduce(hd_ctx* ctx, const LowRank& lr, const float* V, int64_t n, int3
         HD_CUDA(ctx, cudaFuncSetAttribute(su ? k_lr_reduce_tc<1> : k_lr_reduce_tc<0>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
         attr[su] = true;
-    }
-    static int variant = -1;
-    if (variant < 0) {
-        const char* s = getenv("HD_TC_MN_VARIANT");
-        variant = s ? atoi(s) : 0;
     }
     const int64_t tiles = (n + BM - 1) / BM;
     const int grid = lr.nchunk;
@@ -827,8 +827,10 @@ int lr_tc_reduce(hd_ctx* ctx, const LowRank& lr, const float* V, int64_t n, int3
         a.fold = fold;
         a.rpad = lr.rpad;
         a.tiles_per_cta = (tiles + grid - 1) / grid;
-        a.lbo = variant == 1 ? 1024 : TILE_BYTES;
-        a.sbo = variant == 1 ? TILE_BYTES : 1024;
+        // MN-major operands: the leading byte offset steps between the 64-element
+        // blocks of M (or N), the stride byte offset between groups of 8 K rows
+        a.lbo = TILE_BYTES;
+        a.sbo = 1024;
         a.tmem_cols = tmem_cols_for(mt * nc);
         a.V = V;
         a.part = lr.part;

@@ -98,6 +98,7 @@ struct hd_server {
     std::deque<Req*> queue;
     std::vector<Req*> slot_req;
     std::unordered_map<uint64_t, Req*> reqs;
+    std::deque<uint64_t> finished;  // tickets retired and not yet reported by hd_serve_completed
     uint64_t next_ticket = 1;
     bool polled = true;
 };
@@ -319,6 +320,12 @@ int hd_serve_step(hd_server* s, int32_t iters, int32_t* busy) {
     }
     bool running = s->nrec > 0;
     for (int j = 0; j < s->slots && !running; ++j) running = s->slot_req[j] != nullptr;
+    // the tensor-core products skip the columns above the highest occupied slot
+    // (admission fills the lowest free slots); per-column arithmetic is unchanged
+    int32_t live = 0;
+    for (int j = 0; j < s->slots; ++j)
+        if (s->slot_req[j]) live = j + 1;
+    E.lr.live = live;
     // ---- iterations of every column
     for (int t = 0; t < iters && running; ++t) {
         int rc = engine_iteration(E, admit_cb, s);
@@ -362,6 +369,7 @@ int hd_serve_step(hd_server* s, int32_t iters, int32_t* busy) {
                 r->out_score.assign(s->h_sc + (size_t)j * s->Kmax, s->h_sc + (size_t)j * s->Kmax + r->K);
                 r->done_s = t_done;
                 r->done = true;
+                s->finished.push_back(r->ticket);
                 s->slot_req[j] = nullptr;
             }
         }
@@ -393,6 +401,17 @@ int hd_serve_poll(hd_server* s, uint64_t ticket, int32_t* idx_out, float* score_
     }
     s->reqs.erase(it);
     delete r;
+    return HD_OK;
+}
+
+int hd_serve_completed(hd_server* s, uint64_t* tickets, int32_t max_tickets, int32_t* count) {
+    if (!s || !count || max_tickets < 0 || (max_tickets > 0 && !tickets)) return HD_ERR_INVALID_ARG;
+    int32_t c = 0;
+    while (c < max_tickets && !s->finished.empty()) {
+        tickets[c++] = s->finished.front();
+        s->finished.pop_front();
+    }
+    *count = c;
     return HD_OK;
 }
 

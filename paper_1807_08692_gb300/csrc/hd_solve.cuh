@@ -38,6 +38,7 @@ struct LowRank {
     __nv_bfloat16* Hhi; // [Bp16][rpad] bf16 (transposed, K-major) high part of H
     __nv_bfloat16* Hlo; // low part
     int32_t Bp16;
+    int32_t live = 0;   // > 0: only columns below this can be active (tensor-core paths skip the rest)
 };
 
 // `gate` (device int, may be null): the kernels return at once when it is 0

@@ -71,6 +71,7 @@ _SIGS = {
     "hd_serve_submit": (C.c_int, [vp, i32, vp, vp, f32, i32, C.POINTER(u64)]),
     "hd_serve_step": (C.c_int, [vp, i32, C.POINTER(i32)]),
     "hd_serve_poll": (C.c_int, [vp, u64, vp, vp, vp]),
+    "hd_serve_completed": (C.c_int, [vp, vp, i32, C.POINTER(i32)]),
     "hd_serve_close": (C.c_int, [vp]),
     "hd_eig_expand": (C.c_int, [vp, vp, vp, i32, vp]),
 }
@@ -530,6 +531,13 @@ class Server:
         self.ctx.check(rc, "hd_serve_poll")
         stats = {f: getattr(st, f) for f, _ in ReqStats._fields_}
         return ids[:K], sc[:K], stats
+
+    def completed(self, max_tickets: int = 4096):
+        """Tickets retired since the last call (poll them for their results)."""
+        buf = np.empty(max_tickets, np.uint64)
+        cnt = i32()
+        self.ctx.check(lib().hd_serve_completed(self._h, _ptr(buf), max_tickets, C.byref(cnt)), "hd_serve_completed")
+        return [int(t) for t in buf[:cnt.value]]
 
     def close(self):
         if self._h:

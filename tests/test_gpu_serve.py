@@ -116,3 +116,23 @@ def test_admission_by_memory_and_errors(gpu_ctx, served, cfg1_data):
     srv.close()
     with pytest.raises(hd.HDError):
         hd.Server(gpu_ctx, g, None, "paper", 0.99, max_slots=4, mem_budget=100, Kmax=10)
+
+
+def test_completed_reports_each_ticket_once(gpu_ctx, served):
+    import paper_1807_08692_gb300 as hd
+    g, eig, reqs = served
+    srv = hd.Server(gpu_ctx, g, eig, "pcg", 0.99, max_slots=4, max_iter=500, Kmax=50)
+    tickets = [srv.submit(i, v, [1e-2, 1e-4, 1e-6][k % 3], 20) for k, (i, v) in enumerate(reqs[:9])]
+    seen = []
+    for _ in range(500):
+        busy = srv.step(1)
+        seen += srv.completed(max_tickets=3)
+        if not busy:
+            break
+    seen += srv.completed()
+    assert sorted(seen) == sorted(tickets) and len(set(seen)) == len(seen)
+    assert srv.completed() == []
+    for t in seen:
+        ids, sc, st = srv.poll(t, 20)
+        assert st["status"] == 0 and len(ids) == 20
+    srv.close()
