@@ -145,6 +145,50 @@ __global__ void __launch_bounds__(256, 8) k_spmm(const int32_t* rp, const int32_
     }
 }
 
+// B <= 4 (one 4-column slab): one warp per row with the lanes over the row's
+// entries, so the index / weight reads are coalesced and 32 gathers of a row are
+// in flight at once; the lane sums meet in a fixed shuffle tree.
+__global__ void __launch_bounds__(256) k_spmm_w4(const int32_t* rp, const int32_t* ci, const float* wv,
+                                                 const float* P, float* Q, int64_t n, int32_t ld, float c1, float c2,
+                                                 const ColState* st) {
+    if (!slab_has_work<4>(st, false)) return;
+    const int lane = threadIdx.x & 31;
+    const int col = blockIdx.y * 4;
+    const int64_t nw = (int64_t)gridDim.x * 8;
+    for (int64_t row = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5); row < n; row += nw) {
+        const int32_t b = rp[row], e = rp[row + 1];
+        float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+        int32_t t = b + lane;
+        for (; t + 32 < e; t += 64) {
+            const int32_t j0 = __ldg(ci + t), j1 = __ldg(ci + t + 32);
+            const float w0 = __ldg(wv + t), w1 = __ldg(wv + t + 32);
+            const float4 v0 = ld4(P + (int64_t)j0 * ld + col), v1 = ld4(P + (int64_t)j1 * ld + col);
+            FMA4(s, w0, v0);
+            FMA4(s, w1, v1);
+        }
+        if (t < e) {
+            const float4 v0 = ld4(P + (int64_t)__ldg(ci + t) * ld + col);
+            FMA4(s, __ldg(wv + t), v0);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
+            s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+            s.z += __shfl_xor_sync(0xffffffffu, s.z, o);
+            s.w += __shfl_xor_sync(0xffffffffu, s.w, o);
+        }
+        if (lane == 0) {
+            const float4 own = ld4(P + row * ld + col);
+            float4 q;
+            q.x = c1 * own.x - c2 * s.x;
+            q.y = c1 * own.y - c2 * s.y;
+            q.z = c1 * own.z - c2 * s.z;
+            q.w = c1 * own.w - c2 * s.w;
+            st4(Q + row * ld + col, q);
+        }
+    }
+}
+
 // Compensated partials of P^T Q per block and column (the layout k_fin_sigma reads).
 template <int S>
 __global__ void __launch_bounds__(256) k_dot(const float* __restrict__ P, const float* __restrict__ Q, int64_t n,
@@ -820,7 +864,10 @@ static int launch_spmm(Engine& E, float c1, float c2, float2* part, const ColSta
     dim3 grid(E.vl.nblk, E.vl.slabs);
     {
         HD_PROF(ctx, "spmm");
-        if (E.segK <= 1) {
+        if (E.segK <= 1 && E.vl.S == 4) {
+            k_spmm_w4<<<grid, 256, 0, ctx->stream>>>(g->row_ptr, g->col, g->val, E.P, E.Q, E.n, E.Bp, c1, c2, st);
+            HD_CHECK_LAUNCH(ctx);
+        } else if (E.segK <= 1) {
             HD_DISPATCH_S(E.vl.S, (k_spmm<SS><<<grid, 256, 0, ctx->stream>>>(g->row_ptr, g->col, g->val, E.P, E.Q,
                                                                               E.n, E.Bp, c1, c2, st)));
             HD_CHECK_LAUNCH(ctx);

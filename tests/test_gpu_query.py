@@ -268,3 +268,17 @@ def test_graph_tuning_reported(gpu_ctx, cfg1_data):
                    1e-4, 100)
     slab, segs = g.tuning(16)
     assert slab in (4, 8, 16) and segs == 1
+
+
+@pytest.mark.parametrize("B", [1, 3, 4])
+def test_small_batches(gpu_ctx, g1, cfg1_data, B):
+    # B <= 4 runs the warp-per-row SpMM
+    import paper_1807_08692_gb300 as hd
+    yp, yi, yv = y_arrays(cfg1_data["yp"], cfg1_data["yi"], cfg1_data["yv"])
+    sub = (yp[:B + 1].copy(), yi[:yp[B]].copy(), yv[:yp[B]].copy())
+    lam, U = cfg1_data["lam"][:30], cfg1_data["U"][:, :30]
+    eig = hd.eig_from_host(gpu_ctx, g1, lam, U, "bf16")
+    for e, m in ((None, "paper"), (eig, "pcg")):
+        X, it, rr, st = hd.query_batch(gpu_ctx, g1, e, m, *sub, 0.99, 1e-6, 500)
+        assert np.all(st == 0)
+        assert rel_l2_cols(X.cpu().numpy().astype(np.float64), cfg1_data["xstar"][:, :B]).max() <= TOL_REL
