@@ -219,15 +219,23 @@ __global__ void __launch_bounds__(1024) k_topk_sample(const float* X, int64_t n,
     }
 }
 
-__global__ void k_topk_filter(const float* X, int64_t n, int32_t B, int32_t ld, const int32_t* Kd,
-                              const uint32_t* tau, int* cnt, uint64_t* cand) {
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * B; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = e / B;
-        const int j = (int)(e % B);
-        const uint32_t key = float_key(X[i * ld + j]);
-        if (key >= __ldg(tau + j) && __ldg(Kd + j) > 0) {
-            const int p = atomicAdd(&cnt[j], 1);
-            if (p < TK_CAP) cand[(int64_t)j * TK_CAP + p] = ((uint64_t)key << 32) | (uint64_t)(~(uint32_t)i);
+// Each thread keeps one column (B <= 256: 256 / B rows per block step) so the
+// column's threshold and K stay in registers and no index is divided per element.
+__global__ void __launch_bounds__(256) k_topk_filter(const float* X, int64_t n, int32_t B, int32_t ld,
+                                                     const int32_t* Kd, const uint32_t* tau, int* cnt, uint64_t* cand) {
+    const bool narrow = B <= 256;
+    const int R = narrow ? 256 / B : 1;
+    const int rt = narrow ? (int)threadIdx.x / B : 0;
+    if (rt >= R) return;
+    for (int j = narrow ? (int)threadIdx.x % B : (int)threadIdx.x; j < B; j += narrow ? B : 256) {
+        const uint32_t tj = __ldg(tau + j);
+        if (__ldg(Kd + j) <= 0) continue;
+        for (int64_t i = (int64_t)blockIdx.x * R + rt; i < n; i += (int64_t)gridDim.x * R) {
+            const uint32_t key = float_key(X[i * ld + j]);
+            if (key >= tj) {
+                const int p = atomicAdd(&cnt[j], 1);
+                if (p < TK_CAP) cand[(int64_t)j * TK_CAP + p] = ((uint64_t)key << 32) | (uint64_t)(~(uint32_t)i);
+            }
         }
     }
 }
@@ -300,7 +308,7 @@ int hd_rank_impl(hd_ctx* ctx, const float* Xd, int64_t n, int32_t B, int32_t ldx
     }
     k_topk_sample<<<B, 1024, 0, ctx->stream>>>(src, m, ld, Kd, tau, cnt);
     HD_CHECK_LAUNCH(ctx);
-    const int gc = std::max(1, std::min<int>(ceil_div(m * B, 256), ctx->num_sms * 8));
+    const int gc = std::max(1, std::min<int>(ceil_div(m * B, 256 * 8), ctx->num_sms * 8));
     k_topk_filter<<<gc, 256, 0, ctx->stream>>>(src, m, B, ld, Kd, tau, cnt, cand);
     HD_CHECK_LAUNCH(ctx);
     k_topk_sort<<<B, 1024, TK_CAP * 8, ctx->stream>>>(cand, cnt, Kd, m, Kmax, idx_d, score_d, fail);
@@ -356,7 +364,7 @@ static int radix_rank(hd_ctx* ctx, const float* src, int64_t m, int32_t B, int32
             HD_CHECK_LAUNCH(ctx);
         }
     }
-    const int gc = std::max(1, std::min<int>(ceil_div(m * B, 256), ctx->num_sms * 8));
+    const int gc = std::max(1, std::min<int>(ceil_div(m * B, 256 * 8), ctx->num_sms * 8));
     k_collect<<<gc, 256, 0, ctx->stream>>>(src, m, B, ld, st, Kmax, cand);
     HD_CHECK_LAUNCH(ctx);
     int P = 1;

@@ -100,6 +100,7 @@ struct hd_server {
     std::unordered_map<uint64_t, Req*> reqs;
     std::deque<uint64_t> finished;  // tickets retired and not yet reported by hd_serve_completed
     uint64_t next_ticket = 1;
+    int S_full = 4;  // SpMM slab width measured for the whole batch
     bool polled = true;
 };
 
@@ -157,6 +158,7 @@ int hd_serve_open(hd_ctx* ctx, const hd_graph* g, const hd_eig* eig, int mode, f
     E.ctx = ctx;
     E.g = g;
     E.n = n;
+    engine_set_reduction(E);
     E.B = slots;
     E.Bp = (slots + 3) / 4 * 4;
     E.vl = vec_launch(ctx, n, E.Bp);  // re-tuned below once the buffers exist
@@ -174,7 +176,7 @@ int hd_serve_open(hd_ctx* ctx, const hd_graph* g, const hd_eig* eig, int mode, f
     if (lr_on) nchunk = lr_nchunk(ctx, eig, Bp);
     s->cap_nnz = Bp * 512;
     const size_t vec = (size_t)n * Bp * 4;
-    size_t bytes = 4 * ws_size(vec) + ws_size((size_t)ctx->num_sms * 8 * Bp * 8) + ws_size(Bp * sizeof(ColState)) +
+    size_t bytes = 4 * ws_size(vec) + ws_size((size_t)E.nch * Bp * 8) + ws_size(Bp * sizeof(ColState)) +
                    ws_size(64) + ws_size(Bp * sizeof(AdmitRec)) + 2 * ws_size((size_t)s->cap_nnz * 4) +
                    2 * ws_size((size_t)Bp * Kmax * 4);
     if (lr_on)
@@ -191,11 +193,13 @@ int hd_serve_open(hd_ctx* ctx, const hd_graph* g, const hd_eig* eig, int mode, f
     E.P = cv.take<float>((size_t)n * Bp);
     E.Q = cv.take<float>((size_t)n * Bp);
     E.X = cv.take<float>((size_t)n * Bp);
-    E.part = cv.take<float2>((size_t)ctx->num_sms * 8 * Bp);
+    E.part = cv.take<float2>((size_t)E.nch * Bp);
     E.st = cv.take<ColState>(Bp);
     E.num_active = cv.take<int>(16);
     E.err = E.num_active + 1;
     E.vl = vec_launch(ctx, n, Bp, tune_slab(ctx, g, Bp, E.P, E.Q));
+    s->S_full = E.vl.S;
+    E.warp_rows = false;
     {
         const int trc = tune_segments(ctx, E);
         if (trc) {
@@ -326,6 +330,17 @@ int hd_serve_step(hd_server* s, int32_t iters, int32_t* busy) {
     for (int j = 0; j < s->slots; ++j)
         if (s->slot_req[j]) live = j + 1;
     E.lr.live = live;
+    // the narrowest slab that holds every occupied column (at most the width
+    // measured for the full batch): a lightly loaded server gathers less per
+    // SpMM row.  Results do not depend on it: the reductions are chunked by
+    // rows, and every slab width sums a row's entries in the same order.
+    int S = s->S_full;
+    for (int c : {4, 8, 16, 32, 64, 128})
+        if (c >= live && c <= s->S_full && Bp % c == 0) {
+            S = c;
+            break;
+        }
+    if (S != E.vl.S) E.vl = vec_launch(ctx, E.n, Bp, S);
     // ---- iterations of every column
     for (int t = 0; t < iters && running; ++t) {
         int rc = engine_iteration(E, admit_cb, s);

@@ -24,33 +24,6 @@ __device__ __forceinline__ float4 ld4(const float* p) { return __ldg(reinterpret
 __device__ __forceinline__ float4 ld4v(const float* p) { return *reinterpret_cast<const float4*>(p); }
 __device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
 
-// Reduce per-thread compensated sums of 4 columns to S per-block partials.
-// Lanes sharing columns are l, l + L, l + 2L, ... with L = S / 4.
-template <int S>
-__device__ __forceinline__ void block_reduce_cols(KSum (&a)[4], float2* out) {
-    constexpr int L = S / 4;
-    __shared__ float2 sm[8][S];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int off = L; off < 32; off <<= 1)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            KSum o;
-            o.s = __shfl_xor_sync(0xffffffffu, a[c].s, off);
-            o.c = __shfl_xor_sync(0xffffffffu, a[c].c, off);
-            ksum_merge(a[c], o);
-        }
-    if (lane < L)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) sm[warp][4 * lane + c] = make_float2(a[c].s, a[c].c);
-    __syncthreads();
-    if (threadIdx.x < S) {
-        KSum t = {0.0f, 0.0f};
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) ksum_merge(t, KSum{sm[w][threadIdx.x].x, sm[w][threadIdx.x].y});
-        out[threadIdx.x] = make_float2(t.s, t.c);
-    }
-}
-
 // ------------------------------------------------------------------ kernels
 // R[:, j] += y_j (one thread per column: duplicates summed in input order).
 __global__ void k_scatter_y(const int32_t* y_ptr, const int32_t* y_idx, const float* y_val, int32_t B, int64_t n,
@@ -189,40 +162,19 @@ __global__ void __launch_bounds__(256) k_spmm_w4(const int32_t* rp, const int32_
     }
 }
 
-// Compensated partials of P^T Q per block and column (the layout k_fin_sigma reads).
-template <int S>
-__global__ void __launch_bounds__(256) k_dot(const float* __restrict__ P, const float* __restrict__ Q, int64_t n,
-                                             int32_t ld, float2* __restrict__ part, const ColState* __restrict__ st) {
-    constexpr int L = S / 4;
-    constexpr int RPB = 256 / L;
-    if (!slab_has_work<S>(st, false)) return;
-    const int g = (threadIdx.x & 31) % L;
-    const int col = blockIdx.y * S + 4 * g;
-    KSum acc[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
-    for (int64_t row = (int64_t)blockIdx.x * RPB + threadIdx.x / L; row < n; row += (int64_t)gridDim.x * RPB) {
-        const float4 a = ld4(P + row * ld + col), b = ld4(Q + row * ld + col);
-        ksum_add(acc[0], a.x * b.x);
-        ksum_add(acc[1], a.y * b.y);
-        ksum_add(acc[2], a.z * b.z);
-        ksum_add(acc[3], a.w * b.w);
-    }
-    block_reduce_cols<S>(acc, part + (int64_t)blockIdx.x * ld + blockIdx.y * S);
-}
-
 // Per-column operators (truncated systems): column j's row t holds the entries
 // off[j * n + t] .. off[j * n + t + 1] of (ci, wv); columns j >= B are empty.
-// Q = c1 P - c2 W_j P column by column; optional partials of P^T Q.
+// Q = c1 P - c2 W_j P column by column.
 template <int S>
 __global__ void __launch_bounds__(256) k_spmm_cols(const int64_t* __restrict__ off, const int32_t* __restrict__ ci,
                                                    const float* __restrict__ wv, int32_t B, const float* __restrict__ P,
                                                    float* __restrict__ Q, int64_t n, int32_t ld, float c1, float c2,
-                                                   float2* __restrict__ part, const ColState* __restrict__ st) {
+                                                   const ColState* __restrict__ st) {
     constexpr int L = S / 4;
     constexpr int RPB = 256 / L;
     if (!slab_has_work<S>(st, false)) return;
     const int g = (threadIdx.x & 31) % L;
     const int col = blockIdx.y * S + 4 * g;
-    KSum acc[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
     for (int64_t row = (int64_t)blockIdx.x * RPB + threadIdx.x / L; row < n; row += (int64_t)gridDim.x * RPB) {
         float s[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
@@ -247,14 +199,7 @@ __global__ void __launch_bounds__(256) k_spmm_cols(const int64_t* __restrict__ o
         q.z = c1 * own.z - c2 * s[2];
         q.w = c1 * own.w - c2 * s[3];
         st4(Q + row * ld + col, q);
-        if (part) {
-            ksum_add(acc[0], own.x * q.x);
-            ksum_add(acc[1], own.y * q.y);
-            ksum_add(acc[2], own.z * q.z);
-            ksum_add(acc[3], own.w * q.w);
-        }
     }
-    if (part) block_reduce_cols<S>(acc, part + (int64_t)blockIdx.x * ld + blockIdx.y * S);
 }
 
 // Row i's entries in segment s (columns [s w, (s + 1) w)) are
@@ -338,61 +283,138 @@ __global__ void __launch_bounds__(256) k_spmm_seg(const int32_t* __restrict__ lo
     }
 }
 
-// Partials of sum_i V_ij^2.
-template <int S>
-__global__ void __launch_bounds__(256) k_colsq(const float* __restrict__ V, int64_t n, int32_t ld, float2* part) {
-    constexpr int L = S / 4;
-    constexpr int RPB = 256 / L;
-    const int g = (threadIdx.x & 31) % L;
-    const int col = blockIdx.y * S + 4 * g;
-    KSum acc[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
-    for (int64_t row = (int64_t)blockIdx.x * RPB + threadIdx.x / L; row < n; row += (int64_t)gridDim.x * RPB) {
-        const float4 v = ld4v(V + row * ld + col);
-        ksum_add(acc[0], v.x * v.x);
-        ksum_add(acc[1], v.y * v.y);
-        ksum_add(acc[2], v.z * v.z);
-        ksum_add(acc[3], v.w * v.w);
+// ---- column reductions ----
+// Every per-column sum of the solve (||r||^2, p^T q, ||y||^2) is formed the
+// same way whatever the launch shape: rows are cut into chunks of `rch`
+// consecutive rows (rch depends on n only); within a chunk, thread g of 8 sums
+// rows g, g + 8, ... in order for one column quad (compensated fp32), the 8
+// sums meet in a fixed order in shared memory, and the chunk partials
+// [nch][ld] are added in chunk order by the fp64 column kernels.  A column's CG
+// scalars are therefore the same bit for bit whatever the slab width, the
+// batch width or the other columns of the batch.
+constexpr int RG = 8;      // threads per chunk and quad
+constexpr int RQ = 128;    // quads per block (at most)
+
+int reduction_chunk_rows(int64_t n) {
+    const int64_t r = (n + 4095) / 4096;
+    return (int)std::max<int64_t>(512, (r + RG - 1) / RG * RG);
+}
+
+// thread -> (chunk = blockIdx.x, quad, g); false when the quad has no column to work on
+__device__ __forceinline__ bool red_thread(int64_t n, int32_t ld, int rch, const ColState* st, bool include_fresh,
+                                           int64_t& r0, int64_t& r1, int& col, int& g) {
+    const int nq = ld >> 2;
+    const int qpb = nq < RQ ? nq : RQ;
+    const int quad = blockIdx.y * RQ + (int)threadIdx.x % qpb;
+    g = (int)threadIdx.x / qpb;
+    col = 4 * quad;
+    r0 = (int64_t)blockIdx.x * rch + g;
+    r1 = min(n, (int64_t)(blockIdx.x + 1) * rch);
+    if (quad >= nq) return false;
+    if (!st) return true;
+    bool w = false;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) w |= st[col + c].active || (include_fresh && st[col + c].fresh);
+    return w;
+}
+
+// combine the RG partial sums of each quad in g order and store the chunk partial
+__device__ __forceinline__ void red_finish(float2* part, int32_t ld, bool work, int col, int g, const KSum (&a)[4]) {
+    extern __shared__ float2 red_sm[];  // [RG][qpb * 4]
+    const int nq = ld >> 2;
+    const int qpb = nq < RQ ? nq : RQ;
+    const int ql = (int)threadIdx.x % qpb;
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+        red_sm[g * qpb * 4 + ql * 4 + c] = work ? make_float2(a[c].s, a[c].c) : make_float2(0.f, 0.f);
+    __syncthreads();
+    if (g != 0 || !work) return;
+    KSum t[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        t[c] = KSum{red_sm[ql * 4 + c].x, red_sm[ql * 4 + c].y};
+        for (int h = 1; h < RG; ++h)
+            ksum_merge(t[c], KSum{red_sm[h * qpb * 4 + ql * 4 + c].x, red_sm[h * qpb * 4 + ql * 4 + c].y});
     }
-    block_reduce_cols<S>(acc, part + (int64_t)blockIdx.x * ld + blockIdx.y * S);
+    float4* d = reinterpret_cast<float4*>(part + (int64_t)blockIdx.x * ld + col);
+    d[0] = make_float4(t[0].s, t[0].c, t[1].s, t[1].c);
+    d[1] = make_float4(t[2].s, t[2].c, t[3].s, t[3].c);
+}
+
+// Partials of sum_i V_ij^2 (every column).
+__global__ void __launch_bounds__(1024) k_colsq(const float* __restrict__ V, int64_t n, int32_t ld, int rch,
+                                                float2* __restrict__ part) {
+    int64_t r0, r1;
+    int col, g;
+    const bool work = red_thread(n, ld, rch, nullptr, false, r0, r1, col, g);
+    KSum acc[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+    if (work)
+        for (int64_t row = r0; row < r1; row += RG) {
+            const float4 v = ld4v(V + row * ld + col);
+            ksum_add(acc[0], v.x * v.x);
+            ksum_add(acc[1], v.y * v.y);
+            ksum_add(acc[2], v.z * v.z);
+            ksum_add(acc[3], v.w * v.w);
+        }
+    red_finish(part, ld, work, col, g, acc);
+}
+
+// Partials of P^T Q (columns being iterated).
+__global__ void __launch_bounds__(1024) k_dot(const float* __restrict__ P, const float* __restrict__ Q, int64_t n,
+                                              int32_t ld, int rch, float2* __restrict__ part,
+                                              const ColState* __restrict__ st) {
+    int64_t r0, r1;
+    int col, g;
+    const bool work = red_thread(n, ld, rch, st, false, r0, r1, col, g);
+    KSum acc[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+    if (work)
+        for (int64_t row = r0; row < r1; row += RG) {
+            const float4 a = ld4(P + row * ld + col), b = ld4(Q + row * ld + col);
+            ksum_add(acc[0], a.x * b.x);
+            ksum_add(acc[1], a.y * b.y);
+            ksum_add(acc[2], a.z * b.z);
+            ksum_add(acc[3], a.w * b.w);
+        }
+    red_finish(part, ld, work, col, g, acc);
 }
 
 // X += xs a P; R -= a Q; partials of ||R||^2.
-template <int S>
-__global__ void __launch_bounds__(256) k_update(float* __restrict__ X, float* __restrict__ R,
-                                                const float* __restrict__ P, const float* __restrict__ Q, int64_t n,
-                                                int32_t ld, const ColState* __restrict__ st, float xs,
-                                                float2* __restrict__ part) {
-    constexpr int L = S / 4;
-    constexpr int RPB = 256 / L;
-    if (!slab_has_work<S>(st, true)) return;
-    const int g = (threadIdx.x & 31) % L;
-    const int col = blockIdx.y * S + 4 * g;
-    const float a0 = (float)st[col].a, a1 = (float)st[col + 1].a, a2 = (float)st[col + 2].a, a3 = (float)st[col + 3].a;
-    const float x0 = xs * a0, x1 = xs * a1, x2 = xs * a2, x3 = xs * a3;
-    // a column being (re)admitted starts from x = 0, r = 0 (its y is scattered next)
-    const bool f0 = st[col].fresh, f1 = st[col + 1].fresh, f2 = st[col + 2].fresh, f3 = st[col + 3].fresh;
-    const bool any_fresh = f0 | f1 | f2 | f3;
+__global__ void __launch_bounds__(1024) k_update(float* __restrict__ X, float* __restrict__ R,
+                                                 const float* __restrict__ P, const float* __restrict__ Q, int64_t n,
+                                                 int32_t ld, int rch, const ColState* __restrict__ st, float xs,
+                                                 float2* __restrict__ part) {
+    int64_t r0, r1;
+    int col, g;
+    const bool work = red_thread(n, ld, rch, st, true, r0, r1, col, g);
     KSum acc[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
-    for (int64_t row = (int64_t)blockIdx.x * RPB + threadIdx.x / L; row < n; row += (int64_t)gridDim.x * RPB) {
-        const int64_t o = row * ld + col;
-        const float4 p = ld4v(P + o), q = ld4v(Q + o);
-        float4 x = ld4v(X + o), r = ld4v(R + o);
-        x.x = fmaf(x0, p.x, x.x); x.y = fmaf(x1, p.y, x.y); x.z = fmaf(x2, p.z, x.z); x.w = fmaf(x3, p.w, x.w);
-        r.x = fmaf(-a0, q.x, r.x); r.y = fmaf(-a1, q.y, r.y); r.z = fmaf(-a2, q.z, r.z); r.w = fmaf(-a3, q.w, r.w);
-        if (any_fresh) {
-            if (f0) x.x = r.x = 0.0f;
-            if (f1) x.y = r.y = 0.0f;
-            if (f2) x.z = r.z = 0.0f;
-            if (f3) x.w = r.w = 0.0f;
+    if (work) {
+        const float a0 = (float)st[col].a, a1 = (float)st[col + 1].a, a2 = (float)st[col + 2].a,
+                    a3 = (float)st[col + 3].a;
+        const float x0 = xs * a0, x1 = xs * a1, x2 = xs * a2, x3 = xs * a3;
+        // a column being (re)admitted starts from x = 0, r = 0 (its y is scattered next)
+        const bool f0 = st[col].fresh, f1 = st[col + 1].fresh, f2 = st[col + 2].fresh, f3 = st[col + 3].fresh;
+        const bool any_fresh = f0 | f1 | f2 | f3;
+        for (int64_t row = r0; row < r1; row += RG) {
+            const int64_t o = row * ld + col;
+            const float4 p = ld4v(P + o), q = ld4v(Q + o);
+            float4 x = ld4v(X + o), r = ld4v(R + o);
+            x.x = fmaf(x0, p.x, x.x); x.y = fmaf(x1, p.y, x.y); x.z = fmaf(x2, p.z, x.z); x.w = fmaf(x3, p.w, x.w);
+            r.x = fmaf(-a0, q.x, r.x); r.y = fmaf(-a1, q.y, r.y); r.z = fmaf(-a2, q.z, r.z); r.w = fmaf(-a3, q.w, r.w);
+            if (any_fresh) {
+                if (f0) x.x = r.x = 0.0f;
+                if (f1) x.y = r.y = 0.0f;
+                if (f2) x.z = r.z = 0.0f;
+                if (f3) x.w = r.w = 0.0f;
+            }
+            st4(X + o, x);
+            st4(R + o, r);
+            ksum_add(acc[0], r.x * r.x);
+            ksum_add(acc[1], r.y * r.y);
+            ksum_add(acc[2], r.z * r.z);
+            ksum_add(acc[3], r.w * r.w);
         }
-        st4(X + o, x);
-        st4(R + o, r);
-        ksum_add(acc[0], r.x * r.x);
-        ksum_add(acc[1], r.y * r.y);
-        ksum_add(acc[2], r.z * r.z);
-        ksum_add(acc[3], r.w * r.w);
     }
-    block_reduce_cols<S>(acc, part + (int64_t)blockIdx.x * ld + blockIdx.y * S);
+    red_finish(part, ld, work, col, g, acc);
 }
 
 // P = R + beta P.
@@ -857,6 +879,46 @@ int hd_spmm_apply(hd_ctx* ctx, const hd_graph* g, const float* P, float* Q, int3
     return HD_OK;
 }
 
+// grid and block of the column reductions: one block row per chunk, up to 128 quads x 8 threads
+static inline dim3 red_grid(const Engine& E) {
+    const int nq = E.Bp / 4;
+    return dim3((unsigned)E.nch, (unsigned)ceil_div(nq, RQ));
+}
+static inline unsigned red_block(const Engine& E) {
+    const int nq = E.Bp / 4;
+    return (unsigned)(RG * (nq < RQ ? nq : RQ));
+}
+static inline size_t red_smem(const Engine& E) { return (size_t)red_block(E) * 4 * sizeof(float2); }
+
+static int launch_dot(Engine& E, float2* part, const ColState* st) {
+    hd_ctx* ctx = E.ctx;
+    HD_PROF(ctx, "dot");
+    k_dot<<<red_grid(E), red_block(E), red_smem(E), ctx->stream>>>(E.P, E.Q, E.n, E.Bp, E.rch, part, st);
+    HD_CHECK_LAUNCH(ctx);
+    return HD_OK;
+}
+
+static int launch_update(Engine& E) {
+    hd_ctx* ctx = E.ctx;
+    HD_PROF(ctx, "update");
+    k_update<<<red_grid(E), red_block(E), red_smem(E), ctx->stream>>>(E.X, E.R, E.P, E.Q, E.n, E.Bp, E.rch, E.st, E.xs, E.part);
+    HD_CHECK_LAUNCH(ctx);
+    return HD_OK;
+}
+
+static int launch_colsq(Engine& E, const float* V) {
+    hd_ctx* ctx = E.ctx;
+    HD_PROF(ctx, "colsq");
+    k_colsq<<<red_grid(E), red_block(E), red_smem(E), ctx->stream>>>(V, E.n, E.Bp, E.rch, E.part);
+    HD_CHECK_LAUNCH(ctx);
+    return HD_OK;
+}
+
+void engine_set_reduction(Engine& E) {
+    E.rch = reduction_chunk_rows(E.n);
+    E.nch = (E.n + E.rch - 1) / E.rch;
+}
+
 // Q = c1 P - c2 W P with the engine's slab width and segments (+ P^T Q partials)
 static int launch_spmm(Engine& E, float c1, float c2, float2* part, const ColState* st) {
     hd_ctx* ctx = E.ctx;
@@ -864,7 +926,7 @@ static int launch_spmm(Engine& E, float c1, float c2, float2* part, const ColSta
     dim3 grid(E.vl.nblk, E.vl.slabs);
     {
         HD_PROF(ctx, "spmm");
-        if (E.segK <= 1 && E.vl.S == 4) {
+        if (E.segK <= 1 && E.vl.S == 4 && E.warp_rows) {
             k_spmm_w4<<<grid, 256, 0, ctx->stream>>>(g->row_ptr, g->col, g->val, E.P, E.Q, E.n, E.Bp, c1, c2, st);
             HD_CHECK_LAUNCH(ctx);
         } else if (E.segK <= 1) {
@@ -880,11 +942,7 @@ static int launch_spmm(Engine& E, float c1, float c2, float2* part, const ColSta
             }
         }
     }
-    if (part) {
-        HD_PROF(ctx, "dot");
-        HD_DISPATCH_S(E.vl.S, (k_dot<SS><<<grid, 256, 0, ctx->stream>>>(E.P, E.Q, E.n, E.Bp, part, st)));
-        HD_CHECK_LAUNCH(ctx);
-    }
+    if (part) return launch_dot(E, part, st);
     return HD_OK;
 }
 
@@ -987,29 +1045,31 @@ int engine_iteration(Engine& S_, int (*after_update)(void*), void* arg) {
     const int r = S_.r;
     const bool lr_on = S_.has_lr;
     const int eff_mode = S_.eff_mode;
-    const float c1 = S_.c1, c2 = S_.c2, xs = S_.xs;
+    const float c1 = S_.c1, c2 = S_.c2;
     const int32_t max_iter = S_.max_iter;
     const double* Cd = lr_on ? S_.lr.C : nullptr;
     int rc;
     if (eff_mode == HD_MODE_PCG) {
         if ((rc = launch_spmm(S_, c1, c2, S_.part, S_.st))) return rc;
         { HD_PROF(ctx, "scalar");
-        k_fin_sigma<<<Bp, 128, 0, ctx->stream>>>(S_.part, S_.vl.nblk, Bp, S_.st, nullptr, nullptr, 0); }
+        k_fin_sigma<<<Bp, 128, 0, ctx->stream>>>(S_.part, (int)S_.nch, Bp, S_.st, nullptr, nullptr, 0); }
         HD_CHECK_LAUNCH(ctx);
-        LAUNCH_VEC(k_update, S_.X, S_.R, S_.P, S_.Q, n, Bp, S_.st, xs, S_.part);
+        if ((rc = launch_update(S_))) return rc;
     if (after_update && (rc = after_update(arg))) return rc;
         if ((rc = lr_reduce(ctx, S_.lr, S_.R, n, Bp, S_.num_active))) return rc;
         if ((rc = lr_finish(ctx, S_.lr, Bp, S_.dcoef))) return rc;
         { HD_PROF(ctx, "scalar");
         HD_CUDA(ctx, cudaMemsetAsync(S_.num_active, 0, sizeof(int), ctx->stream));
-        k_fin_rr<<<Bp, 128, 0, ctx->stream>>>(S_.part, S_.vl.nblk, Bp, S_.st, max_iter, Cd, S_.dcoef, r,
+        k_fin_rr<<<Bp, 128, 0, ctx->stream>>>(S_.part, (int)S_.nch, Bp, S_.st, max_iter, Cd, S_.dcoef, r,
                                              S_.num_active); }
         HD_CHECK_LAUNCH(ctx);
         if ((rc = lr_expand(ctx, S_.lr, EXP_DIRECTION, S_.P, S_.R, S_.P, n, Bp, S_.st, S_.num_active))) return rc;
     } else {
         if (S_.ts)
-            LAUNCH_VEC(k_spmm_cols, S_.ts->off, S_.ts->ci, S_.ts->wv, S_.ts->B, S_.P, S_.Q, n, Bp, c1, c2, S_.part,
-                       S_.st);
+        {
+            LAUNCH_VEC(k_spmm_cols, S_.ts->off, S_.ts->ci, S_.ts->wv, S_.ts->B, S_.P, S_.Q, n, Bp, c1, c2, S_.st);
+            if ((rc = launch_dot(S_, S_.part, S_.st))) return rc;
+        }
         else if ((rc = launch_spmm(S_, c1, c2, S_.part, S_.st)))
             return rc;
         if (lr_on) {
@@ -1017,14 +1077,14 @@ int engine_iteration(Engine& S_, int (*after_update)(void*), void* arg) {
                 return rc;
         }
         { HD_PROF(ctx, "scalar");
-        k_fin_sigma<<<Bp, 128, 0, ctx->stream>>>(S_.part, S_.vl.nblk, Bp, S_.st, Cd,
+        k_fin_sigma<<<Bp, 128, 0, ctx->stream>>>(S_.part, (int)S_.nch, Bp, S_.st, Cd,
                                                 lr_on ? S_.opcoef : nullptr, r); }
         HD_CHECK_LAUNCH(ctx);
-        LAUNCH_VEC(k_update, S_.X, S_.R, S_.P, S_.Q, n, Bp, S_.st, xs, S_.part);
+        if ((rc = launch_update(S_))) return rc;
     if (after_update && (rc = after_update(arg))) return rc;
         { HD_PROF(ctx, "scalar");
         HD_CUDA(ctx, cudaMemsetAsync(S_.num_active, 0, sizeof(int), ctx->stream));
-        k_fin_rr<<<Bp, 128, 0, ctx->stream>>>(S_.part, S_.vl.nblk, Bp, S_.st, max_iter, nullptr, nullptr, 0,
+        k_fin_rr<<<Bp, 128, 0, ctx->stream>>>(S_.part, (int)S_.nch, Bp, S_.st, max_iter, nullptr, nullptr, 0,
                                              S_.num_active); }
         HD_CHECK_LAUNCH(ctx);
         LAUNCH_VEC(k_direction, S_.P, S_.R, n, Bp, S_.st);
@@ -1055,7 +1115,7 @@ static int run_iterations_graph(Engine& E, int iters) {
         (uint64_t)(E.has_lr ? E.lr.e->sp_rp : nullptr), (uint64_t)(E.has_lr ? E.lr.e->sp_cp : nullptr), (uint64_t)E.R, (uint64_t)E.P, (uint64_t)E.Q, (uint64_t)E.X,
         (uint64_t)E.part, (uint64_t)E.st, (uint64_t)E.num_active, (uint64_t)E.lr.part, (uint64_t)E.lr.C,
         (uint64_t)E.lr.H, (uint64_t)E.lr.Hhi, (uint64_t)E.lr.Hlo, (uint64_t)E.dcoef, (uint64_t)E.opcoef,
-        (uint64_t)E.segK, (uint64_t)E.seg, (uint64_t)E.Bp, (uint64_t)E.vl.S, (uint64_t)E.vl.nblk, (uint64_t)E.vl.slabs, (uint64_t)E.lr.nchunk,
+        (uint64_t)E.segK, (uint64_t)E.seg, (uint64_t)E.nch, (uint64_t)E.Bp, (uint64_t)E.vl.S, (uint64_t)E.vl.nblk, (uint64_t)E.vl.slabs, (uint64_t)E.lr.nchunk,
         (uint64_t)E.lr.rpad, (uint64_t)E.lr.Bp16, (uint64_t)E.has_lr, (uint64_t)E.eff_mode, (uint64_t)E.r,
         (uint64_t)E.max_iter, (uint64_t)iters, fbits(E.c1), fbits(E.c2),
         fbits(E.xs), (uint64_t)ctx->stream};
@@ -1136,6 +1196,7 @@ int hd_query_impl(hd_ctx* ctx, const hd_graph* g, const TruncSys* ts, const hd_e
     S_.g = g;
     S_.ts = ts;
     S_.n = ts ? ts->smax : g->n;
+    engine_set_reduction(S_);
     S_.B = B;
     S_.Bp = (B + 3) / 4 * 4;
     S_.vl = vec_launch(ctx, S_.n, S_.Bp, pick_slab(S_.Bp));
@@ -1166,7 +1227,7 @@ int hd_query_impl(hd_ctx* ctx, const hd_graph* g, const TruncSys* ts, const hd_e
     if (lr_on) nchunk = lr_nchunk(ctx, eig, Bp);
 
     size_t vec = (size_t)n * Bp * sizeof(float);
-    size_t bytes = 3 * ws_size(vec) + (x_direct ? 0 : ws_size(vec)) + ws_size((size_t)ctx->num_sms * 8 * Bp * sizeof(float2)) +
+    size_t bytes = 3 * ws_size(vec) + (x_direct ? 0 : ws_size(vec)) + ws_size((size_t)S_.nch * Bp * sizeof(float2)) +
                    ws_size(Bp * sizeof(ColState)) + ws_size(64) + ws_size((B + 1) * 4) + 2 * ws_size(nnz_y * 4 + 4) +
                    ws_size(B * 4);
     if (lr_on)
@@ -1180,7 +1241,7 @@ int hd_query_impl(hd_ctx* ctx, const hd_graph* g, const TruncSys* ts, const hd_e
     S_.P = cv.take<float>((size_t)n * Bp);
     S_.Q = cv.take<float>((size_t)n * Bp);
     S_.X = x_direct ? X : cv.take<float>((size_t)n * Bp);
-    S_.part = cv.take<float2>((size_t)ctx->num_sms * 8 * Bp);
+    S_.part = cv.take<float2>((size_t)S_.nch * Bp);
     S_.st = cv.take<ColState>(Bp);
     S_.num_active = cv.take<int>(16);
     S_.err = S_.num_active + 1;
@@ -1251,9 +1312,9 @@ int hd_query_impl(hd_ctx* ctx, const hd_graph* g, const TruncSys* ts, const hd_e
     HD_CHECK_LAUNCH(ctx);
     const double* Cd = lr_on ? S_.lr.C : nullptr;
     if (eff_mode == HD_MODE_PAPER) {
-        LAUNCH_VEC(k_colsq, S_.R, n, Bp, S_.part);
+        if ((rc = launch_colsq(S_, S_.R))) return rc;
         HD_CUDA(ctx, cudaMemsetAsync(S_.num_active, 0, sizeof(int), ctx->stream));
-        k_fin_setup<<<Bp, 128, 0, ctx->stream>>>(S_.part, S_.vl.nblk, Bp, B, (const float*)tl, S_.st, nullptr, nullptr,
+        k_fin_setup<<<Bp, 128, 0, ctx->stream>>>(S_.part, (int)S_.nch, Bp, B, (const float*)tl, S_.st, nullptr, nullptr,
                                                 0, S_.num_active);
         HD_CHECK_LAUNCH(ctx);
         HD_CUDA(ctx, cudaMemcpyAsync(S_.P, S_.R, vec, cudaMemcpyDeviceToDevice, ctx->stream));
@@ -1270,20 +1331,20 @@ int hd_query_impl(hd_ctx* ctx, const hd_graph* g, const TruncSys* ts, const hd_e
         if ((rc = lr_expand(ctx, S_.lr, EXP_SET_X, S_.X, nullptr, nullptr, n, Bp, S_.st))) return rc;
         if ((rc = lr_finish(ctx, S_.lr, Bp, S_.ones))) return rc;
         if ((rc = lr_expand(ctx, S_.lr, EXP_SUB_R, S_.R, nullptr, nullptr, n, Bp, S_.st))) return rc;
-        LAUNCH_VEC(k_colsq, S_.R, n, Bp, S_.part);
+        if ((rc = launch_colsq(S_, S_.R))) return rc;
         HD_CUDA(ctx, cudaMemsetAsync(S_.num_active, 0, sizeof(int), ctx->stream));
-        k_fin_setup<<<Bp, 128, 0, ctx->stream>>>(S_.part, S_.vl.nblk, Bp, B, (const float*)tl, S_.st, nullptr, nullptr,
+        k_fin_setup<<<Bp, 128, 0, ctx->stream>>>(S_.part, (int)S_.nch, Bp, B, (const float*)tl, S_.st, nullptr, nullptr,
                                                 0, S_.num_active);
         HD_CHECK_LAUNCH(ctx);
         HD_CUDA(ctx, cudaMemcpyAsync(S_.P, S_.R, vec, cudaMemcpyDeviceToDevice, ctx->stream));
         if ((rc = lr_reduce(ctx, S_.lr, S_.P, n, Bp))) return rc;
         if ((rc = lr_finish(ctx, S_.lr, Bp, S_.opcoef))) return rc;
     } else {  // PCG
-        LAUNCH_VEC(k_colsq, S_.R, n, Bp, S_.part);
+        if ((rc = launch_colsq(S_, S_.R))) return rc;
         if ((rc = lr_reduce(ctx, S_.lr, S_.R, n, Bp))) return rc;
         if ((rc = lr_finish(ctx, S_.lr, Bp, S_.dcoef))) return rc;
         HD_CUDA(ctx, cudaMemsetAsync(S_.num_active, 0, sizeof(int), ctx->stream));
-        k_fin_setup<<<Bp, 128, 0, ctx->stream>>>(S_.part, S_.vl.nblk, Bp, B, (const float*)tl, S_.st, Cd, S_.dcoef, r,
+        k_fin_setup<<<Bp, 128, 0, ctx->stream>>>(S_.part, (int)S_.nch, Bp, B, (const float*)tl, S_.st, Cd, S_.dcoef, r,
                                                 S_.num_active);
         HD_CHECK_LAUNCH(ctx);
         HD_CUDA(ctx, cudaMemsetAsync(S_.P, 0, vec, ctx->stream));

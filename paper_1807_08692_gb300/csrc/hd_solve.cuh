@@ -84,7 +84,12 @@ struct Engine {
     int64_t n = 0;
     int32_t B = 0, Bp = 0;
     VecLaunch vl{};
+    int rch = 64;                      // rows per reduction chunk (depends on n only)
+    int64_t nch = 0;                   // reduction chunks: column partials are [nch][Bp]
     int segK = 1;                      // SpMM node-range segments (1: one pass)
+    // 4-column slabs may use the warp-per-row SpMM (its sums run in another
+    // order than the other slab widths'; the server keeps one order throughout)
+    bool warp_rows = true;
     const int32_t* seg = nullptr;      // their row bounds [segK + 1][n]
     float *R = nullptr, *P = nullptr, *Q = nullptr, *X = nullptr;
     float2* part = nullptr;
@@ -109,6 +114,9 @@ int simt_nchunk(hd_ctx* ctx, int64_t n, int rpad, int Bp);
 // (graph, Bp) over K in {1, 2, 4, 8} (HD_SEGMENTS overrides); sets E.segK / E.seg.
 int tune_segments(hd_ctx* ctx, Engine& E);
 int engine_iteration(Engine& E, int (*after_update)(void*), void* arg);
+// rows per reduction chunk for n rows, and the engine's chunk count from it
+int reduction_chunk_rows(int64_t n);
+void engine_set_reduction(Engine& E);
 int hd_query_impl(hd_ctx* ctx, const hd_graph* g, const TruncSys* ts, const hd_eig* eig, int mode, int32_t B,
                   const int32_t* y_ptr, const int32_t* y_idx, const float* y_val, float alpha, const float* tol,
                   int32_t max_iter, float* X, int32_t ldx, int32_t* iters, float* relres, int32_t* status);

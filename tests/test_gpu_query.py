@@ -282,3 +282,33 @@ def test_small_batches(gpu_ctx, g1, cfg1_data, B):
         X, it, rr, st = hd.query_batch(gpu_ctx, g1, e, m, *sub, 0.99, 1e-6, 500)
         assert np.all(st == 0)
         assert rel_l2_cols(X.cpu().numpy().astype(np.float64), cfg1_data["xstar"][:, :B]).max() <= TOL_REL
+
+
+def test_results_independent_of_slab_width(gpu_ctx, cfg1_data, tmp_path):
+    # column sums are chunked by rows, so the slab width of the vector kernels
+    # (HD_SLAB caps it) leaves every score bit-for-bit unchanged
+    import os
+    import subprocess
+    import sys
+    here = os.path.dirname(os.path.abspath(__file__))
+    rp, col, val = csr_of(cfg1_data["A"])
+    np.savez(tmp_path / "case.npz", rp=rp, col=col, val=val, yp=cfg1_data["yp"], yi=cfg1_data["yi"],
+             yv=cfg1_data["yv"], lam=cfg1_data["lam"][:30], U=cfg1_data["U"][:, :30])
+    script = (
+        "import sys, numpy as np\n"
+        f"sys.path.insert(0, {os.path.dirname(here)!r}); sys.path.insert(0, {here!r})\n"
+        "import paper_1807_08692_gb300 as hd\n"
+        "from _helpers import y_arrays\n"
+        f"z = np.load({str(tmp_path / 'case.npz')!r})\n"
+        "ctx = hd.Context(0)\n"
+        "g = hd.graph_from_csr(ctx, z['rp'], z['col'], z['val'])\n"
+        "eig = hd.eig_from_host(ctx, g, z['lam'], z['U'], 'bf16')\n"
+        "X, it, rr, st = hd.query_batch(ctx, g, eig, 'pcg', *y_arrays(z['yp'], z['yi'], z['yv']), 0.99, 1e-6, 500)\n"
+        "np.save(sys.argv[1], X.cpu().numpy())\n")
+    out = []
+    for S in (8, 16):
+        env = dict(os.environ, HD_SLAB=str(S))
+        f = tmp_path / f"x{S}.npy"
+        subprocess.run([sys.executable, "-c", script, str(f)], env=env, check=True, timeout=300)
+        out.append(np.load(f))
+    assert np.array_equal(out[0].view(np.uint32), out[1].view(np.uint32))
