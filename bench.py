@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--sweep", type=int, default=1, help="run the storage / rank / batch sweep")
     ap.add_argument("--sweep-batches", default="1,16,256")
     ap.add_argument("--shortlist", type=int, default=75000, help="Temporal† shortlist size (0: skip the leg)")
+    ap.add_argument("--sweep-r400", type=int, default=1, help="add an r=400 leg (its own Lanczos) to the sweep")
     ap.add_argument("--trunc-iters", type=int, default=20, help="Temporal† CG iterations (Table 1: 20)")
     return ap.parse_args()
 
@@ -383,10 +384,21 @@ def sweep_leg(ctx, wl, args, alpha):
             e = hd.eig_from_host(ctx, g, lam, U32, st)
             run(f"pcg r={r} {st}", e, "pcg", args.batch, r=r, storage=st)
             e.close()
-        r2 = min(50, r)
-        e = hd.eig_from_host(ctx, g, lam[:r2], np.ascontiguousarray(U32[:, :r2]), "bf16")
-        run(f"pcg r={r2} bf16", e, "pcg", args.batch, r=r2, storage="bf16")
-        e.close()
+        for r2 in sorted({min(50, r), min(100, r)}):
+            if r2 == r:
+                continue
+            e = hd.eig_from_host(ctx, g, lam[:r2], np.ascontiguousarray(U32[:, :r2]), "bf16")
+            run(f"pcg r={r2} bf16", e, "pcg", args.batch, r=r2, storage="bf16")
+            e.close()
+        if args.sweep_r400 and r < 400:
+            # the top of the rank range of the paper's sweep: its own Lanczos run
+            t0 = time.time()
+            e4, lam4, res4, conv4 = hd.eigendecompose(ctx, g, 400, block=32, tol=1e-5, max_restarts=args.restarts,
+                                                      storage="bf16")
+            t_l = time.time() - t0
+            run("pcg r=400 bf16", e4, "pcg", args.batch, r=400, storage="bf16", lanczos_s=round(t_l, 1),
+                lambda_r=round(float(lam4[-1]), 5))
+            e4.close()
         run(f"paper r={r} {args.storage}", wl["eig"], "paper", args.batch, r=r, storage=args.storage)
         # SHybrid (Sec. 5.3): 99% of the embedding's entries dropped
         es = wl["eig"].sparsify(0.99)
@@ -451,9 +463,12 @@ def convergence_leg(ctx, wl, rows_in, alpha):
     t_min = time.perf_counter() - t0
     lam = wl["lam"]
     out = []
-    for r, mode, tol, measured in rows_in:
+    for row in rows_in:
+        r, mode, tol, measured = row[:4]
         if r == 0:
             lam_next = 1.0
+        elif len(row) > 4 and row[4] is not None:
+            lam_next = float(row[4])  # lambda_r of the leg's own eigenpairs (lambda_{r+1} <= it)
         else:
             lam_next = float(lam[min(r, len(lam) - 1)])
         kap, ia, ir = hd.cg_bound(mode if r > 0 else "paper", alpha, lam_next, min(lam_min, lam_next), tol)
@@ -597,7 +612,7 @@ def main():
         for sw in sweep or []:
             if sw["mode"] == args.mode and sw.get("storage") == args.storage and sw["B"] == B \
                     and "sparsity" not in sw and sw["r"] != args.r:
-                rows_in.append((sw["r"], sw["mode"], sw["tol"], sw["iters_max"]))
+                rows_in.append((sw["r"], sw["mode"], sw["tol"], sw["iters_max"], sw.get("lambda_r")))
         conv = convergence_leg(ctx, wl, rows_in, alpha)
     # ---- serving: continuous batching under Poisson load
     serving = None
