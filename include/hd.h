@@ -336,20 +336,25 @@ typedef struct hd_req_stats {
     int32_t iters;      /* CG iterations the request used */
     int32_t status;     /* HD_COL_* */
     float relres;       /* final relative residual ||r|| / ||y|| */
-    int32_t slot;       /* batch column it ran in */
+    int32_t slot;       /* batch column it ran in (narrow-lane columns follow the wide ones) */
 } hd_req_stats;
 
 /* Open a server over a graph and optional eigenpairs.  The server owns one
  * persistent batch of up to max_slots columns (<= 256); with mem_budget > 0
  * the slot count is cut to what fits (each slot needs 4*n*4 + Kmax*8 bytes for
- * its R, P, Q, X columns and ranking).  With eigenpairs the mode must be
- * HD_MODE_PCG (the paper's form needs a per-request spectral term at
- * admission); without, it is temporal CG.  Kmax <= 2048 bounds per-request K.
+ * its R, P, Q, X columns and ranking).  When that batch has at least 8
+ * columns and the budget (if any) holds 4 more, a second, narrow batch of 4
+ * columns is kept too: a lightly loaded server (wide batch idle, queue no
+ * longer than the narrow batch's free columns) admits there, where a request
+ * moves 16 bytes per row instead of 4 x slots; results are the same bits in
+ * either batch.  With eigenpairs the mode must be HD_MODE_PCG (the paper's
+ * form needs a per-request spectral term at admission); without, it is
+ * temporal CG.  Kmax <= 2048 bounds per-request K.
  * Errors: HD_ERR_OOM when not even one slot fits the budget or the device. */
 int hd_serve_open(hd_ctx* ctx, const hd_graph* g, const hd_eig* eig, int mode, float alpha,
                   int32_t max_slots, size_t mem_budget, int32_t max_iter, int32_t Kmax,
                   hd_server** out);
-/* Columns of the persistent batch. */
+/* Columns of the wide persistent batch. */
 int hd_serve_slots(const hd_server* s);
 /* Queue one request: its observation (nnz_y <= 512 host entries, indices in
  * [0, n), duplicates summed), residual tolerance and K <= Kmax.  Copies the

@@ -1,14 +1,22 @@
 // Continuous-batching query server over the multi-RHS CG engine.
 //
-// A server owns one persistent batch of `slots` columns (R, P, Q, X of n x Bp).
-// Requests queue on the host; at each step free columns take queued requests
-// (admission: the column is marked fresh, the next CG update resets it and its
-// observation is scattered in, and the scalar step starts its iteration),
-// every column then advances the same CG iterations, and columns whose
-// residual met their own tolerance retire: their top-K is ranked and copied
-// out and the column is free again.  A column's arithmetic never depends on
-// its slot or on the other columns, so a request gets the same bits alone or
-// in a mix.
+// A server owns persistent batches ("lanes") of columns (R, P, Q, X of n x Bp):
+// the wide lane of `slots` columns and, when there is room, a narrow lane of
+// four.  Requests queue on the host; at each step free columns take queued
+// requests (admission: the column is marked fresh, the next CG update resets it
+// and its observation is scattered in, and the scalar step starts its
+// iteration), every column of a running lane advances the same CG iterations,
+// and columns whose residual met their own tolerance retire: their top-K is
+// ranked and copied out and the column is free again.
+//
+// A lightly loaded server (wide lane idle, queue no longer than the narrow
+// lane's free columns) admits into the narrow lane: its rows are 16 bytes
+// instead of 4 x slots bytes, so one request moves far fewer bytes per
+// iteration.  Otherwise requests go to the wide lane.  A column's arithmetic
+// never depends on its lane, slot or the other columns (per-element SpMM order
+// is the same for every slab width, reductions are chunked by rows, the
+// tensor-core products treat columns independently), so a request gets the
+// same bits alone or in a mix.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -32,7 +40,7 @@ struct Req {
     double bb = 0.0;
     float tol = 0.f;
     int32_t K = 0;
-    int32_t slot = -1;
+    int32_t slot = -1;      // reported slot (narrow-lane slots follow the wide ones)
     double submit_s = 0, admit_s = 0, done_s = 0;
     int32_t iters = 0, status = 0;
     float relres = 0.f;
@@ -73,12 +81,13 @@ __global__ void k_admit_scatter(const AdmitRec* recs, int nrec, const int32_t* y
 
 }  // namespace
 
-struct hd_server {
-    hd_ctx* ctx = nullptr;
-    const hd_graph* g = nullptr;
-    const hd_eig* eig = nullptr;
-    int32_t slots = 0, Kmax = 0, max_iter = 0;
+
+// One persistent batch of columns and everything it needs on both sides.
+struct Lane {
     Engine E;
+    int32_t slots = 0;
+    int32_t slot_base = 0;  // reported slot number of column 0
+    int S_full = 4;         // SpMM slab width measured for the whole lane
     void* dev = nullptr;
     // admission staging
     AdmitRec* d_rec = nullptr;
@@ -89,79 +98,84 @@ struct hd_server {
     float* h_yval = nullptr;
     int32_t cap_nnz = 0;
     int nrec = 0;
+    hd_ctx* ctx = nullptr;
     // ranking outputs
     int32_t* d_idx = nullptr;
     float* d_sc = nullptr;
     int32_t* h_idx = nullptr;
     float* h_sc = nullptr;
     ColState* h_st = nullptr;
-    std::deque<Req*> queue;
     std::vector<Req*> slot_req;
+
+    bool running() const {
+        for (Req* r : slot_req)
+            if (r) return true;
+        return false;
+    }
+    int32_t free_slots() const {
+        int32_t f = 0;
+        for (Req* r : slot_req) f += r == nullptr;
+        return f;
+    }
+};
+
+struct hd_server {
+    hd_ctx* ctx = nullptr;
+    const hd_graph* g = nullptr;
+    const hd_eig* eig = nullptr;
+    int32_t Kmax = 0, max_iter = 0;
+    Lane lanes[2];  // [0] wide, [1] narrow (slots == 0 when absent)
+    std::deque<Req*> queue;
     std::unordered_map<uint64_t, Req*> reqs;
     std::deque<uint64_t> finished;  // tickets retired and not yet reported by hd_serve_completed
     uint64_t next_ticket = 1;
-    int S_full = 4;  // SpMM slab width measured for the whole batch
-    bool polled = true;
 };
+
+static void lane_free(hd_ctx* ctx, Lane& L) {
+    if (ctx) cudaStreamSynchronize(ctx->stream);
+    cudaFree(L.dev);
+    cudaFreeHost(L.h_rec);
+    cudaFreeHost(L.h_yidx);
+    cudaFreeHost(L.h_yval);
+    cudaFreeHost(L.h_idx);
+    cudaFreeHost(L.h_sc);
+    cudaFreeHost(L.h_st);
+    L = Lane();
+}
 
 static void server_free(hd_server* s) {
     if (!s) return;
-    if (s->ctx) cudaStreamSynchronize(s->ctx->stream);
-    cudaFree(s->dev);
-    cudaFreeHost(s->h_rec);
-    cudaFreeHost(s->h_yidx);
-    cudaFreeHost(s->h_yval);
-    cudaFreeHost(s->h_idx);
-    cudaFreeHost(s->h_sc);
-    cudaFreeHost(s->h_st);
+    for (Lane& L : s->lanes) lane_free(s->ctx, L);
     for (auto& kv : s->reqs) delete kv.second;
     delete s;
 }
 
 static int admit_cb(void* arg) {
-    hd_server* s = (hd_server*)arg;
-    if (!s->nrec) return HD_OK;
-    hd_ctx* ctx = s->ctx;
-    k_admit_scatter<<<ceil_div(s->nrec, 64), 64, 0, ctx->stream>>>(s->d_rec, s->nrec, s->d_yidx, s->d_yval, s->E.R,
-                                                                   s->E.Bp);
+    Lane* L = (Lane*)arg;
+    if (!L->nrec) return HD_OK;
+    hd_ctx* ctx = L->ctx;
+    k_admit_scatter<<<ceil_div(L->nrec, 64), 64, 0, ctx->stream>>>(L->d_rec, L->nrec, L->d_yidx, L->d_yval, L->E.R,
+                                                                   L->E.Bp);
     HD_CHECK_LAUNCH(ctx);
-    s->nrec = 0;
+    L->nrec = 0;
     return HD_OK;
 }
 
-extern "C" {
-
-int hd_serve_open(hd_ctx* ctx, const hd_graph* g, const hd_eig* eig, int mode, float alpha, int32_t max_slots,
-                  size_t mem_budget, int32_t max_iter, int32_t Kmax, hd_server** out) {
-    if (!ctx || !g || !out || max_slots < 1 || max_slots > 256 || Kmax < 1 || Kmax > 2048 || max_iter < 1)
-        return HD_ERR_INVALID_ARG;
-    if (!(alpha >= 0.0f && alpha < 1.0f)) return hd_fail(ctx, HD_ERR_INVALID_ARG, "alpha=%g", alpha);
+// Buffers and engine of one lane of `slots` columns.
+static int lane_open(hd_ctx* ctx, const hd_graph* g, const hd_eig* eig, float alpha, int32_t slots, int32_t max_iter,
+                     int32_t Kmax, int32_t slot_base, Lane& L) {
     const bool lr_on = eig && eig->r > 0;
-    if (lr_on && mode != HD_MODE_PCG)
-        return hd_fail(ctx, HD_ERR_INVALID_ARG, "the server runs PCG with eigenpairs (mode %d unsupported)", mode);
-    *out = nullptr;
-    HD_CUDA(ctx, cudaSetDevice(ctx->device));
     const int64_t n = g->n;
-    // admission by device memory: each slot holds R, P, Q, X columns and its ranking
-    const size_t per_slot = (size_t)4 * n * 4 + (size_t)Kmax * 8;
-    int32_t slots = max_slots;
-    if (mem_budget > 0) slots = (int32_t)std::min<size_t>(max_slots, mem_budget / per_slot);
-    if (slots < 1) return hd_fail(ctx, HD_ERR_OOM, "memory budget %zu below one slot (%zu bytes)", mem_budget, per_slot);
-    hd_server* s = new hd_server();
-    s->ctx = ctx;
-    s->g = g;
-    s->eig = eig;
-    s->slots = slots;
-    s->Kmax = Kmax;
-    s->max_iter = max_iter;
-    Engine& E = s->E;
+    L.ctx = ctx;
+    L.slots = slots;
+    L.slot_base = slot_base;
+    Engine& E = L.E;
     E.ctx = ctx;
     E.g = g;
     E.n = n;
     engine_set_reduction(E);
     E.B = slots;
     E.Bp = (slots + 3) / 4 * 4;
-    E.vl = vec_launch(ctx, n, E.Bp);  // re-tuned below once the buffers exist
     E.has_lr = lr_on;
     E.r = lr_on ? eig->r : 0;
     E.eff_mode = lr_on ? HD_MODE_PCG : HD_MODE_PAPER;
@@ -169,26 +183,29 @@ int hd_serve_open(hd_ctx* ctx, const hd_graph* g, const hd_eig* eig, int mode, f
     E.c2 = (float)((double)alpha / (1.0 - (double)alpha));
     E.xs = 1.0f;
     E.max_iter = max_iter;
+    // one SpMM order in every lane: thread-per-row sums, a single pass
+    E.warp_rows = false;
+    E.segK = 1;
+    E.seg = nullptr;
     const int32_t Bp = E.Bp;
     const int rpad = lr_on ? (eig->r + 63) / 64 * 64 : 0;
     const int Bp16 = (Bp + 15) / 16 * 16;
-    int nchunk = 0;
-    if (lr_on) nchunk = lr_nchunk(ctx, eig, Bp);
-    s->cap_nnz = Bp * 512;
+    const int nchunk = lr_on ? lr_nchunk(ctx, eig, Bp) : 0;
+    L.cap_nnz = Bp * 512;
     const size_t vec = (size_t)n * Bp * 4;
     size_t bytes = 4 * ws_size(vec) + ws_size((size_t)E.nch * Bp * 8) + ws_size(Bp * sizeof(ColState)) +
-                   ws_size(64) + ws_size(Bp * sizeof(AdmitRec)) + 2 * ws_size((size_t)s->cap_nnz * 4) +
+                   ws_size(64) + ws_size(Bp * sizeof(AdmitRec)) + 2 * ws_size((size_t)L.cap_nnz * 4) +
                    2 * ws_size((size_t)Bp * Kmax * 4);
     if (lr_on)
         bytes += ws_size((size_t)nchunk * rpad * Bp * 4) + ws_size((size_t)rpad * Bp * 8) +
                  ws_size((size_t)rpad * Bp * 4) + 2 * ws_size((size_t)Bp16 * rpad * 2) + ws_size(rpad * 8);
-    if (cudaMalloc(&s->dev, bytes) != cudaSuccess) {
+    if (cudaMalloc(&L.dev, bytes) != cudaSuccess) {
         cudaGetLastError();
-        server_free(s);
+        L.dev = nullptr;
         return hd_fail(ctx, HD_ERR_OOM, "server buffers: %zu bytes", bytes);
     }
-    s->slot_req.assign(slots, nullptr);
-    WsCarver cv(s->dev);
+    L.slot_req.assign(slots, nullptr);
+    WsCarver cv(L.dev);
     E.R = cv.take<float>((size_t)n * Bp);
     E.P = cv.take<float>((size_t)n * Bp);
     E.Q = cv.take<float>((size_t)n * Bp);
@@ -198,20 +215,12 @@ int hd_serve_open(hd_ctx* ctx, const hd_graph* g, const hd_eig* eig, int mode, f
     E.num_active = cv.take<int>(16);
     E.err = E.num_active + 1;
     E.vl = vec_launch(ctx, n, Bp, tune_slab(ctx, g, Bp, E.P, E.Q));
-    s->S_full = E.vl.S;
-    E.warp_rows = false;
-    {
-        const int trc = tune_segments(ctx, E);
-        if (trc) {
-            server_free(s);
-            return trc;
-        }
-    }
-    s->d_rec = cv.take<AdmitRec>(Bp);
-    s->d_yidx = cv.take<int32_t>(s->cap_nnz);
-    s->d_yval = cv.take<float>(s->cap_nnz);
-    s->d_idx = cv.take<int32_t>((size_t)Bp * Kmax);
-    s->d_sc = cv.take<float>((size_t)Bp * Kmax);
+    L.S_full = E.vl.S;
+    L.d_rec = cv.take<AdmitRec>(Bp);
+    L.d_yidx = cv.take<int32_t>(L.cap_nnz);
+    L.d_yval = cv.take<float>(L.cap_nnz);
+    L.d_idx = cv.take<int32_t>((size_t)Bp * Kmax);
+    L.d_sc = cv.take<float>((size_t)Bp * Kmax);
     if (lr_on) {
         E.lr.e = eig;
         E.lr.rpad = rpad;
@@ -232,25 +241,189 @@ int hd_serve_open(hd_ctx* ctx, const hd_graph* g, const hd_eig* eig, int mode, f
         HD_CUDA(ctx, cudaMemsetAsync(E.lr.Hhi, 0, (size_t)Bp16 * rpad * 2, ctx->stream));
         HD_CUDA(ctx, cudaMemsetAsync(E.lr.Hlo, 0, (size_t)Bp16 * rpad * 2, ctx->stream));
     }
-    HD_CUDA(ctx, cudaMemsetAsync(s->dev, 0, 4 * ws_size(vec), ctx->stream));
+    HD_CUDA(ctx, cudaMemsetAsync(L.dev, 0, 4 * ws_size(vec), ctx->stream));
+    HD_CUDA(ctx, cudaMemsetAsync(E.num_active, 0, 16 * sizeof(int), ctx->stream));
     std::vector<ColState> st0(Bp);
     for (auto& c : st0) {
         memset(&c, 0, sizeof c);
         c.status = HD_COL_EMPTY;
     }
     HD_CUDA(ctx, cudaMemcpyAsync(E.st, st0.data(), Bp * sizeof(ColState), cudaMemcpyHostToDevice, ctx->stream));
-    if (cudaMallocHost(&s->h_rec, Bp * sizeof(AdmitRec)) || cudaMallocHost(&s->h_yidx, (size_t)s->cap_nnz * 4) ||
-        cudaMallocHost(&s->h_yval, (size_t)s->cap_nnz * 4) || cudaMallocHost(&s->h_idx, (size_t)Bp * Kmax * 4) ||
-        cudaMallocHost(&s->h_sc, (size_t)Bp * Kmax * 4) || cudaMallocHost(&s->h_st, Bp * sizeof(ColState))) {
-        server_free(s);
+    if (cudaMallocHost(&L.h_rec, Bp * sizeof(AdmitRec)) || cudaMallocHost(&L.h_yidx, (size_t)L.cap_nnz * 4) ||
+        cudaMallocHost(&L.h_yval, (size_t)L.cap_nnz * 4) || cudaMallocHost(&L.h_idx, (size_t)Bp * Kmax * 4) ||
+        cudaMallocHost(&L.h_sc, (size_t)Bp * Kmax * 4) || cudaMallocHost(&L.h_st, Bp * sizeof(ColState))) {
+        cudaGetLastError();
         return hd_fail(ctx, HD_ERR_OOM, "pinned host buffers");
     }
+    return HD_OK;
+}
+
+// Move queued requests into free columns of lane L (lowest free slot first).
+static int lane_admit(hd_server* s, Lane& L, int32_t& iters) {
+    hd_ctx* ctx = s->ctx;
+    L.nrec = 0;
+    int32_t off = 0;
+    for (int j = 0; j < L.slots && !s->queue.empty(); ++j) {
+        if (L.slot_req[j]) continue;
+        Req* r = s->queue.front();
+        if (off + (int32_t)r->idx.size() > L.cap_nnz) break;
+        s->queue.pop_front();
+        r->slot = L.slot_base + j;
+        r->admit_s = now_s();
+        L.slot_req[j] = r;
+        AdmitRec& a = L.h_rec[L.nrec++];
+        a.slot = j;
+        a.off = off;
+        a.cnt = (int32_t)r->idx.size();
+        a.tol = r->tol;
+        a.bb = r->bb;
+        std::copy(r->idx.begin(), r->idx.end(), L.h_yidx + off);
+        std::copy(r->val.begin(), r->val.end(), L.h_yval + off);
+        off += a.cnt;
+    }
+    if (L.nrec) {
+        HD_CUDA(ctx, cudaMemcpyAsync(L.d_rec, L.h_rec, L.nrec * sizeof(AdmitRec), cudaMemcpyHostToDevice, ctx->stream));
+        HD_CUDA(ctx, cudaMemcpyAsync(L.d_yidx, L.h_yidx, (size_t)off * 4, cudaMemcpyHostToDevice, ctx->stream));
+        HD_CUDA(ctx, cudaMemcpyAsync(L.d_yval, L.h_yval, (size_t)off * 4, cudaMemcpyHostToDevice, ctx->stream));
+        k_admit_mark<<<ceil_div(L.nrec, 64), 64, 0, ctx->stream>>>(L.d_rec, L.nrec, L.E.st, L.E.num_active);
+        HD_CHECK_LAUNCH(ctx);
+        if (iters < 1) iters = 1;  // the admission completes inside the next iteration
+    }
+    return HD_OK;
+}
+
+// `iters` CG iterations of lane L, then retirement of its stopped columns.
+static int lane_step(hd_server* s, Lane& L, int32_t iters) {
+    hd_ctx* ctx = s->ctx;
+    Engine& E = L.E;
+    const int32_t Bp = E.Bp;
+    const bool running = L.nrec > 0 || L.running();
+    if (!running) return HD_OK;
+    // the tensor-core products skip the columns above the highest occupied slot
+    // (admission fills the lowest free slots); per-column arithmetic is unchanged
+    int32_t live = 0;
+    for (int j = 0; j < L.slots; ++j)
+        if (L.slot_req[j]) live = j + 1;
+    E.lr.live = live;
+    // the narrowest slab that holds every occupied column (at most the width
+    // measured for the full lane): a lightly loaded lane gathers less per SpMM
+    // row.  Results do not depend on it: the reductions are chunked by rows,
+    // and every slab width sums a row's entries in the same order.
+    int S = L.S_full;
+    for (int c : {4, 8, 16, 32, 64, 128})
+        if (c >= live && c <= L.S_full && Bp % c == 0) {
+            S = c;
+            break;
+        }
+    if (S != E.vl.S) E.vl = vec_launch(ctx, E.n, Bp, S);
+    for (int t = 0; t < iters; ++t) {
+        int rc = engine_iteration(E, admit_cb, &L);
+        if (rc) return rc;
+    }
+    // ---- poll and retire
+    HD_CUDA(ctx, cudaMemcpyAsync(L.h_st, E.st, Bp * sizeof(ColState), cudaMemcpyDeviceToHost, ctx->stream));
     HD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    std::vector<int32_t> Kc(Bp, 0);
+    std::vector<int> fin;
+    for (int j = 0; j < L.slots; ++j) {
+        Req* r = L.slot_req[j];
+        if (r && !L.h_st[j].active && !L.h_st[j].fresh) {
+            Kc[j] = r->K;
+            fin.push_back(j);
+        }
+    }
+    if (fin.empty()) return HD_OK;
+    int rc;
+    {
+        HD_PROF(ctx, "rank");
+        rc = hd_rank_impl(ctx, E.X, E.n, Bp, Bp, Kc.data(), s->Kmax, 0, L.d_idx, L.d_sc);
+    }
+    if (rc) return rc;
+    for (int j : fin) {
+        HD_CUDA(ctx, cudaMemcpyAsync(L.h_idx + (size_t)j * s->Kmax, L.d_idx + (size_t)j * s->Kmax,
+                                     (size_t)s->Kmax * 4, cudaMemcpyDeviceToHost, ctx->stream));
+        HD_CUDA(ctx, cudaMemcpyAsync(L.h_sc + (size_t)j * s->Kmax, L.d_sc + (size_t)j * s->Kmax,
+                                     (size_t)s->Kmax * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    HD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    const double t_done = now_s();
+    for (int j : fin) {
+        Req* r = L.slot_req[j];
+        const ColState& c = L.h_st[j];
+        r->iters = c.iters;
+        r->status = c.status;
+        r->relres = c.bb > 0 ? (float)std::sqrt(c.rr / c.bb) : 0.f;
+        r->out_idx.assign(L.h_idx + (size_t)j * s->Kmax, L.h_idx + (size_t)j * s->Kmax + r->K);
+        r->out_score.assign(L.h_sc + (size_t)j * s->Kmax, L.h_sc + (size_t)j * s->Kmax + r->K);
+        r->done_s = t_done;
+        r->done = true;
+        s->finished.push_back(r->ticket);
+        L.slot_req[j] = nullptr;
+    }
+    return HD_OK;
+}
+
+// Launch, once, every kernel a lane can use later (one iteration per slab
+// width with no column active, so every kernel returns at once, and a ranking
+// with K = 0): the first launch of a kernel loads its module, which would
+// otherwise stall the first steps that need it; the ranking also reserves its
+// workspace at the lane's size here.
+static int lane_warm(hd_server* s, Lane& L) {
+    hd_ctx* ctx = s->ctx;
+    Engine& E = L.E;
+    for (int c : {4, 8, 16, 32, 64, 128}) {
+        if (c > L.S_full || E.Bp % c) continue;
+        E.vl = vec_launch(ctx, E.n, E.Bp, c);
+        int rc = engine_iteration(E, nullptr, nullptr);
+        if (rc) return rc;
+    }
+    E.vl = vec_launch(ctx, E.n, E.Bp, L.S_full);
+    std::vector<int32_t> K0(E.Bp, 0);
+    return hd_rank_impl(ctx, E.X, E.n, E.Bp, E.Bp, K0.data(), s->Kmax, 0, L.d_idx, L.d_sc);
+}
+
+extern "C" {
+
+int hd_serve_open(hd_ctx* ctx, const hd_graph* g, const hd_eig* eig, int mode, float alpha, int32_t max_slots,
+                  size_t mem_budget, int32_t max_iter, int32_t Kmax, hd_server** out) {
+    if (!ctx || !g || !out || max_slots < 1 || max_slots > 256 || Kmax < 1 || Kmax > 2048 || max_iter < 1)
+        return HD_ERR_INVALID_ARG;
+    if (!(alpha >= 0.0f && alpha < 1.0f)) return hd_fail(ctx, HD_ERR_INVALID_ARG, "alpha=%g", alpha);
+    const bool lr_on = eig && eig->r > 0;
+    if (lr_on && mode != HD_MODE_PCG)
+        return hd_fail(ctx, HD_ERR_INVALID_ARG, "the server runs PCG with eigenpairs (mode %d unsupported)", mode);
+    *out = nullptr;
+    HD_CUDA(ctx, cudaSetDevice(ctx->device));
+    const int64_t n = g->n;
+    // admission by device memory: each slot holds R, P, Q, X columns and its ranking
+    const size_t per_slot = (size_t)4 * n * 4 + (size_t)Kmax * 8;
+    int32_t slots = max_slots;
+    if (mem_budget > 0) slots = (int32_t)std::min<size_t>(max_slots, mem_budget / per_slot);
+    if (slots < 1) return hd_fail(ctx, HD_ERR_OOM, "memory budget %zu below one slot (%zu bytes)", mem_budget, per_slot);
+    // the narrow lane: four more columns when the wide lane has at least eight
+    // and the budget (if any) holds them too
+    const bool narrow = slots >= 8 && (mem_budget == 0 || mem_budget / per_slot >= (size_t)slots + 4);
+    hd_server* s = new hd_server();
+    s->ctx = ctx;
+    s->g = g;
+    s->eig = eig;
+    s->Kmax = Kmax;
+    s->max_iter = max_iter;
+    int rc = lane_open(ctx, g, eig, alpha, slots, max_iter, Kmax, 0, s->lanes[0]);
+    if (!rc && narrow) rc = lane_open(ctx, g, eig, alpha, 4, max_iter, Kmax, slots, s->lanes[1]);
+    // the wide lane last: the shared workspace is reserved at its (larger) size
+    if (!rc && narrow) rc = lane_warm(s, s->lanes[1]);
+    if (!rc) rc = lane_warm(s, s->lanes[0]);
+    if (!rc) rc = hd_check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "server set-up", __FILE__, __LINE__);
+    if (rc) {
+        server_free(s);
+        return rc;
+    }
     *out = s;
     return HD_OK;
 }
 
-int hd_serve_slots(const hd_server* s) { return s ? s->slots : 0; }
+int hd_serve_slots(const hd_server* s) { return s ? s->lanes[0].slots : 0; }
 
 int hd_serve_submit(hd_server* s, int32_t nnz_y, const int32_t* idx, const float* val, float tol, int32_t K,
                     uint64_t* ticket) {
@@ -290,108 +463,24 @@ int hd_serve_submit(hd_server* s, int32_t nnz_y, const int32_t* idx, const float
 
 int hd_serve_step(hd_server* s, int32_t iters, int32_t* busy) {
     if (!s || iters < 0) return HD_ERR_INVALID_ARG;
-    hd_ctx* ctx = s->ctx;
-    Engine& E = s->E;
-    const int32_t Bp = E.Bp;
-    // ---- admission into free columns
-    s->nrec = 0;
-    int32_t off = 0;
-    for (int j = 0; j < s->slots && !s->queue.empty(); ++j) {
-        if (s->slot_req[j]) continue;
-        Req* r = s->queue.front();
-        if (off + (int32_t)r->idx.size() > s->cap_nnz) break;
-        s->queue.pop_front();
-        r->slot = j;
-        r->admit_s = now_s();
-        s->slot_req[j] = r;
-        AdmitRec& a = s->h_rec[s->nrec++];
-        a.slot = j;
-        a.off = off;
-        a.cnt = (int32_t)r->idx.size();
-        a.tol = r->tol;
-        a.bb = r->bb;
-        std::copy(r->idx.begin(), r->idx.end(), s->h_yidx + off);
-        std::copy(r->val.begin(), r->val.end(), s->h_yval + off);
-        off += a.cnt;
-    }
-    if (s->nrec) {
-        HD_CUDA(ctx, cudaMemcpyAsync(s->d_rec, s->h_rec, s->nrec * sizeof(AdmitRec), cudaMemcpyHostToDevice, ctx->stream));
-        HD_CUDA(ctx, cudaMemcpyAsync(s->d_yidx, s->h_yidx, (size_t)off * 4, cudaMemcpyHostToDevice, ctx->stream));
-        HD_CUDA(ctx, cudaMemcpyAsync(s->d_yval, s->h_yval, (size_t)off * 4, cudaMemcpyHostToDevice, ctx->stream));
-        k_admit_mark<<<ceil_div(s->nrec, 64), 64, 0, ctx->stream>>>(s->d_rec, s->nrec, E.st, E.num_active);
-        HD_CHECK_LAUNCH(ctx);
-        if (iters < 1) iters = 1;  // the admission completes inside the next iteration
-    }
-    bool running = s->nrec > 0;
-    for (int j = 0; j < s->slots && !running; ++j) running = s->slot_req[j] != nullptr;
-    // the tensor-core products skip the columns above the highest occupied slot
-    // (admission fills the lowest free slots); per-column arithmetic is unchanged
-    int32_t live = 0;
-    for (int j = 0; j < s->slots; ++j)
-        if (s->slot_req[j]) live = j + 1;
-    E.lr.live = live;
-    // the narrowest slab that holds every occupied column (at most the width
-    // measured for the full batch): a lightly loaded server gathers less per
-    // SpMM row.  Results do not depend on it: the reductions are chunked by
-    // rows, and every slab width sums a row's entries in the same order.
-    int S = s->S_full;
-    for (int c : {4, 8, 16, 32, 64, 128})
-        if (c >= live && c <= s->S_full && Bp % c == 0) {
-            S = c;
-            break;
-        }
-    if (S != E.vl.S) E.vl = vec_launch(ctx, E.n, Bp, S);
-    // ---- iterations of every column
-    for (int t = 0; t < iters && running; ++t) {
-        int rc = engine_iteration(E, admit_cb, s);
+    Lane& W = s->lanes[0];
+    Lane& N = s->lanes[1];
+    int32_t it[2] = {iters, iters};
+    // admission: a lightly loaded server uses the narrow lane
+    if (!s->queue.empty()) {
+        const bool narrow = N.slots > 0 && !W.running() && (int32_t)s->queue.size() <= N.free_slots();
+        int rc = narrow ? lane_admit(s, N, it[1]) : lane_admit(s, W, it[0]);
         if (rc) return rc;
     }
-    // ---- poll and retire
-    if (running) {
-        HD_CUDA(ctx, cudaMemcpyAsync(s->h_st, E.st, Bp * sizeof(ColState), cudaMemcpyDeviceToHost, ctx->stream));
-        HD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-        std::vector<int32_t> Kc(Bp, 0);
-        std::vector<int> fin;
-        for (int j = 0; j < s->slots; ++j) {
-            Req* r = s->slot_req[j];
-            if (r && !s->h_st[j].active && !s->h_st[j].fresh) {
-                Kc[j] = r->K;
-                fin.push_back(j);
-            }
-        }
-        if (!fin.empty()) {
-            int rc;
-            {
-                HD_PROF(ctx, "rank");
-                rc = hd_rank_impl(ctx, E.X, E.n, Bp, Bp, Kc.data(), s->Kmax, 0, s->d_idx, s->d_sc);
-            }
-            if (rc) return rc;
-            for (int j : fin) {
-                HD_CUDA(ctx, cudaMemcpyAsync(s->h_idx + (size_t)j * s->Kmax, s->d_idx + (size_t)j * s->Kmax,
-                                             (size_t)s->Kmax * 4, cudaMemcpyDeviceToHost, ctx->stream));
-                HD_CUDA(ctx, cudaMemcpyAsync(s->h_sc + (size_t)j * s->Kmax, s->d_sc + (size_t)j * s->Kmax,
-                                             (size_t)s->Kmax * 4, cudaMemcpyDeviceToHost, ctx->stream));
-            }
-            HD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-            const double t_done = now_s();
-            for (int j : fin) {
-                Req* r = s->slot_req[j];
-                const ColState& c = s->h_st[j];
-                r->iters = c.iters;
-                r->status = c.status;
-                r->relres = c.bb > 0 ? (float)std::sqrt(c.rr / c.bb) : 0.f;
-                r->out_idx.assign(s->h_idx + (size_t)j * s->Kmax, s->h_idx + (size_t)j * s->Kmax + r->K);
-                r->out_score.assign(s->h_sc + (size_t)j * s->Kmax, s->h_sc + (size_t)j * s->Kmax + r->K);
-                r->done_s = t_done;
-                r->done = true;
-                s->finished.push_back(r->ticket);
-                s->slot_req[j] = nullptr;
-            }
-        }
+    for (int l = 0; l < 2; ++l) {
+        if (s->lanes[l].slots == 0) continue;
+        int rc = lane_step(s, s->lanes[l], it[l]);
+        if (rc) return rc;
     }
     if (busy) {
         int32_t b = (int32_t)s->queue.size();
-        for (int j = 0; j < s->slots; ++j) b += s->slot_req[j] != nullptr;
+        for (const Lane& L : s->lanes)
+            for (Req* r : L.slot_req) b += r != nullptr;
         *busy = b;
     }
     return HD_OK;

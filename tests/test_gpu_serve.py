@@ -136,3 +136,22 @@ def test_completed_reports_each_ticket_once(gpu_ctx, served):
         ids, sc, st = srv.poll(t, 20)
         assert st["status"] == 0 and len(ids) == 20
     srv.close()
+
+
+def test_narrow_and_wide_lanes_agree(gpu_ctx, served):
+    # one request alone runs in the narrow lane (slots >= 12 here), the same
+    # request submitted with a crowd runs in the wide lane: same bits
+    import paper_1807_08692_gb300 as hd
+    g, eig, reqs = served
+    srv = hd.Server(gpu_ctx, g, eig, "pcg", 0.99, max_slots=12, max_iter=500, Kmax=50)
+    q_idx, q_val = reqs[5]
+    alone = _run(srv, [(0, q_idx, q_val, 1e-6, 50)], iters=1)[0]
+    assert alone[2]["slot"] >= 12  # narrow lane
+    crowd = [(0, i, v, 1e-4, 20) for i, v in reqs[10:20]] + [(0, q_idx, q_val, 1e-6, 50)]
+    out = _run(srv, crowd, iters=1)
+    m = out[-1]
+    assert m[2]["slot"] < 12  # wide lane
+    assert np.array_equal(alone[0], m[0])
+    assert np.array_equal(alone[1].view(np.uint32), m[1].view(np.uint32))
+    assert alone[2]["iters"] == m[2]["iters"]
+    srv.close()
