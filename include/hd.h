@@ -271,6 +271,32 @@ int hd_filter_poly(hd_ctx* ctx, const hd_graph* g, const hd_eig* eig, int32_t B,
                    const int32_t* y_ptr, const int32_t* y_idx, const float* y_val,
                    const double* coeffs, int32_t ncoef, float* X, int32_t ldx);
 
+/* ---- checkpoints of the offline artefacts (Sec. 3, Sec. 4.1) -------------- */
+
+/* The graph W and the eigenpairs are computed once offline and reused for
+ * every query; these write them to a flat file and read them back (host
+ * paths; little-endian; the arrays exactly as stored on the device, so a
+ * loaded handle gives bit-identical results).  Files are not portable across
+ * format versions (a magic string is checked).  hd_eig_save rejects
+ * sparsified eigenpairs (sparsify again after loading).  Loading checks the
+ * CSR structure like hd_graph_from_csr.  Errors: HD_ERR_INVALID_ARG (file
+ * missing, short or not a checkpoint), HD_ERR_OOM. */
+int hd_graph_save(hd_ctx* ctx, const hd_graph* g, const char* path);
+int hd_graph_load(hd_ctx* ctx, const char* path, hd_graph** out);
+int hd_eig_save(hd_ctx* ctx, const hd_eig* e, const char* path);
+int hd_eig_load(hd_ctx* ctx, const char* path, hd_eig** out);
+
+/* ---- failure detection (no counterpart in the paper) ---------------------- */
+
+/* Self-test of the bounded waits that keep the tensor-core kernels from
+ * hanging a shared GPU: a one-warp kernel waits on a barrier that nothing
+ * completes (it must give up after limit_us microseconds, 1..1,000,000) and
+ * then on one whose abort flag another lane raises (it must give up at once).
+ * gave_up[2] (host) receives 1 for each wait that gave up.  Returns
+ * HD_ERR_TIMEOUT when both gave up, which is the expected outcome; the
+ * context stays usable. */
+int hd_selftest_wait(hd_ctx* ctx, uint32_t limit_us, int32_t* gave_up);
+
 /* ---- online query (Eq. 17-20) -------------------------------------------- */
 
 /* Solve for B ranking vectors at once (one column per query).
@@ -293,6 +319,8 @@ int hd_filter_poly(hd_ctx* ctx, const hd_graph* g, const hd_eig* eig, int32_t B,
  * hd_profile_enable on, kernels launch one by one instead).  The call is
  * therefore not itself capturable into a caller's graph.  Errors: HD_ERR_INVALID_ARG for bad
  * sizes or indices out of range (checked on the device; X is then undefined),
+ * HD_ERR_TIMEOUT if a tensor-core kernel gave up one of its bounded pipeline
+ * waits (the kernels never hang; X is then undefined),
  * HD_ERR_NOT_CONVERGED is NOT returned: per-column status says it. */
 int hd_query_batch(hd_ctx* ctx, const hd_graph* g, const hd_eig* eig, int mode, int32_t B,
                    const int32_t* y_ptr, const int32_t* y_idx, const float* y_val, float alpha,

@@ -8,5 +8,5 @@ from . import hd  # noqa: F401
 from .hd import (  # noqa: F401
     Context, Graph, Eig, HDError, build_graph, graph_from_csr, knn, observe, observe_regional, eig_from_host,
     eigendecompose, query_batch, rank, Server, spectrum_min, cg_bound, convergence_table,
-    filter_poly, temporal_truncated, rank_shortlists,
+    filter_poly, temporal_truncated, rank_shortlists, graph_load, eig_load, selftest_wait,
 )

@@ -273,6 +273,22 @@ int hd_graph_alloc_internal(hd_ctx* ctx, int64_t n, int64_t nnz, hd_graph** out)
 }
 void hd_graph_free_internal(hd_graph* g) { graph_free(g); }
 
+// row_ptr monotone from 0 to nnz and every column in [0, n) (checked on the device)
+int hd_graph_check(hd_ctx* ctx, const hd_graph* g) {
+    const int64_t n = g->n, nnz = g->nnz;
+    HD_CUDA(ctx, cudaMemsetAsync(ctx->d_flags, 0, sizeof(int), ctx->stream));
+    const int64_t m = n > nnz ? n : nnz;
+    k_check_csr<<<ceil_div(m, 256) > 4096 ? 4096 : ceil_div(m, 256), 256, 0, ctx->stream>>>(g->row_ptr, g->col, n,
+                                                                                        nnz, ctx->d_flags);
+    HD_CHECK_LAUNCH(ctx);
+    HD_CUDA(ctx, cudaMemcpyAsync(ctx->h_poll, ctx->d_flags, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    HD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (ctx->h_poll[0])
+        return hd_fail(ctx, HD_ERR_INVALID_ARG,
+                       ctx->h_poll[0] == 1 ? "row_ptr not monotone from 0 to nnz" : "column index out of range");
+    return HD_OK;
+}
+
 extern "C" {
 
 int hd_graph_from_csr(hd_ctx* ctx, int64_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col,

@@ -186,6 +186,8 @@ int hd_knn_impl(hd_ctx* ctx, const void* Xd, int64_t n, int32_t d, int dtype, co
 int hd_graph_from_lists(hd_ctx* ctx, int64_t n, int32_t k, const int32_t* idx_d, const float* sim_d,
                         float gamma, int sym, hd_graph** out);
 int hd_normalize_graph(hd_ctx* ctx, hd_graph* g);
+int hd_graph_alloc_internal(hd_ctx* ctx, int64_t n, int64_t nnz, hd_graph** out);
+int hd_graph_check(hd_ctx* ctx, const hd_graph* g);
 int hd_eig_alloc(hd_ctx* ctx, int64_t n, int32_t r, int storage, hd_eig** out);
 int hd_eig_store_from_device_f32(hd_ctx* ctx, hd_eig* e, const float* U_d, int32_t ldsrc);
 int hd_eig_sparse_export(hd_ctx* ctx, const hd_eig* e, float* dst);

@@ -721,8 +721,18 @@ int lr_tc_nchunk(hd_ctx* ctx, int64_t n) {
     return (int)std::max<int64_t>(1, std::min<int64_t>(ctx->num_sms, tiles));
 }
 
-static int check_err(hd_ctx* ctx, const char* what) {
-    (void)what;
+// The tensor-core kernels record a bounded wait that ran out (mbarrier timeout,
+// codes 11-25) in d_flags[2] (expansion) and d_flags[3] (reduction) instead of
+// hanging; callers read the flags at their next host synchronisation.
+int lr_tc_check_flags(hd_ctx* ctx) {
+    HD_CUDA(ctx, cudaMemcpyAsync(ctx->h_poll + 8, ctx->d_flags + 2, 2 * sizeof(int), cudaMemcpyDeviceToHost,
+                                 ctx->stream));
+    HD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (ctx->h_poll[8] || ctx->h_poll[9]) {
+        const int e = ctx->h_poll[8], r = ctx->h_poll[9];
+        HD_CUDA(ctx, cudaMemsetAsync(ctx->d_flags + 2, 0, 2 * sizeof(int), ctx->stream));
+        return hd_fail(ctx, HD_ERR_TIMEOUT, "tensor-core pipeline wait ran out (expansion %d, reduction %d)", e, r);
+    }
     return HD_OK;
 }
 
@@ -784,7 +794,7 @@ int lr_tc_expand(hd_ctx* ctx, const LowRank& lr, int op, float* out, const float
             k_lr_expand_tc<0><<<grid, THREADS, smem, ctx->stream>>>(tu, th, tl, a, ctx->d_flags + 2);
         HD_CHECK_LAUNCH(ctx);
     }
-    return check_err(ctx, "expand");
+    return HD_OK;
 }
 
 int lr_tc_reduce(hd_ctx* ctx, const LowRank& lr, const float* V, int64_t n, int32_t Bp, const int* gate) {
@@ -844,4 +854,39 @@ int lr_tc_reduce(hd_ctx* ctx, const LowRank& lr, const float* V, int64_t n, int3
         HD_CHECK_LAUNCH(ctx);
     }
     return HD_OK;
+}
+
+// ------------------------------------------------------------------ bounded-wait self-test
+// One warp: lane 0 waits on an mbarrier that nothing completes (it must give
+// up after limit_ns), then on a second one while lane 1 raises the abort flag
+// (it must give up at once).  out[0] / out[1]: 1 when each wait gave up.
+__global__ void k_wait_selftest(uint64_t limit_ns, int* out) {
+    __shared__ uint64_t bar[2];
+    __shared__ int abort_flag;
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&bar[0], 1);
+        tc::mbar_init(&bar[1], 1);
+        abort_flag = 0;
+        tc::fence_barrier_init();
+    }
+    __syncwarp();
+    if (threadIdx.x == 0) out[0] = tc::mbar_wait(&bar[0], 0, nullptr, limit_ns) ? 0 : 1;
+    __syncwarp();
+    if (threadIdx.x == 1) *(volatile int*)&abort_flag = 1;
+    __syncwarp();
+    if (threadIdx.x == 0) out[1] = tc::mbar_wait(&bar[1], 0, (volatile int*)&abort_flag, 1000000000ull) ? 0 : 1;
+}
+
+extern "C" int hd_selftest_wait(hd_ctx* ctx, uint32_t limit_us, int32_t* gave_up) {
+    if (!ctx || !gave_up || limit_us == 0 || limit_us > 1000000) return HD_ERR_INVALID_ARG;
+    HD_CUDA(ctx, cudaSetDevice(ctx->device));
+    HD_CUDA(ctx, cudaMemsetAsync(ctx->d_flags + 4, 0, 2 * sizeof(int), ctx->stream));
+    k_wait_selftest<<<1, 32, 0, ctx->stream>>>((uint64_t)limit_us * 1000ull, ctx->d_flags + 4);
+    HD_CHECK_LAUNCH(ctx);
+    HD_CUDA(ctx, cudaMemcpyAsync(ctx->h_poll + 12, ctx->d_flags + 4, 2 * sizeof(int), cudaMemcpyDeviceToHost,
+                                 ctx->stream));
+    HD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    gave_up[0] = ctx->h_poll[12];
+    gave_up[1] = ctx->h_poll[13];
+    return (gave_up[0] && gave_up[1]) ? HD_ERR_TIMEOUT : HD_OK;
 }

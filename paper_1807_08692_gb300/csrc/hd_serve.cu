@@ -323,6 +323,10 @@ static int lane_step(hd_server* s, Lane& L, int32_t iters) {
     // ---- poll and retire
     HD_CUDA(ctx, cudaMemcpyAsync(L.h_st, E.st, Bp * sizeof(ColState), cudaMemcpyDeviceToHost, ctx->stream));
     HD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (E.has_lr && lr_use_tensor_cores(E.lr.e)) {
+        const int frc = lr_tc_check_flags(ctx);
+        if (frc) return frc;
+    }
     std::vector<int32_t> Kc(Bp, 0);
     std::vector<int> fin;
     for (int j = 0; j < L.slots; ++j) {

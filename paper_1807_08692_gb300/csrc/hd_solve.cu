@@ -1374,8 +1374,12 @@ int hd_query_impl(hd_ctx* ctx, const hd_graph* g, const TruncSys* ts, const hd_e
         }
         it += todo;
         HD_CUDA(ctx, cudaMemcpyAsync(ctx->h_poll, S_.num_active, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+        // the tensor-core kernels' wait flags ride along with the poll
+        HD_CUDA(ctx, cudaMemcpyAsync(ctx->h_poll + 8, ctx->d_flags + 2, 2 * sizeof(int), cudaMemcpyDeviceToHost,
+                                     ctx->stream));
         HD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
         active = ctx->h_poll[0];
+        if (ctx->h_poll[8] || ctx->h_poll[9]) return lr_tc_check_flags(ctx);
     }
 
     // ---------------- outputs
@@ -1450,6 +1454,7 @@ extern "C" int hd_eig_project(hd_ctx* ctx, const hd_eig* e, const float* V, int3
     cudaMemcpyKind kind = hd_is_device_ptr(C_out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     HD_CUDA(ctx, cudaMemcpyAsync(C_out, lr.C, (size_t)e->r * B * 8, kind, ctx->stream));
     HD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (lr_use_tensor_cores(e) && (rc = lr_tc_check_flags(ctx))) return rc;
     return HD_OK;
 }
 
@@ -1481,6 +1486,7 @@ extern "C" int hd_eig_expand(hd_ctx* ctx, const hd_eig* e, const double* H, int3
     if ((rc = lr_finish(ctx, lr, B, ones))) return rc;
     if ((rc = lr_expand(ctx, lr, EXP_SET_X, X_out, nullptr, nullptr, e->n, B, nullptr))) return rc;
     HD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (lr_use_tensor_cores(e) && (rc = lr_tc_check_flags(ctx))) return rc;
     return HD_OK;
 }
 
@@ -1596,5 +1602,6 @@ extern "C" int hd_filter_poly(hd_ctx* ctx, const hd_graph* g, const hd_eig* eig,
                                        cudaMemcpyDeviceToHost, ctx->stream));
     }
     HD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (lr_on && lr_use_tensor_cores(eig) && (rc = lr_tc_check_flags(ctx))) return rc;
     return HD_OK;
 }

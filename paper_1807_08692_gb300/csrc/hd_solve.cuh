@@ -48,6 +48,9 @@ int lr_finish(hd_ctx* ctx, const LowRank& lr, int32_t Bp, const double* coef);
 int lr_expand(hd_ctx* ctx, const LowRank& lr, int op, float* out, const float* Rv, const float* Pv, int64_t n,
               int32_t Bp, const ColState* st, const int* gate = nullptr);
 bool lr_use_tensor_cores(const hd_eig* e);
+// HD_ERR_TIMEOUT (flags cleared) if a tensor-core kernel gave up a bounded wait
+// since the last check; synchronises the context's stream
+int lr_tc_check_flags(hd_ctx* ctx);
 // partial-sum chunks of the reduction for this embedding and batch width
 int lr_nchunk(hd_ctx* ctx, const hd_eig* e, int32_t Bp);
 int lr_sparse_nchunk(hd_ctx* ctx, const hd_eig* e);

@@ -58,6 +58,11 @@ _SIGS = {
     "hd_eig_info": (C.c_int, [vp, C.POINTER(i32), C.POINTER(C.c_int)]),
     "hd_eig_sparsify": (C.c_int, [vp, vp, f64, C.POINTER(vp)]),
     "hd_filter_poly": (C.c_int, [vp, vp, vp, i32, vp, vp, vp, vp, i32, vp, i32]),
+    "hd_selftest_wait": (C.c_int, [vp, C.c_uint32, vp]),
+    "hd_graph_save": (C.c_int, [vp, vp, C.c_char_p]),
+    "hd_graph_load": (C.c_int, [vp, C.c_char_p, C.POINTER(vp)]),
+    "hd_eig_save": (C.c_int, [vp, vp, C.c_char_p]),
+    "hd_eig_load": (C.c_int, [vp, C.c_char_p, C.POINTER(vp)]),
     "hd_temporal_truncated": (C.c_int, [vp, vp, i32, vp, vp, vp, vp, vp, f32, vp, i32, vp, i32, vp, vp, vp]),
     "hd_eig_nnz": (C.c_int, [vp, C.POINTER(C.c_int64)]),
     "hd_eig_export": (C.c_int, [vp, vp, vp, vp]),
@@ -189,6 +194,10 @@ class Graph:
     def handle(self):
         return self._h
 
+    def save(self, path: str):
+        """Write the graph to a checkpoint file (hd_graph_save)."""
+        self.ctx.check(lib().hd_graph_save(self.ctx.handle, self._h, str(path).encode()), "hd_graph_save")
+
     def tuning(self, B: int):
         """(slab, segments) the SpMM measured for batch width B, or None before any solve at that width."""
         sl, sg = i32(), i32()
@@ -235,6 +244,10 @@ class Eig:
         v = C.c_int64()
         lib().hd_eig_nnz(self._h, C.byref(v))
         return v.value
+
+    def save(self, path: str):
+        """Write the eigenpairs to a checkpoint file (hd_eig_save)."""
+        self.ctx.check(lib().hd_eig_save(self.ctx.handle, self._h, str(path).encode()), "hd_eig_save")
 
     def sparsify(self, sparsity: float) -> "Eig":
         """SHybrid (Sec. 5.3): a new handle keeping the largest-magnitude
@@ -321,6 +334,32 @@ def observe(ctx: Context, X, Q, k_y: int, gamma: float = 3.0):
                                _ptr(idx), _ptr(val)), "hd_observe")
     m = int(ptr[-1])
     return ptr, idx[:m].copy(), val[:m].copy()
+
+
+def graph_load(ctx: Context, path: str) -> "Graph":
+    """A graph from a checkpoint written by Graph.save."""
+    h = vp()
+    ctx.check(lib().hd_graph_load(ctx.handle, str(path).encode(), C.byref(h)), "hd_graph_load")
+    return Graph(ctx, h)
+
+
+def eig_load(ctx: Context, path: str) -> "Eig":
+    """Eigenpairs from a checkpoint written by Eig.save."""
+    h = vp()
+    ctx.check(lib().hd_eig_load(ctx.handle, str(path).encode(), C.byref(h)), "hd_eig_load")
+    with open(path, "rb") as f:
+        f.seek(8)
+        n = int(np.frombuffer(f.read(8), np.int64)[0])
+    return Eig(ctx, h, n)
+
+
+def selftest_wait(ctx: Context, limit_us: int = 20000):
+    """(gave_up_on_timeout, gave_up_on_abort) of the bounded-wait self-test."""
+    g = np.zeros(2, np.int32)
+    rc = lib().hd_selftest_wait(ctx.handle, limit_us, _ptr(g))
+    if rc not in (OK, ERR_TIMEOUT):
+        ctx.check(rc, "hd_selftest_wait")
+    return bool(g[0]), bool(g[1])
 
 
 def observe_regional(ctx: Context, X, Q, regions: int, k_y: int, gamma: float = 3.0):
