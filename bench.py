@@ -145,12 +145,12 @@ def build_workload(args, ctx, rank):
     nq = 2 * bmax
     if R > 1:
         # query images drawn like the database's (own seed), one observation per image
-        Qv, _ = synth.regional_database(c.seed + 7000 + 1000 * rank, nq, R, d, c.ncl, c.kappa_lo, c.kappa_hi,
+        Qv, _ = synth.regional_database(query_seed(c.seed + 7000, rank), nq, R, d, c.ncl, c.kappa_lo, c.kappa_hi,
                                         c.extra.get("p_stay", 0.8))
         Qt = torch.from_numpy(Qv).to(Xt.dtype).cuda()
         yp, yi, yv = hd.observe_regional(ctx, Xt, Qt, R, c.k_y, c.gamma)
     else:
-        Qv = synth.queries(c.seed + 1000 * rank, nq, d, c.ncl, c.kappa_lo, c.kappa_hi, c.sizes, c.zipf_s)
+        Qv = synth.queries(query_seed(c.seed, rank), nq, d, c.ncl, c.kappa_lo, c.kappa_hi, c.sizes, c.zipf_s)
         Qt = torch.from_numpy(Qv).to(Xt.dtype).cuda()
         yp, yi, yv = hd.observe(ctx, Xt, Qt, c.k_y, c.gamma)
     yall = (yp, yi, yv)
@@ -536,6 +536,31 @@ def serve_leg(ctx, wl, eig, args, rates, alpha):
     return out
 
 
+# ------------------------------------------------------------------ replicas
+def max_over_ranks(value: float) -> float:
+    """The largest value over the ranks (the slowest replica's time); the
+    value itself without a process group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(world: int, batch: int, steps: int, slowest_s: float) -> float:
+    """Whole-job queries/s of `world` replicas that each ran `steps` batches of
+    `batch` queries, timed by the slowest replica."""
+    return world * batch * steps / slowest_s
+
+
+def query_seed(cfg_seed: int, rank: int) -> int:
+    """Each replica draws its own query stream (the stream shards by query)."""
+    return cfg_seed + 1000 * rank
+
+
 # ------------------------------------------------------------------ main
 def main():
     args = parse()
@@ -572,18 +597,15 @@ def main():
     hyb = time_leg(ctx, wl, eig, args.mode, tol_h, alpha, args.steps, args.warmup, B, args.topk, False)
     t_wall = time.perf_counter() - t_wall0
     clocks = clk.stop()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    total_s = max_over_ranks(hyb["total_ms"] / 1e3)
+    qps = replica_throughput(world, B, args.steps, total_s)
     # per-kernel event timing for the roofline in a separate pass: profiling
     # brackets every launch with events, so it runs without the CUDA graphs
     prof_steps = min(args.steps, 10)
     hprof = time_leg(ctx, wl, eig, args.mode, tol_h, alpha, prof_steps, 1, B, args.topk, True)
-    if world > 1:
-        torch.distributed.barrier()
-    total_s = hyb["total_ms"] / 1e3
-    if world > 1:
-        t = torch.tensor([total_s], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_s = t.item()
-    qps = world * B * args.steps / total_s
     # ---- r = 0 pure CG leg
     cg = None
     if not args.quick:
@@ -636,8 +658,12 @@ def main():
     nnz = wl["g"].nnz
     gather = nnz * ((B + 3) // 4 * 4) * 4 + 8 * nnz + 4 * (wl["n"] + 1) + 2 * wl["n"] * ((B + 3) // 4 * 4) * 4
     spmm_ms = fam["spmm"][1] / max(fam["spmm"][2], 1)
+    traffic = spmm_traffic(wl, B) if dom == "spmm" else None
     roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": spmm_traffic(wl, B) if dom == "spmm" else None,
+                "frac": round(achieved / peak, 4), "traffic": traffic,
+                # the same launch measured by its DRAM bytes (random gathers re-read rows; see profiles/)
+                "dram_gbs": round(traffic / avg_s / 1e9, 1) if traffic else None,
+                "dram_frac": round(traffic / avg_s / 1e9 / peak, 4) if traffic else None,
                 "spmm_gather_bytes_per_launch": int(gather),
                 "spmm_gather_gbs": round(gather / (spmm_ms / 1e3) / 1e9, 1) if spmm_ms > 0 else None,
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",

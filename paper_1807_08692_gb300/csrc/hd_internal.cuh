@@ -104,6 +104,14 @@ struct hd_eig {
 
 // ---------------------------------------------------------------- errors
 int hd_fail(hd_ctx* ctx, int code, const char* fmt, ...);
+// True the first time it is called for `device` with this flag word (function
+// attributes such as the dynamic shared-memory limit are set per device).
+inline bool hd_first_on_device(uint64_t& mask, int device) {
+    const uint64_t b = 1ull << (device & 63);
+    if (mask & b) return false;
+    mask |= b;
+    return true;
+}
 #define HD_CUDA(ctx, call)                                                            \
     do {                                                                              \
         cudaError_t e_ = (call);                                                      \

@@ -351,10 +351,9 @@ int hd_knn_impl(hd_ctx* ctx, const void* Xd, int64_t n, int32_t d, int dtype, co
     CUtensorMap tq, tx;
     if (hd_make_tmap_2d(&tq, Qd, 2, nq, d, d, BM, BK, 1) || hd_make_tmap_2d(&tx, Xd, 2, n, d, d, BN, BK, 1))
         return hd_fail(ctx, HD_ERR_CUDA, "cuTensorMapEncodeTiled failed");
-    static bool attr = false;
-    if (!attr) {
+    static uint64_t attr = 0;
+    if (hd_first_on_device(attr, ctx->device)) {
         HD_CUDA(ctx, cudaFuncSetAttribute(k_knn_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-        attr = true;
     }
     int nwork = ceil_div(nq, BM);
     int grid = nwork < ctx->num_sms ? nwork : ctx->num_sms;

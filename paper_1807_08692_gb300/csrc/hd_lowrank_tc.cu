@@ -757,11 +757,10 @@ int lr_tc_expand(hd_ctx* ctx, const LowRank& lr, int op, float* out, const float
     while (Nc > 16 && (apipe + STAGE_BYTES + 2 * nkb_b * Nc * 128 > max_smem || Nc > 256)) Nc = (Nc / 2 + 15) / 16 * 16;
     if (apipe + STAGE_BYTES + 2 * nkb_b * Nc * 128 > max_smem)
         return hd_fail(ctx, HD_ERR_INVALID_ARG, "rank %d too large for the tensor-core expansion", e->r);
-    static bool attr[2] = {false, false};
-    if (!attr[su]) {
+    static uint64_t attr[2] = {0, 0};
+    if (hd_first_on_device(attr[su], ctx->device)) {
         HD_CUDA(ctx, cudaFuncSetAttribute(su ? k_lr_expand_tc<1> : k_lr_expand_tc<0>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-        attr[su] = true;
     }
     for (int c0 = 0; c0 < cols; c0 += Nc) {
         const int nc = std::min(Nc, cols - c0);
@@ -818,11 +817,10 @@ int lr_tc_reduce(hd_ctx* ctx, const LowRank& lr, const float* V, int64_t n, int3
     while (Nc > 64 && (smem_of(Nc) > (size_t)max_smem || mt * Nc > 512 || Nc > 256)) Nc -= 64;
     if (mt * Nc > 512 || smem_of(Nc) > (size_t)max_smem)
         return hd_fail(ctx, HD_ERR_INVALID_ARG, "rank %d too large for the tensor-core reduction", e->r);
-    static bool attr[2] = {false, false};
-    if (!attr[su]) {
+    static uint64_t attr[2] = {0, 0};
+    if (hd_first_on_device(attr[su], ctx->device)) {
         HD_CUDA(ctx, cudaFuncSetAttribute(su ? k_lr_reduce_tc<1> : k_lr_reduce_tc<0>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-        attr[su] = true;
     }
     const int64_t tiles = (n + BM - 1) / BM;
     const int grid = lr.nchunk;

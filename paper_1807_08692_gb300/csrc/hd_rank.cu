@@ -301,10 +301,9 @@ int hd_rank_impl(hd_ctx* ctx, const float* Xd, int64_t n, int32_t B, int32_t ldx
         ld = B;
     }
     HD_CUDA(ctx, cudaMemcpyAsync(Kd, K_h, B * 4, cudaMemcpyHostToDevice, ctx->stream));
-    static bool attr = false;
-    if (!attr) {
+    static uint64_t attr = 0;
+    if (hd_first_on_device(attr, ctx->device)) {
         HD_CUDA(ctx, cudaFuncSetAttribute(k_topk_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, TK_CAP * 8));
-        attr = true;
     }
     k_topk_sample<<<B, 1024, 0, ctx->stream>>>(src, m, ld, Kd, tau, cnt);
     HD_CHECK_LAUNCH(ctx);
@@ -339,10 +338,9 @@ static int radix_rank(hd_ctx* ctx, const float* src, int64_t m, int32_t B, int32
     HD_CUDA(ctx, cudaMemsetAsync(hist, 0, (size_t)B * 256 * 4, ctx->stream));
     k_sel_init<<<ceil_div(B, 128), 128, 0, ctx->stream>>>(st, Kd, B, m);
     HD_CHECK_LAUNCH(ctx);
-    static bool attr = false;
-    if (!attr) {
+    static uint64_t attr = 0;
+    if (hd_first_on_device(attr, ctx->device)) {
         HD_CUDA(ctx, cudaFuncSetAttribute(k_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, CG * 256 * 4));
-        attr = true;
     }
     const int gy = ceil_div(B, CG);
     const int gx = std::max(1, std::min<int>(ceil_div(m * std::min(B, CG), 256), ctx->num_sms * 4 / gy + 1));

@@ -777,12 +777,11 @@ int lr_expand(hd_ctx* ctx, const LowRank& lr, int op, float* out, const float* R
     size_t smem = (size_t)e->r * 16 * sizeof(float);
     int gx = (int)std::min<int64_t>(ceil_div(n, 64), (int64_t)ctx->num_sms * 8);
     dim3 grid(gx, ceil_div(Bp, 16));
-    static bool attr = false;
-    if (!attr) {
+    static uint64_t attr = 0;
+    if (hd_first_on_device(attr, ctx->device)) {
         cudaFuncSetAttribute(k_lr_expand_simt<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024 + 1024);
         cudaFuncSetAttribute(k_lr_expand_simt<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024 + 1024);
         cudaFuncSetAttribute(k_lr_expand_simt<__nv_fp8_e4m3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024 + 1024);
-        attr = true;
     }
     if (e->storage == HD_F32)
         k_lr_expand_simt<float><<<grid, 256, smem, ctx->stream>>>((const float*)e->U, e->scale, e->ldu, e->r, lr.H, op,
