@@ -286,7 +286,7 @@ def e2e_leg(ctx, wl, eig, mode, tol, alpha, K, B, topk):
 
 
 # DRAM bytes per launch of the SpMM measured by ncu (profiles/spmm_n1m_b64.md):
-# k_spmm<64> on a 1M-node k=50 graph (d=256 descriptors, nnz 62,097,728), B=64.
+# k_spmm<32> on a 1M-node k=50 graph (d=256 descriptors, nnz 62,097,728), B=64.
 # Scaled to another graph by nnz (the gathered rows dominate); reported only
 # while the kernel source still hashes to the value the counters were taken on.
 SPMM_NCU = {"dram_bytes": 8560559360, "nnz": 62097728, "n": 1000000, "B": 64, "slab": 32,

@@ -404,6 +404,8 @@ int hd_serve_poll(hd_server* s, uint64_t ticket, int32_t* idx_out, float* score_
  * many requests in flight poll only the finished ones.  *count receives the
  * number written to tickets[] (host). */
 int hd_serve_completed(hd_server* s, uint64_t* tickets, int32_t max_tickets, int32_t* count);
+/* Frees the server's buffers.  A server uses its context until it is closed:
+ * close every server before hd_destroy of its context. */
 int hd_serve_close(hd_server* s);
 
 #ifdef __cplusplus

@@ -9,6 +9,7 @@ from __future__ import annotations
 
 import ctypes as C
 import os
+import weakref
 
 import numpy as np
 
@@ -109,6 +110,16 @@ def exported_symbols():
     return [n for n in _SIGS if hasattr(lib(), n)]
 
 
+def _typed(x, np_dtype, torch_name: str):
+    """numpy input as a contiguous array of np_dtype; a tensor must already have
+    that element type (it is passed by pointer)."""
+    if x is None or isinstance(x, np.ndarray) or isinstance(x, (list, tuple)):
+        return None if x is None else np.ascontiguousarray(x, np_dtype)
+    if hasattr(x, "dtype") and str(x.dtype) != f"torch.{torch_name}":
+        raise TypeError(f"expected a {torch_name} tensor, got {x.dtype}")
+    return x
+
+
 def _ptr(x):
     """Pointer of a torch tensor, a numpy array or None."""
     if x is None:
@@ -142,6 +153,8 @@ class Context:
         if rc != OK:
             raise HDError(rc, "hd_create failed")
         self.device = device
+        # servers keep a pointer to the context: they are closed before it
+        self._servers = weakref.WeakSet()
 
     @property
     def handle(self):
@@ -173,6 +186,8 @@ class Context:
 
     def close(self):
         if self._h:
+            for s in list(self._servers):
+                s.close()
             lib().hd_destroy(self._h)
             self._h = vp()
 
@@ -453,6 +468,9 @@ def query_batch(ctx: Context, g: Graph, eig, mode, y_ptr, y_idx, y_val, alpha: f
     """
     import torch
     B = len(y_ptr) - 1
+    y_ptr = _typed(y_ptr, np.int32, "int32")
+    y_idx = _typed(y_idx, np.int32, "int32")
+    y_val = _typed(y_val, np.float32, "float32")
     if isinstance(mode, str):
         mode = MODES[mode]
     if np.isscalar(tol):
@@ -544,6 +562,7 @@ class Server:
         m = MODES[mode] if isinstance(mode, str) else mode
         ctx.check(lib().hd_serve_open(ctx.handle, g.handle, eig.handle if eig is not None else None, m, alpha,
                                       max_slots, mem_budget, max_iter, Kmax, C.byref(self._h)), "hd_serve_open")
+        ctx._servers.add(self)
         self.slots = int(lib().hd_serve_slots(self._h))
 
     def submit(self, idx, val, tol: float, K: int) -> int:

@@ -155,3 +155,28 @@ def test_narrow_and_wide_lanes_agree(gpu_ctx, served):
     assert np.array_equal(alone[1].view(np.uint32), m[1].view(np.uint32))
     assert alone[2]["iters"] == m[2]["iters"]
     srv.close()
+
+
+def test_served_request_equals_batch_solve(gpu_ctx, served):
+    # a request alone takes one admission iteration (its column is reset, y is
+    # scattered in and z0 = M^-1 y formed) and then the batch solver's PCG
+    # iterations for the same y, with the same ranking
+    import paper_1807_08692_gb300 as hd
+    g, eig, reqs = served
+    srv = hd.Server(gpu_ctx, g, eig, "pcg", 0.99, max_slots=8, max_iter=500, Kmax=20)
+    for q in (7, 8):
+        i, v = reqs[q]
+        t = srv.submit(i, v, 1e-6, 20)
+        steps, res = 0, None
+        while res is None and steps < 100:
+            srv.step(1)
+            steps += 1
+            res = srv.poll(t, 20)
+        assert res is not None and res[2]["status"] == 0
+        assert steps == res[2]["iters"] + 1
+        X, it, rr, st = hd.query_batch(gpu_ctx, g, eig, "pcg", np.array([0, len(i)], np.int32), i, v, 0.99, 1e-6, 500)
+        assert st[0] == 0 and abs(int(it[0]) - res[2]["iters"]) <= 1
+        x = X[:, 0].cpu().numpy().astype(np.float64)
+        ref, _ = ORank.topk(x, 20)
+        assert ORank.ranks_match(res[0], ref, x, 1e-5 * x.max())
+    srv.close()
