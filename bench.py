@@ -327,6 +327,7 @@ def algorithmic_bytes(wl, B, eig):
         "direction": 3 * vec,                           # read R, P; write P
         "lr_reduce": ub + vec,                          # U and R once
         "lr_expand": ub + 3 * vec,                      # U, R, P; write P
+        "rank": vec,                                    # X once (top-K)
     }
 
 
@@ -664,6 +665,9 @@ def main():
     gather = nnz * ((B + 3) // 4 * 4) * 4 + 8 * nnz + 4 * (wl["n"] + 1) + 2 * wl["n"] * ((B + 3) // 4 * 4) * 4
     spmm_ms = fam["spmm"][1] / max(fam["spmm"][2], 1)
     traffic = spmm_traffic(wl, B) if dom == "spmm" else None
+    # the whole step: every family's algorithmic bytes over its launches that did work
+    path_bytes = sum(ab[f] * fam[f][2] for f in fam if f in ab) / prof_steps
+    path_gbs = path_bytes / (hprof["total_ms"] / prof_steps / 1e3) / 1e9
     roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
                 # the same launch measured by its DRAM bytes (random gathers re-read rows; see profiles/)
@@ -674,6 +678,8 @@ def main():
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
                 "algorithmic_bytes_per_launch": int(ab[dom]), "avg_launch_ms": round(avg_s * 1e3, 4),
                 "share_of_step": round(ms / hprof["total_ms"], 4),
+                "path_algorithmic_bytes_per_step": int(path_bytes), "path_gbs": round(path_gbs, 1),
+                "path_frac": round(path_gbs / peak, 4),
                 "profiled_steps": prof_steps,
                 "profiled_ms_per_step": round(hprof["total_ms"] / prof_steps, 4),
                 "profiled_launches_per_step": round(hprof["launches"] / prof_steps, 1),
