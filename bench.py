@@ -665,9 +665,14 @@ def main():
     gather = nnz * ((B + 3) // 4 * 4) * 4 + 8 * nnz + 4 * (wl["n"] + 1) + 2 * wl["n"] * ((B + 3) // 4 * 4) * 4
     spmm_ms = fam["spmm"][1] / max(fam["spmm"][2], 1)
     traffic = spmm_traffic(wl, B) if dom == "spmm" else None
-    # the whole step: every family's algorithmic bytes over its launches that did work
-    path_bytes = sum(ab[f] * fam[f][2] for f in fam if f in ab) / prof_steps
-    path_gbs = path_bytes / (hprof["total_ms"] / prof_steps / 1e3) / 1e9
+    # the whole step against a fully fused design's bytes: per CG iteration W
+    # once (8 nnz), U twice (U^T P and U H) and nine n x B vector passes; once per
+    # step the spectral term (U, one vector) and the top-K (one vector)
+    s_u = {0: 4, 1: 2, 2: 1}[eig.storage] if eig is not None else 0
+    r_u = eig.r if eig is not None else 0
+    n_, vb = wl["n"], wl["n"] * B * 4
+    path_bytes = int(hyb["iters"].max()) * (8 * nnz + 2 * n_ * r_u * s_u + 9 * vb) + n_ * r_u * s_u + 2 * vb
+    path_gbs = path_bytes / (hyb["total_ms"] / args.steps / 1e3) / 1e9
     roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
                 # the same launch measured by its DRAM bytes (random gathers re-read rows; see profiles/)
