@@ -355,7 +355,7 @@ int hd_rank(hd_ctx* ctx, const float* X, int64_t n, int32_t B, int32_t ldx, cons
 int hd_rank_static(hd_ctx* ctx, const float* X, int64_t n, int32_t B, int32_t ldx,
                    const int32_t* K, int32_t Kmax, int32_t* idx_out, float* score_out);
 
-/* ---- serving: continuous batching (spec serving pattern) ---------------- */
+/* ---- serving: continuous batching (no counterpart in the paper) ------------- */
 
 typedef struct hd_req_stats {
     double submit_s;    /* host steady clock (s) at hd_serve_submit */

@@ -100,9 +100,23 @@ __global__ void __launch_bounds__(256, 8) k_spmm(const int32_t* rp, const int32_
                 FMA4(s2, w[u + 1], v[u + 1]);
             }
         }
-        for (; t < e; ++t) {
-            const float4 v0 = ld4(P + (int64_t)ci[t] * ld + col);
-            FMA4(s, wv[t], v0);
+        // the last e - t < 8 entries, four gathers issued before their
+        // multiply-adds, which still run one entry after another
+        for (; t < e; t += 4) {
+            const int m = e - t;
+            float4 v[4];
+            float w[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                w[u] = u < m ? __ldg(wv + t + u) : 0.f;
+                v[u] = u < m ? ld4(P + (int64_t)__ldg(ci + t + u) * ld + col) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (u < m) {
+                    FMA4(s, w[u], v[u]);
+                }
+            }
         }
         s.x += s2.x;
         s.y += s2.y;
