@@ -17,7 +17,8 @@
  *    device.  All input buffers stay owned by the caller and are only read
  *    during the call; output buffers are caller-provided.
  *  - Handles (hd_ctx, hd_graph, hd_eig, hd_server) are allocated by the
- *    library and released with the matching *_destroy call.
+ *    library and released with the matching *_destroy call (hd_serve_close
+ *    for a server, before hd_destroy of its context).
  *  - All device work of a context is issued on the context's stream, in
  *    order.  Calls are thread-compatible per context, not thread-safe.
  *  - Dense n x B blocks are row-major: element (i, j) at i * ld + j.
@@ -85,8 +86,9 @@ int hd_num_sms(const hd_ctx* ctx);
 /* Per-kernel device timing: while enabled, every launch of the library's
  * main kernels is bracketed by CUDA events on the context's stream.
  * hd_profile_read synchronises the stream and returns, for the kernel family
- * `name` ("spmm", "update", "direction", "lr_reduce", "lr_expand", "scalar",
- * "rank", "knn"), the number of launches and their summed duration since the
+ * `name` ("spmm", "dot", "update", "direction", "colsq", "lr_reduce",
+ * "lr_expand", "scalar", "rank", "knn", "trunc_build"), the number of
+ * launches and their summed duration since the
  * last read, then clears that family.  busy_launches (may be NULL) counts the
  * launches that took at least 5% of the family's longest one: kernels of an
  * iteration return at once when none of their columns is active, and those
