@@ -200,6 +200,13 @@ __global__ void __launch_bounds__(1024) k_topk_sample(const float* X, int64_t n,
     __shared__ uint64_t sk[TK_SAMPLE];
     const int j = blockIdx.x;
     const int64_t K = (int64_t)Kd[j] < n ? (int64_t)Kd[j] : n;
+    if (K <= 0) {  // nothing to rank in this column (the filter and the sort skip it too)
+        if (threadIdx.x == 0) {
+            tau[j] = 0xFFFFFFFFu;
+            cnt[j] = 0;
+        }
+        return;
+    }
     const int s = (int)(n < TK_SAMPLE ? n : (int64_t)TK_SAMPLE);
     for (int t = threadIdx.x; t < TK_SAMPLE; t += blockDim.x) {
         uint64_t v = 0;
