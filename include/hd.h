@@ -64,6 +64,7 @@ extern "C" {
 #define HD_COL_MAX_ITER 1
 #define HD_COL_BREAKDOWN 2       /* p^T A p <= 0 or not finite */
 #define HD_COL_EMPTY 3           /* y == 0: x = 0 after 0 iterations */
+#define HD_COL_CANCELLED 4       /* serving: withdrawn by hd_serve_cancel, no ranking */
 
 typedef struct hd_ctx hd_ctx;
 typedef struct hd_graph hd_graph;
@@ -320,7 +321,8 @@ int hd_selftest_wait(hd_ctx* ctx, uint32_t limit_us, int32_t* gave_up);
  * width, alpha and max_iter stay the same (any change re-captures it; with
  * hd_profile_enable on, kernels launch one by one instead).  The call is
  * therefore not itself capturable into a caller's graph.  Errors: HD_ERR_INVALID_ARG for bad
- * sizes or indices out of range (checked on the device; X is then undefined),
+ * sizes, indices out of range or non-finite observation values (checked on
+ * the device before any iteration; X is then undefined),
  * HD_ERR_TIMEOUT if a tensor-core kernel gave up one of its bounded pipeline
  * waits (the kernels never hang; X is then undefined),
  * HD_ERR_NOT_CONVERGED is NOT returned: per-column status says it. */
@@ -387,8 +389,8 @@ int hd_serve_open(hd_ctx* ctx, const hd_graph* g, const hd_eig* eig, int mode, f
 /* Columns of the wide persistent batch. */
 int hd_serve_slots(const hd_server* s);
 /* Queue one request: its observation (nnz_y <= 512 host entries, indices in
- * [0, n), duplicates summed), residual tolerance and K <= Kmax.  Copies the
- * arrays; returns a ticket.  Errors: HD_ERR_INVALID_ARG. */
+ * [0, n), finite values, duplicates summed), residual tolerance and K <= Kmax.
+ * Copies the arrays; returns a ticket.  Errors: HD_ERR_INVALID_ARG. */
 int hd_serve_submit(hd_server* s, int32_t nnz_y, const int32_t* idx, const float* val, float tol,
                     int32_t K, uint64_t* ticket);
 /* Admit queued requests into free columns, run `iters` CG iterations of the
@@ -398,9 +400,18 @@ int hd_serve_submit(hd_server* s, int32_t nnz_y, const int32_t* idx, const float
 int hd_serve_step(hd_server* s, int32_t iters, int32_t* busy);
 /* HD_PENDING while the request runs; then copies its K ids / scores (host)
  * and stats, forgets the ticket and returns HD_OK.  HD_ERR_NOT_FOUND for an
- * unknown ticket. */
+ * unknown ticket.  A cancelled request reports status HD_COL_CANCELLED and
+ * writes no ids or scores. */
 int hd_serve_poll(hd_server* s, uint64_t ticket, int32_t* idx_out, float* score_out,
                   hd_req_stats* st);
+/* Withdraw a request: a queued one leaves the queue, a running one frees its
+ * column at once (the column is marked inactive on the context's stream, so
+ * the batch's next iterations skip it and the column can take the next
+ * request).  The request then polls as finished with status
+ * HD_COL_CANCELLED and is reported by hd_serve_completed.  HD_OK also for a
+ * request that had already finished (its results stay); HD_ERR_NOT_FOUND for
+ * an unknown or already polled ticket. */
+int hd_serve_cancel(hd_server* s, uint64_t ticket);
 /* Tickets retired by hd_serve_step since the last call, in retirement order
  * (at most max_tickets; the rest stay for the next call): lets a caller with
  * many requests in flight poll only the finished ones.  *count receives the

@@ -71,6 +71,15 @@ __global__ void k_admit_mark(const AdmitRec* recs, int nrec, ColState* st, int* 
     atomicAdd(num_active, 1);  // admitted columns are work for this iteration's gated kernels
 }
 
+// a cancelled request's column: inactive from the next kernel on
+__global__ void k_cancel_col(ColState* st, int j) {
+    st[j].active = 0;
+    st[j].fresh = 0;
+    st[j].a = 0.0;
+    st[j].beta = 0.0;
+    st[j].status = HD_COL_CANCELLED;
+}
+
 __global__ void k_admit_scatter(const AdmitRec* recs, int nrec, const int32_t* yidx, const float* yval, float* R,
                                 int32_t ld) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -441,6 +450,10 @@ int hd_serve_submit(hd_server* s, int32_t nnz_y, const int32_t* idx, const float
             delete r;
             return hd_fail(s->ctx, HD_ERR_INVALID_ARG, "observation index %d out of range", idx[t]);
         }
+        if (!std::isfinite(val[t])) {
+            delete r;
+            return hd_fail(s->ctx, HD_ERR_INVALID_ARG, "observation value %d is not finite", t);
+        }
         e[t] = {idx[t], val[t]};
     }
     r->idx.assign(idx, idx + nnz_y);
@@ -487,6 +500,32 @@ int hd_serve_step(hd_server* s, int32_t iters, int32_t* busy) {
             for (Req* r : L.slot_req) b += r != nullptr;
         *busy = b;
     }
+    return HD_OK;
+}
+
+int hd_serve_cancel(hd_server* s, uint64_t ticket) {
+    if (!s) return HD_ERR_INVALID_ARG;
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return HD_ERR_NOT_FOUND;
+    Req* r = it->second;
+    if (r->done) return HD_OK;
+    auto q = std::find(s->queue.begin(), s->queue.end(), r);
+    if (q != s->queue.end()) {
+        s->queue.erase(q);
+    } else {
+        // running: free its column now; the column stops iterating at once
+        for (Lane& L : s->lanes)
+            for (int j = 0; j < L.slots; ++j)
+                if (L.slot_req[j] == r) {
+                    k_cancel_col<<<1, 1, 0, s->ctx->stream>>>(L.E.st, j);
+                    HD_CHECK_LAUNCH(s->ctx);
+                    L.slot_req[j] = nullptr;
+                }
+    }
+    r->status = HD_COL_CANCELLED;
+    r->done_s = now_s();
+    r->done = true;
+    s->finished.push_back(r->ticket);
     return HD_OK;
 }
 

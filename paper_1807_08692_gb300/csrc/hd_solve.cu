@@ -36,12 +36,13 @@ __global__ void k_scatter_y(const int32_t* y_ptr, const int32_t* y_idx, const fl
         return;
     }
     for (int32_t t = b; t < e; ++t) {
-        int32_t i = y_idx[t];
-        if (i < 0 || i >= n) {
+        const int32_t i = y_idx[t];
+        const float v = y_val[t];
+        if (i < 0 || i >= n || !isfinite(v)) {
             atomicExch(err, 1);
             continue;
         }
-        R[(int64_t)i * ld + j] += y_val[t];
+        R[(int64_t)i * ld + j] += v;
     }
 }
 
@@ -1375,7 +1376,8 @@ int hd_query_impl(hd_ctx* ctx, const hd_graph* g, const TruncSys* ts, const hd_e
     int it = 0;
     HD_CUDA(ctx, cudaMemcpyAsync(ctx->h_poll, S_.num_active, 2 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     HD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    if (ctx->h_poll[1]) return hd_fail(ctx, HD_ERR_INVALID_ARG, "observation index out of range or bad y_ptr");
+    if (ctx->h_poll[1])
+        return hd_fail(ctx, HD_ERR_INVALID_ARG, "bad observation: index out of range, non-finite value or bad y_ptr");
     int active = ctx->h_poll[0];
     while (active > 0 && it < max_iter) {
         const int todo = std::min(poll_every, max_iter - it);
@@ -1606,7 +1608,8 @@ extern "C" int hd_filter_poly(hd_ctx* ctx, const hd_graph* g, const hd_eig* eig,
     }
     HD_CUDA(ctx, cudaMemcpyAsync(ctx->h_poll, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     HD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    if (ctx->h_poll[0]) return hd_fail(ctx, HD_ERR_INVALID_ARG, "observation index out of range or bad y_ptr");
+    if (ctx->h_poll[0])
+        return hd_fail(ctx, HD_ERR_INVALID_ARG, "bad observation: index out of range, non-finite value or bad y_ptr");
     if (hd_is_device_ptr(X)) {
         k_copy_out<<<ceil_div(n * B, 256), 256, 0, ctx->stream>>>(acc, Bp, X, ldx, B, n);
         HD_CHECK_LAUNCH(ctx);

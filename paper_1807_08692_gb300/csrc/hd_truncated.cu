@@ -121,7 +121,7 @@ __global__ void k_ts_map_y(const int32_t* y_ptr, const int32_t* y_idx, const flo
     if (j >= B) return;
     for (int32_t q = y_ptr[j]; q < y_ptr[j + 1]; ++q) {
         const int32_t i = y_idx[q];
-        if (i < 0 || i >= n) {
+        if (i < 0 || i >= n || !isfinite(y_val[q])) {
             atomicExch(err, 3);
             y_loc[q] = 0;
             y_lv[q] = 0.0f;
@@ -320,7 +320,7 @@ extern "C" int hd_temporal_truncated(hd_ctx* ctx, const hd_graph* g, int32_t B, 
     if (!rc) {
         TS_CUDA(cudaMemcpyAsync(ctx->h_poll, err, 4, cudaMemcpyDeviceToHost, ctx->stream));
         TS_CUDA(cudaStreamSynchronize(ctx->stream));
-        if (ctx->h_poll[0]) rc = hd_fail(ctx, HD_ERR_INVALID_ARG, "observation index out of range");
+        if (ctx->h_poll[0]) rc = hd_fail(ctx, HD_ERR_INVALID_ARG, "bad observation: index out of range or non-finite value");
     }
     release();
     return rc;

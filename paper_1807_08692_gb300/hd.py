@@ -78,6 +78,7 @@ _SIGS = {
     "hd_serve_step": (C.c_int, [vp, i32, C.POINTER(i32)]),
     "hd_serve_poll": (C.c_int, [vp, u64, vp, vp, vp]),
     "hd_serve_completed": (C.c_int, [vp, vp, i32, C.POINTER(i32)]),
+    "hd_serve_cancel": (C.c_int, [vp, u64]),
     "hd_serve_close": (C.c_int, [vp]),
     "hd_eig_expand": (C.c_int, [vp, vp, vp, i32, vp]),
 }
@@ -589,6 +590,10 @@ class Server:
         self.ctx.check(rc, "hd_serve_poll")
         stats = {f: getattr(st, f) for f, _ in ReqStats._fields_}
         return ids[:K], sc[:K], stats
+
+    def cancel(self, ticket: int):
+        """Withdraw a queued or running request (it then polls with status 4, no ranking)."""
+        self.ctx.check(lib().hd_serve_cancel(self._h, ticket), "hd_serve_cancel")
 
     def completed(self, max_tickets: int = 4096):
         """Tickets retired since the last call (poll them for their results)."""

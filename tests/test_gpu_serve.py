@@ -180,3 +180,58 @@ def test_served_request_equals_batch_solve(gpu_ctx, served):
         ref, _ = ORank.topk(x, 20)
         assert ORank.ranks_match(res[0], ref, x, 1e-5 * x.max())
     srv.close()
+
+
+def test_cancel_queued_and_running_requests(gpu_ctx, served):
+    # a queued request leaves the queue, a running one frees its column at
+    # once; neither is ranked, and the others get exactly their results alone
+    import paper_1807_08692_gb300 as hd
+    g, eig, reqs = served
+    srv = hd.Server(gpu_ctx, g, eig, "pcg", 0.99, max_slots=4, max_iter=500, Kmax=20)
+    alone = _run(srv, [(0, *reqs[11], 1e-6, 20)], iters=1)[0]
+    srv.completed()                  # already polled by _run
+    t = [srv.submit(i, v, 1e-6, 20) for i, v in (reqs[11], reqs[12], reqs[13], reqs[14], reqs[15], reqs[16])]
+    srv.step(1)                      # four running (wide lane), two queued
+    srv.cancel(t[5])                 # queued
+    srv.cancel(t[1])                 # running
+    with pytest.raises(hd.HDError):
+        srv.cancel(12345)
+    done = {}
+    for _ in range(200):
+        busy = srv.step(1)
+        for tk in srv.completed():
+            done[tk] = srv.poll(tk, 20)
+        if not busy:
+            break
+    for tk in srv.completed():
+        done[tk] = srv.poll(tk, 20)
+    assert sorted(done) == sorted(t)
+    assert done[t[1]][2]["status"] == 4 and done[t[5]][2]["status"] == 4
+    for k in (0, 2, 3, 4):
+        assert done[t[k]][2]["status"] == 0
+    assert np.array_equal(done[t[0]][0], alone[0])
+    assert np.array_equal(done[t[0]][1].view(np.uint32), alone[1].view(np.uint32))
+    # the queued request that followed got the cancelled one's column
+    assert done[t[4]][2]["slot"] == done[t[1]][2]["slot"]
+    srv.close()
+
+
+def test_non_finite_observations_rejected(gpu_ctx, served):
+    import paper_1807_08692_gb300 as hd
+    g, eig, reqs = served
+    i, v = reqs[2]
+    bad = np.array(v, np.float32)
+    bad[1] = np.nan
+    srv = hd.Server(gpu_ctx, g, eig, "pcg", 0.99, max_slots=4, max_iter=500, Kmax=20)
+    with pytest.raises(hd.HDError):
+        srv.submit(i, bad, 1e-6, 20)
+    srv.close()
+    y_ptr = np.array([0, len(i)], np.int32)
+    with pytest.raises(hd.HDError):
+        hd.query_batch(gpu_ctx, g, eig, "pcg", y_ptr, i, bad, 0.99, 1e-6, 100)
+    bad[1] = np.inf
+    with pytest.raises(hd.HDError):
+        hd.query_batch(gpu_ctx, g, None, "paper", y_ptr, i, bad, 0.99, 1e-6, 100)
+    # the context stays usable
+    X, it, rr, st = hd.query_batch(gpu_ctx, g, eig, "pcg", y_ptr, i, v, 0.99, 1e-6, 500)
+    assert st[0] == 0
