@@ -12,6 +12,7 @@ import test_oracle_graph as TG
 import test_oracle_spectral as TS
 import test_oracle_truncated as TT
 from oracle import diffusion as D
+from oracle import general as GE
 from oracle import graph as G
 from oracle import observe as O
 from oracle import rank as R
@@ -95,6 +96,13 @@ def _sparsify_earlier_first(U1, sparsity):
     return out.reshape(U.shape)
 
 
+def _poly_coefficients_reversed(apply_A, coeffs, y):
+    acc = np.zeros_like(np.asarray(y, dtype=np.float64))
+    for c in list(coeffs):
+        acc = apply_A(acc) + c * y
+    return acc
+
+
 def _regional_first_region_only(Xdb, Q, regions, k_y, gamma=3.0):
     p, i, v = O.observe(Xdb, Q[::regions], k_y, gamma)
     return p, i, v
@@ -127,6 +135,8 @@ MUTANTS = [
      lambda g: TS.test_sparsify_keeps_largest_magnitudes()),
     ("regional observation from one region", O, "observe_regional", _regional_first_region_only,
      lambda g: TG.test_observe_regional_is_the_sum_of_region_observations()),
+    ("polynomial coefficients reversed", GE, "poly_apply", _poly_coefficients_reversed,
+     lambda g: TS.test_poly_apply_against_dense_spectral_evaluation(g)),
 ]
 
 

@@ -80,6 +80,20 @@ def test_theorem2_polynomial(small_graph):
     assert np.allclose(general.hybrid_poly(W, U, lam, coeffs, y), direct, atol=1e-12)
 
 
+def test_poly_apply_against_dense_spectral_evaluation(small_graph):
+    # h(W) y for a polynomial h by Horner's rule equals V h(Lambda) V^T y from a
+    # full dense eigendecomposition and the sum of explicit matrix powers.
+    W = small_graph["W"].toarray()
+    coeffs = [0.3, 0.5, -0.2, 0.0, 0.0, 0.1]
+    y = np.random.default_rng(2).standard_normal(60)
+    lam, V = np.linalg.eigh(W)
+    ref = V @ (np.polyval(coeffs[::-1], lam) * (V.T @ y))
+    powers = sum(c * (np.linalg.matrix_power(W, i) @ y) for i, c in enumerate(coeffs))
+    got = general.poly_apply(lambda z: W @ z, coeffs, y)
+    assert np.allclose(got, ref, atol=1e-12)
+    assert np.allclose(got, powers, atol=1e-12)
+
+
 def test_kappa_formulas(small_graph):
     # Eq. 22 and Eq. 23 against condition numbers of the dense matrices.
     W = small_graph["W"].toarray()
