@@ -42,3 +42,22 @@ def test_product_path_does_not_import_the_oracle():
                 txt = open(os.path.join(dp, f)).read()
                 assert not re.search(r"^\s*(from|import)\s+oracle", txt, re.M), f
                 assert "oracle/" not in txt, f
+
+
+def test_binding_marshals_element_types():
+    # numpy inputs become the ABI's element types; a tensor of the wrong type
+    # is refused (it would be passed by pointer and misread)
+    import numpy as np
+    import torch
+    from paper_1807_08692_gb300 import hd
+    a = hd._typed(np.arange(5, dtype=np.int64), np.int32, "int32")
+    assert a.dtype == np.int32 and a.flags["C_CONTIGUOUS"] and list(a) == [0, 1, 2, 3, 4]
+    assert hd._typed([0.5, 1.5], np.float32, "float32").dtype == np.float32
+    assert hd._typed(None, np.int32, "int32") is None
+    t = torch.zeros(3, dtype=torch.int32)
+    assert hd._typed(t, np.int32, "int32") is t
+    import pytest
+    with pytest.raises(TypeError):
+        hd._typed(torch.zeros(3, dtype=torch.int64), np.int32, "int32")
+    with pytest.raises(TypeError):
+        hd._typed(torch.zeros(3, dtype=torch.float64), np.float32, "float32")
