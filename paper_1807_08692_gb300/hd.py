@@ -449,9 +449,8 @@ def filter_poly(ctx: Context, g: Graph, eig, y_ptr, y_idx, y_val, coeffs, X=None
     import torch
     B = len(y_ptr) - 1
     co = np.ascontiguousarray(coeffs, dtype=np.float64)
-    yp, yi, yv = (np.ascontiguousarray(y_ptr, np.int32) if isinstance(y_ptr, np.ndarray) else y_ptr,
-                  np.ascontiguousarray(y_idx, np.int32) if isinstance(y_idx, np.ndarray) else y_idx,
-                  np.ascontiguousarray(y_val, np.float32) if isinstance(y_val, np.ndarray) else y_val)
+    yp, yi, yv = (_typed(y_ptr, np.int32, "int32"), _typed(y_idx, np.int32, "int32"),
+                  _typed(y_val, np.float32, "float32"))
     if X is None:
         X = torch.empty((g.n, B), dtype=torch.float32, device="cuda")
     ld = ldx if ldx is not None else (X.shape[1] if hasattr(X, "shape") else B)
@@ -509,7 +508,10 @@ def temporal_truncated(ctx: Context, g: Graph, sl_ptr, sl_idx, y_ptr, y_idx, y_v
     iters = np.zeros(B, np.int32)
     relres = np.zeros(B, np.float32)
     status = np.zeros(B, np.int32)
-    sli = np.ascontiguousarray(sl_idx, np.int32) if isinstance(sl_idx, np.ndarray) else sl_idx
+    sli = _typed(sl_idx, np.int32, "int32")
+    y_ptr = _typed(y_ptr, np.int32, "int32")
+    y_idx = _typed(y_idx, np.int32, "int32")
+    y_val = _typed(y_val, np.float32, "float32")
     ctx.check(lib().hd_temporal_truncated(ctx.handle, g.handle, B, _ptr(slp), _ptr(sli), _ptr(y_ptr), _ptr(y_idx),
                                           _ptr(y_val), alpha, _ptr(tol), max_iter, _ptr(X), X.shape[1], _ptr(iters),
                                           _ptr(relres), _ptr(status)), "hd_temporal_truncated")
