@@ -285,7 +285,7 @@ def e2e_leg(ctx, wl, eig, mode, tol, alpha, K, B, topk):
     return float(np.sum(times)), h2d, d2h
 
 
-# DRAM bytes per launch of the SpMM measured by ncu (profiles/spmm_n1m_b64.md):
+# DRAM bytes per launch of the SpMM measured by ncu (the SpMM summary under profiles/):
 # k_spmm<32> on a 1M-node k=50 graph (d=256 descriptors, nnz 62,097,728), B=64.
 # Scaled to another graph by nnz (the gathered rows dominate); reported only
 # while the kernel source still hashes to the value the counters were taken on.
