@@ -95,9 +95,67 @@ def pcg(apply_A, apply_Minv, b: np.ndarray, tol: float, max_iter: int) -> CGResu
     return CGResult(x, it, np.asarray(res), bool(res[-1] <= tol * bnorm))
 
 
-def laplacian_op(W, alpha: float):
+def rows_matmul(W, Z, threads: int = 1) -> np.ndarray:
+    """W @ Z, with the rows of W split into `threads` consecutive ranges done on
+    threads.  Each output row is the same sum over the same entries in the same
+    order as in W @ Z, so the result is identical; only the wall time differs."""
+    if threads <= 1 or W.shape[0] < 4 * threads:
+        return W @ Z
+    from concurrent.futures import ThreadPoolExecutor
+    Z = np.asarray(Z)
+    bounds = np.linspace(0, W.shape[0], threads + 1).astype(np.int64)
+    out = np.empty((W.shape[0],) + Z.shape[1:], dtype=np.result_type(W.dtype, Z.dtype))
+
+    def part(t):
+        out[bounds[t]:bounds[t + 1]] = W[bounds[t]:bounds[t + 1]] @ Z
+
+    with ThreadPoolExecutor(threads) as ex:
+        list(ex.map(part, range(threads)))
+    return out
+
+
+def cg_columns(apply_A, Bm, tol: float, max_iter: int, apply_Minv=None):
+    """CG (PCG with apply_Minv) on every column of Bm, all columns at once.
+
+    Each column runs the recurrences of `cg` / `pcg` above with its own step
+    lengths and stops on its own ||r_j|| <= tol ||b_j|| (or max_iter); only the
+    operator and preconditioner products are taken on the block of columns
+    still running.  Returns (X, iters per column, recursive ||r_j|| / ||b_j||).
+    """
+    Bm = _columns(Bm)
+    m = Bm.shape[1]
+    X = np.zeros_like(Bm)
+    R = Bm.copy()
+    Z = R.copy() if apply_Minv is None else np.asarray(apply_Minv(R), dtype=np.float64)
+    P = Z.copy()
+    rho = np.einsum("ij,ij->j", R, Z)
+    bnorm = np.linalg.norm(Bm, axis=0)
+    rnorm = np.linalg.norm(R, axis=0)
+    iters = np.zeros(m, dtype=np.int64)
+    running = (rnorm > tol * bnorm) & (iters < max_iter)
+    while running.any():
+        c = np.where(running)[0]
+        Pc = P[:, c]
+        Qc = apply_A(Pc)
+        a = rho[c] / np.einsum("ij,ij->j", Pc, Qc)
+        X[:, c] += a * Pc
+        Rc = R[:, c] - a * Qc
+        R[:, c] = Rc
+        Zc = Rc if apply_Minv is None else np.asarray(apply_Minv(Rc), dtype=np.float64)
+        rho_new = np.einsum("ij,ij->j", Rc, Zc)
+        P[:, c] = Zc + (rho_new / rho[c]) * Pc
+        rho[c] = rho_new
+        iters[c] += 1
+        rnorm[c] = np.linalg.norm(Rc, axis=0)
+        running = (rnorm > tol * bnorm) & (iters < max_iter)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        rel = np.where(bnorm > 0, rnorm / np.where(bnorm > 0, bnorm, 1.0), 0.0)
+    return X, iters, rel
+
+
+def laplacian_op(W, alpha: float, threads: int = 1):
     """z -> L_alpha(W) z = (z - alpha W z) / (1 - alpha) (Eq. 1)."""
-    return lambda z: (z - alpha * (W @ z)) / (1.0 - alpha)
+    return lambda z: (z - alpha * rows_matmul(W, z, threads)) / (1.0 - alpha)
 
 
 def deflated_laplacian_op(W, U1: np.ndarray, lam1: np.ndarray, alpha: float):

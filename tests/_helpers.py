@@ -63,12 +63,19 @@ def check_knn_lists(idx, sim, Xdb, Q, k, exclude_self, sim_tol):
     return differ
 
 
-def ranking_matches(ids_gpu, ids_ref, score_ref, tie):
-    """At every position the ids agree or their reference scores tie within `tie`."""
-    for a, b in zip(ids_gpu, ids_ref):
-        if a != b and abs(score_ref[a] - score_ref[b]) > tie:
-            return False
-    return True
+def check_ranking(ids, scores, x_ref, x=None, score_tol=0.0, tie_rel=1e-5):
+    """A GPU ranking (ids, scores of length K) is a valid top-K of the oracle's
+    scores x_ref: position by position up to ties of tie_rel * max x_ref, ids
+    distinct, nothing that belongs in the top K left out, and its scores are
+    the ranked vector's (x, the GPU's own scores when given, else x_ref) at
+    those ids within score_tol, in decreasing order with ties to the smaller id."""
+    from oracle import rank as ORank
+    x_ref = np.asarray(x_ref, np.float64)
+    ids = np.asarray(ids)
+    K = ids.size
+    ref, _ = ORank.topk(x_ref, K)
+    assert ORank.ranks_match(ids, ref, x_ref, tie_rel * np.abs(x_ref).max(), scores=scores,
+                             x=x_ref if x is None else x, score_tol=score_tol)
 
 
 def near_tie_rows(X, k, margin, exclude_self=True):

@@ -36,12 +36,15 @@ def test_truncated_matches_oracle(gpu_ctx, cfg1_data):
             # the whole graph: plain temporal filtering, in shortlist order
             assert rel_l2_cols(Xg[:s, j:j + 1], cfg1_data["xstar"][sls[j], j:j + 1]).max() <= 1e-4
     # ranking within each shortlist, mapped back to database ids
-    ids, _ = hd.rank_shortlists(gpu_ctx, hd_tensor(Xg), sl_ptr, sl_idx, 10)
+    ids, sc = hd.rank_shortlists(gpu_ctx, hd_tensor(Xg), sl_ptr, sl_idx, 10)
     for j in range(B):
         ref, _ = T.temporal_truncated(cfg1_data["A"], sls[j], cfg1_data["Y"][:, j], 0.99, 1e-12, 5000)
         k = min(10, sizes[j])
         top, _ = ORank.topk(ref, k)
-        assert ORank.ranks_match(_local(ids[j][:k], sls[j]), top, ref, 1e-5 * ref.max()), j
+        # scores are the solver's fp32 values at the shortlist positions, exactly
+        xg = Xg[:sizes[j], j].astype(np.float32)
+        assert ORank.ranks_match(_local(ids[j][:k], sls[j]), top, ref, 1e-5 * ref.max(), scores=sc[j][:k],
+                                 x=xg), j
 
 
 def hd_tensor(a):

@@ -142,3 +142,38 @@ def test_observation_feeds_dense(small_graph):
     ptr, idx, val = observe.observe(small_graph["X"], small_graph["X"][:2] * 0.9, 4)
     Y = observe.dense(60, ptr, idx, val)
     assert Y.shape == (60, 2) and np.count_nonzero(Y) <= 8
+
+
+def test_rows_matmul_is_the_plain_product(small_graph):
+    # the row-split product computes each row exactly as W @ Z does
+    W = small_graph["W"]
+    Z = np.random.default_rng(4).standard_normal((60, 5))
+    for t in (1, 2, 3, 8):
+        assert np.array_equal(D.rows_matmul(W, Z, t), W @ Z)
+        assert np.array_equal(D.laplacian_op(W, 0.9, t)(Z), D.laplacian_op(W, 0.9)(Z))
+
+
+@pytest.mark.parametrize("tol", [1e-4, 1e-8, 1e-13])
+def test_cg_columns_equals_column_by_column_cg(small_graph, tol):
+    # all columns at once, each with its own step lengths and stopping: the
+    # iteration counts and iterates of the one-column CG / PCG (Sec. 4.4)
+    W = small_graph["W"]
+    Y = _y(60, 5, 7, nnz=3)
+    Y[:, 2] *= 1e-3                       # columns of very different scale
+    A = D.laplacian_op(W, 0.99)
+    X, it, rel = D.cg_columns(A, Y, tol, 500)
+    for j in range(Y.shape[1]):
+        ref = D.cg(A, Y[:, j], tol, 500)
+        assert it[j] == ref.iters
+        assert np.linalg.norm(X[:, j] - ref.x) <= 1e-12 * np.linalg.norm(ref.x)
+        assert rel[j] <= tol
+    lam, U = S.eigenpairs(W, 7)
+    Dw = D.preconditioner_weights(lam, 0.99)
+    Minv = lambda z: z + U @ (Dw[:, None] * (U.T @ z)) if np.ndim(z) == 2 else z + U @ (Dw * (U.T @ z))  # noqa: E731
+    Xp, itp, _ = D.cg_columns(A, Y, tol, 500, apply_Minv=Minv)
+    for j in range(Y.shape[1]):
+        ref = D.pcg(A, Minv, Y[:, j], tol, 500)
+        assert itp[j] == ref.iters
+        assert np.linalg.norm(Xp[:, j] - ref.x) <= 1e-12 * np.linalg.norm(ref.x)
+    if tol < 1e-12:
+        assert _rel(X, D.closed_form(W, Y, 0.99)) < 1e-11

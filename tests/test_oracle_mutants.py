@@ -108,6 +108,37 @@ def _regional_first_region_only(Xdb, Q, regions, k_y, gamma=3.0):
     return p, i, v
 
 
+def _ranks_match_positionwise_only(ids, ids_ref, score_ref, tie, scores=None, x=None, score_tol=0.0):
+    for a, b in zip(ids, ids_ref):
+        if a != b and abs(score_ref[a] - score_ref[b]) > tie:
+            return False
+    return True
+
+
+def _cg_columns_shared_step(apply_A, Bm, tol, max_iter, apply_Minv=None):
+    # one step length for every column (the first column's): a plausible
+    # mistake when vectorising CG over a block
+    Bm = np.asarray(Bm, dtype=np.float64)
+    X = np.zeros_like(Bm)
+    R = Bm.copy()
+    P = R.copy()
+    rho = np.einsum("ij,ij->j", R, R)
+    bn = np.linalg.norm(Bm, axis=0)
+    it = 0
+    with np.errstate(all="ignore"):
+        while it < max_iter and np.any(np.linalg.norm(R, axis=0) > tol * bn):
+            Q = apply_A(P)
+            a = rho[0] / float(P[:, 0] @ Q[:, 0])
+            X += a * P
+            R -= a * Q
+            rn = np.einsum("ij,ij->j", R, R)
+            P = R + (rn / rho) * P
+            rho = rn
+            it += 1
+    m = Bm.shape[1]
+    return X, np.full(m, it), np.linalg.norm(R, axis=0) / bn
+
+
 MUTANTS = [
     ("g drops (1-alpha)", D, "g_alpha", _g_no_one_minus_alpha,
      lambda g: TD.test_hybrid_every_rank_equals_closed_form(g, 5)),
@@ -137,6 +168,10 @@ MUTANTS = [
      lambda g: TG.test_observe_regional_is_the_sum_of_region_observations()),
     ("polynomial coefficients reversed", GE, "poly_apply", _poly_coefficients_reversed,
      lambda g: TS.test_poly_apply_against_dense_spectral_evaluation(g)),
+    ("ranking check position-wise only", R, "ranks_match", _ranks_match_positionwise_only,
+     lambda g: TS.test_ranks_match_rejects_invalid_rankings()),
+    ("block CG with one step length", D, "cg_columns", _cg_columns_shared_step,
+     lambda g: TD.test_cg_columns_equals_column_by_column_cg(g, 1e-8)),
 ]
 
 

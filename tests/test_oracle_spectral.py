@@ -172,6 +172,36 @@ def test_pooled_and_rank_match():
     assert not rank.ranks_match([2, 0, 1], [0, 1, 2], ref, 1e-6)
 
 
+def test_ranks_match_rejects_invalid_rankings():
+    # Sec. 3: items ranked by decreasing score; a ranking may differ from the
+    # reference only inside score ties, and must still be a ranking.
+    ref = np.array([1.0, 1.0, 1.0, 0.5, 0.2])
+    ids_ref, _ = rank.topk(ref, 3)
+    assert list(ids_ref) == [0, 1, 2]
+    assert rank.ranks_match([2, 0, 1], ids_ref, ref, 1e-9)            # a reordered tie run
+    assert not rank.ranks_match([0, 0, 1], ids_ref, ref, 1e-9)        # an id twice inside the tie run
+    assert not rank.ranks_match([0, 1, 5], ids_ref, ref, 1e-9)        # id out of range
+    assert not rank.ranks_match([0, 1, 3], ids_ref, ref, 1e-9)        # 0.5 is not tied with 1.0
+    assert not rank.ranks_match([0, 1], ids_ref, ref, 1e-9)           # wrong length
+    # a ranking shifted down a chain of near-ties leaves out an item that belongs in it
+    chain = np.array([5.0, 4.9, 4.8, 4.7, 0.0])
+    cref, _ = rank.topk(chain, 3)
+    assert rank.ranks_match([1, 0, 2], cref, chain, 0.15)
+    assert not rank.ranks_match([1, 2, 3], cref, chain, 0.15)
+    # the ranking's own scores: equal to the ranked vector at the ids, non-increasing,
+    # equal scores with the smaller id first
+    x = np.array([1.0, 1.0, 1.0, 0.5, 0.2], dtype=np.float32)
+    assert rank.ranks_match([0, 1, 2], ids_ref, ref, 1e-9, scores=x[[0, 1, 2]], x=x)
+    assert not rank.ranks_match([0, 1, 2], ids_ref, ref, 1e-9, scores=[1.0, 1.0, 0.9], x=x)
+    assert not rank.ranks_match([1, 0, 2], ids_ref, ref, 1e-9, scores=x[[1, 0, 2]], x=x)
+    y = np.array([1.0, 1.0 + 1e-12, 1.0, 0.5, 0.2])
+    assert rank.ranks_match([1, 0, 2], ids_ref, ref, 1e-9, scores=y[[1, 0, 2]], x=y)
+    assert not rank.ranks_match([0, 1, 2], ids_ref, ref, 1e-9, scores=y[[0, 1, 2]], x=y)
+    # pooled scores: equal within a relative tolerance
+    assert rank.ranks_match([0, 1, 2], ids_ref, ref, 1e-9, scores=[1.0 + 1e-8, 1.0, 1.0], x=ref,
+                            score_tol=1e-6)
+
+
 def test_kappa_deflated_against_dense(small_graph):
     # Sec. 4.4: W_r keeps r zero eigenvalues; for every r (including r with
     # lambda_{r+1} < 0, where Eq. 23 alone would not apply) the condition
