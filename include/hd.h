@@ -58,6 +58,11 @@ extern "C" {
 #define HD_MODE_PAPER 0          /* Eq. 17-20: x = U1 g(L1) U1^T y + CG on L_a(W - U1 L1 U1^T) x^t = y */
 #define HD_MODE_PROJ 1           /* x = U1 h(L1) U1^T y + (1-a) x2, (I - a W_r) x2 = (I - U1 U1^T) y */
 #define HD_MODE_PCG 2            /* PCG on L_a(W) x = y, M^-1 = I + U1 diag(a l/(1 - a l)) U1^T */
+/* Or-ed into HD_MODE_PAPER or HD_MODE_PROJ: X receives the temporal term alone
+ * (x^t of Eq. 19, or (1-a) x2 of the projected form) instead of x^s + x^t, so
+ * the temporal solve can be checked on its own (Eq. 19-20).  Invalid with
+ * HD_MODE_PCG, which has no separate terms. */
+#define HD_MODE_TEMPORAL_ONLY 0x100
 
 /* ---- per-column status --------------------------------------------------- */
 #define HD_COL_CONVERGED 0
@@ -65,6 +70,8 @@ extern "C" {
 #define HD_COL_BREAKDOWN 2       /* p^T A p <= 0 or not finite */
 #define HD_COL_EMPTY 3           /* y == 0: x = 0 after 0 iterations */
 #define HD_COL_CANCELLED 4       /* serving: withdrawn by hd_serve_cancel, no ranking */
+#define HD_COL_STAGNATED 5       /* the recursive residual met tol, the true residual did not, even
+                                    after the allowed residual replacements (fp32 floor) */
 
 typedef struct hd_ctx hd_ctx;
 typedef struct hd_graph hd_graph;
@@ -82,13 +89,17 @@ int hd_destroy(hd_ctx* ctx);
 const char* hd_last_error(const hd_ctx* ctx);
 /* Number of library kernel launches issued on this context so far. */
 int64_t hd_launch_count(const hd_ctx* ctx);
+/* Bytes of device workspace the context currently holds (grown on demand by
+ * the calls that need scratch, released by hd_destroy). */
+int hd_workspace_bytes(const hd_ctx* ctx, size_t* bytes);
 /* Number of streaming multiprocessors of the context's device. */
 int hd_num_sms(const hd_ctx* ctx);
 /* Per-kernel device timing: while enabled, every launch of the library's
  * main kernels is bracketed by CUDA events on the context's stream.
  * hd_profile_read synchronises the stream and returns, for the kernel family
- * `name` ("spmm", "dot", "update", "direction", "colsq", "lr_reduce",
- * "lr_expand", "scalar", "rank", "knn", "trunc_build"), the number of
+ * `name` ("spmm", "resid" (the true-residual SpMM), "dot", "update",
+ * "direction", "colsq", "lr_reduce", "lr_expand", "scalar", "rank", "knn",
+ * "trunc_build"), the number of
  * launches and their summed duration since the
  * last read, then clears that family.  busy_launches (may be NULL) counts the
  * launches that took at least 5% of the family's longest one: kernels of an
@@ -202,6 +213,9 @@ int hd_cg_bound(int mode, double alpha, double lam_next, double lam_min, double 
                 double* kappa_out, int32_t* iters_anorm, int32_t* iters_resid);
 
 int hd_eig_info(const hd_eig* e, int32_t* r, int* storage);
+/* Thick restarts the block Lanczos run that computed e took (-1 for
+ * eigenpairs given by the caller, loaded or sparsified). */
+int hd_eig_restarts(const hd_eig* e, int32_t* restarts);
 
 /* SHybrid (Sec. 5.3, Table 1, Fig. 2): a new eigenpair handle whose U keeps
  * only the largest-magnitude entries of src's stored U.  The
@@ -254,7 +268,7 @@ int hd_eig_expand(hd_ctx* ctx, const hd_eig* e, const double* H, int32_t B, floa
  * or duplicated shortlist id or observation index, HD_ERR_OOM. */
 int hd_temporal_truncated(hd_ctx* ctx, const hd_graph* g, int32_t B, const int32_t* sl_ptr,
                           const int32_t* sl_idx, const int32_t* y_ptr, const int32_t* y_idx,
-                          const float* y_val, float alpha, const float* tol, int32_t max_iter,
+                          const float* y_val, double alpha, const float* tol, int32_t max_iter,
                           float* X, int32_t ldx, int32_t* iters, float* relres, int32_t* status);
 
 /* ---- general transfer functions (Appendix A) ------------------------------ */
@@ -304,21 +318,33 @@ int hd_selftest_wait(hd_ctx* ctx, uint32_t limit_us, int32_t* gave_up);
 
 /* Solve for B ranking vectors at once (one column per query).
  *  eig      : NULL or r = 0 gives temporal filtering (Eq. 2) in every mode.
- *  mode     : HD_MODE_PAPER / HD_MODE_PROJ / HD_MODE_PCG (see above).
+ *  mode     : HD_MODE_PAPER / HD_MODE_PROJ / HD_MODE_PCG (see above), the
+ *             first two optionally or-ed with HD_MODE_TEMPORAL_ONLY.
  *  y_ptr[B+1], y_idx, y_val : the sparse observations (host or device);
  *             indices in [0, n); duplicates are summed.
  *  alpha    : in [0, 1).
- *  tol[B]   : per-column relative residual tolerance (host or device); the
- *             column stops when ||r||_2 <= tol ||b||_2 (recursive residual).
+ *  tol[B]   : per-column relative residual tolerance (host or device).
  *  max_iter : maximum operator applications per column.
  *  X        : output, n x B scores with leading dimension ldx >= B
  *             (host or device).  X = x^s + x^t.
  *  iters[B], relres[B], status[B] : per column (host or device, may be NULL).
- * The solve runs without host synchronisation except a poll of an active-
- * column count every four iterations.  Those four iterations are one CUDA
- * graph, captured on the context's own side stream the first time and
- * replayed on the context's stream while the graph, eigenpairs, mode, batch
- * width, alpha and max_iter stay the same (any change re-captures it; with
+ * Stopping (x0 = 0, Sec. 4.4): a column stops iterating when its recursive
+ * residual r satisfies ||r||_2 <= tol ||b||_2.  The true residual b - A x of
+ * the system the column solves (A = L_a(W) for HD_MODE_PCG and temporal
+ * filtering, L_a(W - U1 L1 U1^T) for the paper's form, b = y, or
+ * (I - U1 U1^T) y for the projected form) is then computed once for the whole
+ * batch with the same kernels.  A column whose true residual is above
+ * tol ||b||_2 is restarted from its x with r := b - A x (residual
+ * replacement), at most 3 times per call and within max_iter; if it still
+ * misses, its status is HD_COL_STAGNATED.  relres[j] is the final TRUE
+ * relative residual ||b - A x|| / ||b||, computed in fp32 on the device.
+ * The solve runs without host synchronisation except polls of an active-
+ * column count: the first after as many iterations as the previous solve on
+ * the context took (same graph, eigenpairs, mode and batch width; 4 otherwise,
+ * at most 8), then every 2.  Each such run of iterations is one CUDA graph,
+ * captured on the context's own side stream the first time and replayed on
+ * the context's stream while the graph, eigenpairs, mode, batch width, alpha
+ * and max_iter stay the same (any change re-captures it; with
  * hd_profile_enable on, kernels launch one by one instead).  The call is
  * therefore not itself capturable into a caller's graph.  Errors: HD_ERR_INVALID_ARG for bad
  * sizes, indices out of range or non-finite observation values (checked on
@@ -327,7 +353,7 @@ int hd_selftest_wait(hd_ctx* ctx, uint32_t limit_us, int32_t* gave_up);
  * waits (the kernels never hang; X is then undefined),
  * HD_ERR_NOT_CONVERGED is NOT returned: per-column status says it. */
 int hd_query_batch(hd_ctx* ctx, const hd_graph* g, const hd_eig* eig, int mode, int32_t B,
-                   const int32_t* y_ptr, const int32_t* y_idx, const float* y_val, float alpha,
+                   const int32_t* y_ptr, const int32_t* y_idx, const float* y_val, double alpha,
                    const float* tol, int32_t max_iter, float* X, int32_t ldx, int32_t* iters,
                    float* relres, int32_t* status);
 
@@ -349,12 +375,17 @@ int hd_rank(hd_ctx* ctx, const float* X, int64_t n, int32_t B, int32_t ldx, cons
  * entirely reserved by another framework's caching allocator, or a plugin that
  * may only use memory handed to it.  Scratch is one file-scope device array of
  * about 4.3 MB (B <= 256 columns, Kmax <= 2048) that every device using the
- * library holds until the process exits.  The first call on a device looks up
- * that array's device address (cudaGetSymbolAddress), so make it before any
- * stream capture.  All calls share the array: calls whose work overlaps on the
- * GPU (different streams or contexts, or host threads) race and must be
- * serialised by the caller.  X (n x B, leading dimension ldx), idx_out and
- * score_out (B x Kmax) must be device memory; K[B] is host.  No pooling.
+ * library holds until the process exits.  The first call on a device (again
+ * after hd_destroy of a context on it) looks up that array's device address
+ * with cudaGetSymbolAddress; the cached address assumes the device is not
+ * reset while a context on it is alive.  The call cannot be captured into a
+ * CUDA graph: it copies K from host memory and, when ties fall at a column's
+ * K-th place, reads state back and synchronises the stream.  K is read during
+ * the call only (the library copies it).  All calls share the array: calls
+ * whose work overlaps on the GPU (different streams or contexts, or host
+ * threads) race and must be serialised by the caller.  X (n x B, leading
+ * dimension ldx), idx_out and score_out (B x Kmax) must be device memory; K[B]
+ * is host.  No pooling.
  * Errors: HD_ERR_INVALID_ARG beyond the limits or for host X/outputs. */
 int hd_rank_static(hd_ctx* ctx, const float* X, int64_t n, int32_t B, int32_t ldx,
                    const int32_t* K, int32_t Kmax, int32_t* idx_out, float* score_out);
@@ -383,7 +414,7 @@ typedef struct hd_req_stats {
  * form needs a per-request spectral term at admission); without, it is
  * temporal CG.  Kmax <= 2048 bounds per-request K.
  * Errors: HD_ERR_OOM when not even one slot fits the budget or the device. */
-int hd_serve_open(hd_ctx* ctx, const hd_graph* g, const hd_eig* eig, int mode, float alpha,
+int hd_serve_open(hd_ctx* ctx, const hd_graph* g, const hd_eig* eig, int mode, double alpha,
                   int32_t max_slots, size_t mem_budget, int32_t max_iter, int32_t Kmax,
                   hd_server** out);
 /* Columns of the wide persistent batch. */

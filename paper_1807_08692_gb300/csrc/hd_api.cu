@@ -116,10 +116,11 @@ int hd_destroy(hd_ctx* ctx) {
     if (!ctx) return HD_OK;
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
+    hd_rank_static_forget(ctx->device);
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->h_poll) cudaFreeHost(ctx->h_poll);
     if (ctx->d_flags) cudaFree(ctx->d_flags);
-    if (ctx->iter_exec) cudaGraphExecDestroy(ctx->iter_exec);
+    for (auto& kv : ctx->iter_graphs) cudaGraphExecDestroy(kv.second.exec);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     for (auto& kv : ctx->prof_ev)
         for (auto& pr : kv.second) {
@@ -167,6 +168,11 @@ int hd_profile_read(hd_ctx* ctx, const char* name, int64_t* launches, double* to
     return HD_OK;
 }
 int64_t hd_launch_count(const hd_ctx* ctx) { return ctx ? ctx->launches : 0; }
+int hd_workspace_bytes(const hd_ctx* ctx, size_t* bytes) {
+    if (!ctx || !bytes) return HD_ERR_INVALID_ARG;
+    *bytes = ctx->ws_bytes;
+    return HD_OK;
+}
 int hd_num_sms(const hd_ctx* ctx) { return ctx ? ctx->num_sms : 0; }
 
 }  // extern "C"
@@ -518,6 +524,12 @@ int hd_eig_info(const hd_eig* e, int32_t* r, int* storage) {
     if (!e) return HD_ERR_INVALID_ARG;
     if (r) *r = e->r;
     if (storage) *storage = e->storage;
+    return HD_OK;
+}
+
+int hd_eig_restarts(const hd_eig* e, int32_t* restarts) {
+    if (!e || !restarts) return HD_ERR_INVALID_ARG;
+    *restarts = e->restarts;
     return HD_OK;
 }
 

@@ -24,12 +24,18 @@ struct hd_ctx {
     // pinned host words for polling device counters
     int* h_poll = nullptr;
     int* d_flags = nullptr;   // [0]: device-side error flag, [1..]: misc counters
-    // CUDA graph of `graph_iters` CG iterations, re-captured when the solve's
-    // pointers or scalars change (key); launched on `stream`
+    // CUDA graphs of runs of CG iterations, keyed by everything the kernels
+    // take as arguments plus the run length (a few kept; re-captured when the
+    // solve's pointers or scalars change); launched on `stream`
+    struct IterGraph {
+        cudaGraphExec_t exec = nullptr;
+        int64_t launches = 0;
+    };
     cudaStream_t cap_stream = nullptr;
-    cudaGraphExec_t iter_exec = nullptr;
-    std::vector<uint64_t> iter_key;
-    int64_t iter_launches = 0;
+    std::map<std::vector<uint64_t>, IterGraph> iter_graphs;
+    // iterations the previous solve with the same key (run length left out) took
+    std::vector<uint64_t> hint_key;
+    int iter_hint = 0;
     // per-kernel event timing (hd_profile_enable)
     bool prof = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -75,6 +81,8 @@ struct hd_graph {
     // chosen per padded batch width
     mutable std::map<int, int32_t*> seg_bounds;
     mutable std::map<int, int> seg_cache;
+    // entries in the longest row (measured on first use; -1 until then)
+    mutable int32_t max_row = -1;
 };
 
 struct hd_eig {
@@ -91,6 +99,7 @@ struct hd_eig {
     int32_t lds = 0;
     double* lambda_d = nullptr;
     std::vector<double> lambda_h;
+    int32_t restarts = -1;    // thick restarts of the Lanczos run that made it (-1: not from Lanczos)
     // sparsified embedding (hd_eig_sparsify): U is not stored densely then
     bool sparse = false;
     int64_t nnz = 0;
@@ -139,6 +148,8 @@ bool hd_is_device_ptr(const void* p);
 // Workspace: returns a device pointer of at least `bytes`, 256-aligned,
 // valid until the next hd_ws_reserve on the same context.
 int hd_ws_reserve(hd_ctx* ctx, size_t bytes, void** out);
+// drop the cached device address of hd_rank_static's scratch on a device
+void hd_rank_static_forget(int device);
 struct WsCarver {
     char* base;
     size_t off = 0;

@@ -372,6 +372,7 @@ static int lanczos_top(hd_ctx* ctx, const hd_graph* g, int32_t r, int32_t block,
             }
             hd_eig* e;
             TRY(hd_eig_alloc(ctx, n, r, storage, &e));
+            e->restarts = restart;
             e->lambda_h.assign(thk.begin(), thk.begin() + r);
             HD_CUDA(ctx, cudaMemcpyAsync(e->lambda_d, thk.data(), (size_t)r * 8, cudaMemcpyHostToDevice, ctx->stream));
             float* U32;

@@ -8,6 +8,7 @@
 // (score descending, id ascending).  The K survivors are then sorted per column
 // with a bitonic sort on (key, ~id).
 #include <algorithm>
+#include <atomic>
 #include <vector>
 
 #include "hd_internal.cuh"
@@ -428,9 +429,15 @@ constexpr size_t RS_BYTES = RS_STATE + RS_HIST + RS_CAND + RS_K;  // about 4.3 M
 static __device__ __align__(256) unsigned char g_rank_scratch[RS_BYTES];
 
 // Device address of g_rank_scratch per device (the host-side symbol is only a
-// stand-in and must never be handed to a kernel).  Filled on the first call on
-// each device, with that device current.
-static void* g_rank_scratch_dev[64] = {nullptr};
+// stand-in and must never be handed to a kernel).  Looked up on the first call
+// on each device, with that device current; hd_destroy forgets it, so a device
+// reset between contexts leads to a fresh lookup.  While a context is alive the
+// cached address assumes its device is not reset.
+static std::atomic<void*> g_rank_scratch_dev[64];
+
+void hd_rank_static_forget(int device) {
+    if (device >= 0 && device < 64) g_rank_scratch_dev[device].store(nullptr);
+}
 
 extern "C" int hd_rank_static(hd_ctx* ctx, const float* X, int64_t n, int32_t B, int32_t ldx, const int32_t* K,
                               int32_t Kmax, int32_t* idx_out, float* score_out) {
@@ -441,28 +448,34 @@ extern "C" int hd_rank_static(hd_ctx* ctx, const float* X, int64_t n, int32_t B,
                        RS_MAX_K);
     if (!hd_is_device_ptr(X) || !hd_is_device_ptr(idx_out) || !hd_is_device_ptr(score_out))
         return hd_fail(ctx, HD_ERR_INVALID_ARG, "hd_rank_static: X and the outputs must be device memory");
-    for (int j = 0; j < B; ++j)
-        if (K[j] < 0 || K[j] > Kmax) return hd_fail(ctx, HD_ERR_INVALID_ARG, "K[%d]=%d outside [0, Kmax]", j, K[j]);
+    // K is copied here, so the caller's array is only read during the call
+    // (the device copy below then reads the library's pageable copy, which the
+    // runtime stages before returning)
+    int32_t kh[RS_MAX_B];
+    for (int j = 0; j < B; ++j) {
+        kh[j] = K[j];
+        if (kh[j] < 0 || kh[j] > Kmax) return hd_fail(ctx, HD_ERR_INVALID_ARG, "K[%d]=%d outside [0, Kmax]", j, kh[j]);
+    }
     if (ctx->device < 0 || ctx->device >= 64) return hd_fail(ctx, HD_ERR_INVALID_ARG, "device %d", ctx->device);
     HD_CUDA(ctx, cudaSetDevice(ctx->device));
-    if (!g_rank_scratch_dev[ctx->device]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_rank_scratch);
-        if (e != cudaSuccess || !p)
+    void* base_p = g_rank_scratch_dev[ctx->device].load();
+    if (!base_p) {
+        cudaError_t e = cudaGetSymbolAddress(&base_p, g_rank_scratch);
+        if (e != cudaSuccess || !base_p)
             return hd_fail(ctx, HD_ERR_CUDA, "cudaGetSymbolAddress(g_rank_scratch): %s", cudaGetErrorString(e));
-        g_rank_scratch_dev[ctx->device] = p;
+        g_rank_scratch_dev[ctx->device].store(base_p);
+        HD_CUDA(ctx, cudaFuncSetAttribute(k_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, CG * 256 * 4));
     }
-    char* base = (char*)g_rank_scratch_dev[ctx->device];
+    char* base = (char*)base_p;
     SelState* st = (SelState*)base;
     uint32_t* hist = (uint32_t*)(base + RS_STATE);
     uint64_t* cand = (uint64_t*)(base + RS_STATE + RS_HIST);
     int32_t* Kd = (int32_t*)(base + RS_STATE + RS_HIST + RS_CAND);
     // the array keeps the previous call's contents: the histogram must start at zero
     HD_CUDA(ctx, cudaMemsetAsync(hist, 0, (size_t)B * 256 * sizeof(uint32_t), ctx->stream));
-    HD_CUDA(ctx, cudaMemcpyAsync(Kd, K, B * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+    HD_CUDA(ctx, cudaMemcpyAsync(Kd, kh, B * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
     k_sel_init<<<ceil_div(B, 128), 128, 0, ctx->stream>>>(st, Kd, B, n);
     HD_CHECK_LAUNCH(ctx);
-    HD_CUDA(ctx, cudaFuncSetAttribute(k_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, CG * 256 * 4));
     const int gy = ceil_div(B, CG);
     const int gx = std::max(1, std::min<int>(ceil_div(n * std::min(B, CG), 256), ctx->num_sms * 4 / gy + 1));
     const size_t hsm = (size_t)std::min(B, CG) * 256 * 4;

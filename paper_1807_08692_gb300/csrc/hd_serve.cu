@@ -171,7 +171,7 @@ static int admit_cb(void* arg) {
 }
 
 // Buffers and engine of one lane of `slots` columns.
-static int lane_open(hd_ctx* ctx, const hd_graph* g, const hd_eig* eig, float alpha, int32_t slots, int32_t max_iter,
+static int lane_open(hd_ctx* ctx, const hd_graph* g, const hd_eig* eig, double alpha, int32_t slots, int32_t max_iter,
                      int32_t Kmax, int32_t slot_base, Lane& L) {
     const bool lr_on = eig && eig->r > 0;
     const int64_t n = g->n;
@@ -397,11 +397,11 @@ static int lane_warm(hd_server* s, Lane& L) {
 
 extern "C" {
 
-int hd_serve_open(hd_ctx* ctx, const hd_graph* g, const hd_eig* eig, int mode, float alpha, int32_t max_slots,
+int hd_serve_open(hd_ctx* ctx, const hd_graph* g, const hd_eig* eig, int mode, double alpha, int32_t max_slots,
                   size_t mem_budget, int32_t max_iter, int32_t Kmax, hd_server** out) {
     if (!ctx || !g || !out || max_slots < 1 || max_slots > 256 || Kmax < 1 || Kmax > 2048 || max_iter < 1)
         return HD_ERR_INVALID_ARG;
-    if (!(alpha >= 0.0f && alpha < 1.0f)) return hd_fail(ctx, HD_ERR_INVALID_ARG, "alpha=%g", alpha);
+    if (!(alpha >= 0.0 && alpha < 1.0)) return hd_fail(ctx, HD_ERR_INVALID_ARG, "alpha=%g", alpha);
     const bool lr_on = eig && eig->r > 0;
     if (lr_on && mode != HD_MODE_PCG)
         return hd_fail(ctx, HD_ERR_INVALID_ARG, "the server runs PCG with eigenpairs (mode %d unsupported)", mode);

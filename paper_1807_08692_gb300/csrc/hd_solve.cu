@@ -11,7 +11,11 @@
 //   [PCG: C = U^T R, rho' = rr + sum_k D_k C_k^2, Z = R + U (D o C)]
 //   beta = rho' / rho; P = Z + beta P
 // Columns stop individually (||r|| <= tol ||b||, max_iter, breakdown); a
-// stopped column keeps X and R bit-for-bit (its step length is 0).
+// stopped column keeps X and R bit-for-bit (its step length is 0).  When every
+// column has stopped, the true residual b - A x is formed for the batch; a
+// column whose recursive residual met tol but whose true residual did not is
+// restarted from x with r := b - A x (residual replacement, at most
+// MAX_CONFIRM times), and the true value is what the solve reports.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -70,12 +74,14 @@ __device__ __forceinline__ bool slab_has_work(const ColState* st, bool include_f
 // eight 256-thread blocks per SM, and the extra warps keep more of the random
 // row gathers in flight (measured on the 1M-node graph: 1.58 ms + 0.08 ms for
 // the separate pass against 2.06 ms with the partials fused).
+// `skip` (may be null): the launch returns at once when *skip is not 0.
 template <int S>
 __global__ void __launch_bounds__(256, 8) k_spmm(const int32_t* rp, const int32_t* ci, const float* wv, const float* P,
                                               float* Q, int64_t n, int32_t ld, float c1, float c2,
-                                              const ColState* st) {
+                                              const ColState* st, const int* skip = nullptr) {
     constexpr int L = S / 4;
     constexpr int RPB = 256 / L;
+    if (skip && *skip) return;
     if (!slab_has_work<S>(st, false)) return;
     const int g = (threadIdx.x & 31) % L;
     const int col = blockIdx.y * S + 4 * g;
@@ -177,6 +183,95 @@ __global__ void __launch_bounds__(256) k_spmm_w4(const int32_t* rp, const int32_
     }
 }
 
+// ---- the true residual, accumulated in two fp32 words
+// b - A x with A = c1 I - c2 W cancels: c1 x and c2 W x are ~1/(1 - a) times
+// larger than the result, so the fp32 rounding of W x (relative ~u per term)
+// would reach the residual magnified 1/(1 - a) times (about 7e-7 ||y|| on the
+// 2,000-node graph, as large as a 1e-6 tolerance).  The residual kernels below
+// carry W x as an unevaluated sum hi + lo of two fp32 numbers, built with
+// error-free transformations: the product w v = p + e exactly (e from one fma;
+// Ogita, Rump and Oishi, "Accurate sum and dot product", 2005) and the sum
+// hi + p = s + e exactly (Knuth's TwoSum).  The _rn intrinsics keep the
+// compiler from contracting these into other fma operations.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bv = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bv)), __fsub_rn(b, bv));
+}
+
+// hi + lo += w v
+__device__ __forceinline__ void df_fma(float& hi, float& lo, float w, float v) {
+    const float p = __fmul_rn(w, v);
+    const float pe = __fmaf_rn(w, v, -p);
+    float s, e;
+    two_sum(hi, p, s, e);
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(e, pe));
+}
+
+// -(c1 x - c2 (hi + lo)), rounded once at the end
+__device__ __forceinline__ float neg_operator(float c1, float x, float c2, float hi, float lo) {
+    const float p1 = __fmul_rn(c1, x), e1 = __fmaf_rn(c1, x, -p1);
+    const float p2 = __fmul_rn(c2, hi), e2 = __fmaf_rn(c2, hi, -p2);
+    float d, e3;
+    two_sum(p1, -p2, d, e3);
+    const float tail = __fsub_rn(__fsub_rn(__fadd_rn(e3, e1), e2), __fmul_rn(c2, lo));
+    return -__fadd_rn(d, tail);
+}
+
+// Q = -(c1 X - c2 W X) for the S-column slab blockIdx.y, W X in two words.
+// Runs when *pick is 1 (see k_resid_pick).
+template <int S>
+__global__ void __launch_bounds__(256, 4) k_resid(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                                  const float* __restrict__ wv, const float* __restrict__ X,
+                                                  float* __restrict__ Q, int64_t n, int32_t ld, float c1, float c2,
+                                                  const int* __restrict__ pick) {
+    constexpr int L = S / 4;
+    constexpr int RPB = 256 / L;
+    if (*pick != 1) return;
+    const int g = (threadIdx.x & 31) % L;
+    const int col = blockIdx.y * S + 4 * g;
+    for (int64_t row = (int64_t)blockIdx.x * RPB + threadIdx.x / L; row < n; row += (int64_t)gridDim.x * RPB) {
+        const int32_t b = rp[row], e = rp[row + 1];
+        float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
+        int32_t t = b;
+        for (; t + 4 <= e; t += 4) {
+            int32_t j[4];
+            float w[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                j[u] = __ldg(ci + t + u);
+                w[u] = __ldg(wv + t + u);
+            }
+            float4 v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v[u] = ld4(X + (int64_t)j[u] * ld + col);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                df_fma(hi[0], lo[0], w[u], v[u].x);
+                df_fma(hi[1], lo[1], w[u], v[u].y);
+                df_fma(hi[2], lo[2], w[u], v[u].z);
+                df_fma(hi[3], lo[3], w[u], v[u].w);
+            }
+        }
+        for (; t < e; ++t) {
+            const float w0 = __ldg(wv + t);
+            const float4 v0 = ld4(X + (int64_t)__ldg(ci + t) * ld + col);
+            df_fma(hi[0], lo[0], w0, v0.x);
+            df_fma(hi[1], lo[1], w0, v0.y);
+            df_fma(hi[2], lo[2], w0, v0.z);
+            df_fma(hi[3], lo[3], w0, v0.w);
+        }
+        const float4 own = ld4(X + row * ld + col);
+        float4 q;
+        q.x = neg_operator(c1, own.x, c2, hi[0], lo[0]);
+        q.y = neg_operator(c1, own.y, c2, hi[1], lo[1]);
+        q.z = neg_operator(c1, own.z, c2, hi[2], lo[2]);
+        q.w = neg_operator(c1, own.w, c2, hi[3], lo[3]);
+        st4(Q + row * ld + col, q);
+    }
+}
+
 // Per-column operators (truncated systems): column j's row t holds the entries
 // off[j * n + t] .. off[j * n + t + 1] of (ci, wv); columns j >= B are empty.
 // Q = c1 P - c2 W_j P column by column.
@@ -215,6 +310,43 @@ __global__ void __launch_bounds__(256) k_spmm_cols(const int64_t* __restrict__ o
         q.w = c1 * own.w - c2 * s[3];
         st4(Q + row * ld + col, q);
     }
+}
+
+// Q = -(c1 X - c2 W_j X) column by column (truncated systems), W_j X in two words.
+template <int S>
+__global__ void __launch_bounds__(256) k_resid_cols(const int64_t* __restrict__ off, const int32_t* __restrict__ ci,
+                                                    const float* __restrict__ wv, int32_t B, const float* __restrict__ X,
+                                                    float* __restrict__ Q, int64_t n, int32_t ld, float c1, float c2) {
+    constexpr int L = S / 4;
+    constexpr int RPB = 256 / L;
+    const int g = (threadIdx.x & 31) % L;
+    const int col = blockIdx.y * S + 4 * g;
+    for (int64_t row = (int64_t)blockIdx.x * RPB + threadIdx.x / L; row < n; row += (int64_t)gridDim.x * RPB) {
+        const float4 own = ld4(X + row * ld + col);
+        const float ox[4] = {own.x, own.y, own.z, own.w};
+        float q[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int j = col + c;
+            float hi = 0.f, lo = 0.f;
+            if (j < B) {
+                const int64_t f = (int64_t)j * n + row;
+                const int64_t b = __ldg(off + f), e = __ldg(off + f + 1);
+                for (int64_t t = b; t < e; ++t) df_fma(hi, lo, __ldg(wv + t), __ldg(X + (int64_t)__ldg(ci + t) * ld + j));
+            }
+            q[c] = neg_operator(c1, ox[c], c2, hi, lo);
+        }
+        st4(Q + row * ld + col, make_float4(q[0], q[1], q[2], q[3]));
+    }
+}
+
+// *out = the largest row length (entries) of the CSR graph
+__global__ void k_max_row(const int32_t* __restrict__ rp, int64_t n, int* out) {
+    int m = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        m = max(m, rp[i + 1] - rp[i]);
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, m);
 }
 
 // Row i's entries in segment s (columns [s w, (s + 1) w)) are
@@ -508,6 +640,8 @@ __global__ void k_fin_setup(const float2* part, int nblk, int32_t Bp, int32_t B,
     s.beta = 0.0;
     s.iters = 0;
     s.fresh = 0;
+    s.confirms = 0;
+    s.restart = 0;
     if (j >= B || bb == 0.0) {
         s.active = 0;
         s.status = HD_COL_EMPTY;
@@ -565,6 +699,8 @@ __global__ void k_fin_rr(const float2* part, int nblk, int32_t Bp, ColState* st,
         s.beta = 0.0;
         s.a = 0.0;
         s.iters = 0;
+        s.confirms = 0;
+        s.restart = 0;
         if (s.bb == 0.0) {
             s.active = 0;
             s.status = HD_COL_EMPTY;
@@ -595,6 +731,113 @@ __global__ void k_fin_rr(const float2* part, int nblk, int32_t Bp, ColState* st,
         s.status = HD_COL_MAX_ITER;
     } else {
         atomicAdd(num_active, 1);
+    }
+}
+
+// Which residual kernel runs: the fp32 evaluation of b - A x has an error of
+// at most (c2 gamma_m + 2 u c1) ||x|| + 2 u ||b|| (u = 2^-24; gamma_m = m u /
+// (1 - m u) bounds the rounding of a sum of m products, m the longest row
+// plus one; ||W|x||| <= ||x|| for the nonnegative W of spectral radius 1).
+// When that is at most a tenth of tol ||b|| for every column, the fp32 SpMM
+// runs (*pick = 0), else the two-word kernel (*pick = 1).  part: partials of
+// ||x_j||^2; one block per column.
+__global__ void k_resid_pick(const float2* part, int nblk, int32_t Bp, int32_t B, const ColState* st, double gamma,
+                             double c1, double c2, int* pick) {
+    const int j = blockIdx.x;
+    if (j >= B) return;
+    const double xx = col_sum(part, nblk, Bp, j);
+    if (threadIdx.x != 0) return;
+    const ColState& s = st[j];
+    if (s.status == HD_COL_EMPTY || s.status == HD_COL_CANCELLED || s.bb <= 0.0) return;
+    const double u = 1.0 / 16777216.0;
+    const double bound = (c2 * gamma + 2.0 * u * c1) * sqrt(xx) + 2.0 * u * sqrt(s.bb);
+    // tol2 = tol^2 ||b||^2
+    if (!(bound <= 0.1 * sqrt(s.tol2))) atomicExch(pick, 1);
+}
+
+// ---- confirmation by the true residual (x0 = 0 and a residual stopping rule, Sec. 4.4)
+// Residual replacements allowed per column and solve.
+constexpr int MAX_CONFIRM = 3;
+
+// part: partials of ||T||^2, T = b - A x (every column).  rr := ||T||^2, the
+// value the solve reports.  A column whose recursive residual met tol while
+// ||T|| > tol ||b|| is reactivated with r := T (flag `restart`) while it has
+// iterations and replacements left; otherwise it is STAGNATED.
+__global__ void k_fin_confirm(const float2* part, int nblk, int32_t Bp, int32_t B, ColState* st, int32_t max_iter,
+                              int* num_active) {
+    const int j = blockIdx.x;
+    ColState& s = st[j];
+    if (j >= B || s.status == HD_COL_EMPTY || s.status == HD_COL_CANCELLED) return;
+    const double tt = col_sum(part, nblk, Bp, j);
+    if (threadIdx.x != 0) return;
+    s.rr = tt;
+    s.restart = 0;
+    if (!isfinite(tt)) {
+        s.status = HD_COL_BREAKDOWN;
+        return;
+    }
+    if (s.status != HD_COL_CONVERGED || tt <= s.tol2) return;
+    if (s.iters < max_iter && s.confirms < MAX_CONFIRM) {
+        s.confirms += 1;
+        s.active = 1;
+        s.status = HD_COL_MAX_ITER;
+        s.restart = 1;
+        atomicAdd(num_active, 1);
+    } else {
+        s.status = HD_COL_STAGNATED;
+    }
+}
+
+// R[:, j] := T[:, j] for the columns being restarted.
+__global__ void k_restart_copy(float* __restrict__ R, const float* __restrict__ T, int64_t n, int32_t ld,
+                               const ColState* __restrict__ st) {
+    const int nq = ld >> 2;
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;  // float4 index = row * nq + quad
+    if (e >= n * nq) return;
+    const int col = 4 * (int)(e % nq);
+    const int m = st[col].restart | st[col + 1].restart << 1 | st[col + 2].restart << 2 | st[col + 3].restart << 3;
+    if (!m) return;
+    float4 r = ld4v(R + 4 * e);
+    const float4 t = ld4v(T + 4 * e);
+    if (m & 1) r.x = t.x;
+    if (m & 2) r.y = t.y;
+    if (m & 4) r.z = t.z;
+    if (m & 8) r.w = t.w;
+    st4(R + 4 * e, r);
+}
+
+// Restarted columns: rho = ||r||^2 (+ sum_k coef_k C_k^2 with the
+// preconditioner, C = U^T r), a fresh direction (beta = 0); every other
+// column gets beta = 0 so the direction update leaves it finite.
+__global__ void k_fin_restart(ColState* st, const double* C, const double* coef, int32_t r) {
+    const int j = blockIdx.x;
+    ColState& s = st[j];
+    if (!s.restart) {
+        if (threadIdx.x == 0) s.beta = 0.0;
+        return;
+    }
+    const double lrt = col_lowrank(C, coef, r, gridDim.x, j);
+    if (threadIdx.x != 0) return;
+    s.rho = s.rr + lrt;
+    s.beta = 0.0;
+    s.a = 0.0;
+    s.restart = 0;
+}
+
+// C [rpad][Bp] (fp64) given directly: H = coef o C (fp32 and bf16 hi/lo
+// transposed), the operand layout lr_finish produces from partials.
+__global__ void k_lr_coef(const double* __restrict__ Csrc, int rpad, int32_t Bp, const double* __restrict__ coef,
+                          float* H, __nv_bfloat16* Hhi, __nv_bfloat16* Hlo) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= (int64_t)rpad * Bp) return;
+    const int k = (int)(e / Bp), j = (int)(e % Bp);
+    const double h = coef[k] * Csrc[e];
+    H[e] = (float)h;
+    if (Hhi) {
+        const __nv_bfloat16 hi = __double2bfloat16(h);
+        const __nv_bfloat16 lo = __double2bfloat16(h - (double)__bfloat162float(hi));
+        Hhi[(int64_t)j * rpad + k] = hi;
+        Hlo[(int64_t)j * rpad + k] = lo;
     }
 }
 
@@ -783,6 +1026,15 @@ int lr_finish(hd_ctx* ctx, const LowRank& lr, int32_t Bp, const double* coef) {
     return HD_OK;
 }
 
+// H = coef o Csrc for a C kept from earlier (the operand of lr_expand)
+static int lr_coef(hd_ctx* ctx, const LowRank& lr, int32_t Bp, const double* coef, const double* Csrc) {
+    HD_PROF(ctx, "scalar");
+    const int64_t tot = (int64_t)lr.rpad * Bp;
+    k_lr_coef<<<ceil_div(tot, 256), 256, 0, ctx->stream>>>(Csrc, lr.rpad, Bp, coef, lr.H, lr.Hhi, lr.Hlo);
+    HD_CHECK_LAUNCH(ctx);
+    return HD_OK;
+}
+
 int lr_expand(hd_ctx* ctx, const LowRank& lr, int op, float* out, const float* Rv, const float* Pv, int64_t n,
               int32_t Bp, const ColState* st, const int* gate) {
     HD_PROF(ctx, "lr_expand");
@@ -933,25 +1185,27 @@ void engine_set_reduction(Engine& E) {
     E.nch = (E.n + E.rch - 1) / E.rch;
 }
 
-// Q = c1 P - c2 W P with the engine's slab width and segments (+ P^T Q partials)
-static int launch_spmm(Engine& E, float c1, float c2, float2* part, const ColState* st) {
+// Q = c1 V - c2 W V (V = P unless given) with the engine's slab width and
+// segments (+ P^T Q partials)
+static int launch_spmm(Engine& E, float c1, float c2, float2* part, const ColState* st, const float* V = nullptr) {
     hd_ctx* ctx = E.ctx;
     const hd_graph* g = E.g;
+    const float* Pin = V ? V : E.P;
     dim3 grid(E.vl.nblk, E.vl.slabs);
     {
         HD_PROF(ctx, "spmm");
         if (E.segK <= 1 && E.vl.S == 4 && E.warp_rows) {
-            k_spmm_w4<<<grid, 256, 0, ctx->stream>>>(g->row_ptr, g->col, g->val, E.P, E.Q, E.n, E.Bp, c1, c2, st);
+            k_spmm_w4<<<grid, 256, 0, ctx->stream>>>(g->row_ptr, g->col, g->val, Pin, E.Q, E.n, E.Bp, c1, c2, st);
             HD_CHECK_LAUNCH(ctx);
         } else if (E.segK <= 1) {
-            HD_DISPATCH_S(E.vl.S, (k_spmm<SS><<<grid, 256, 0, ctx->stream>>>(g->row_ptr, g->col, g->val, E.P, E.Q,
+            HD_DISPATCH_S(E.vl.S, (k_spmm<SS><<<grid, 256, 0, ctx->stream>>>(g->row_ptr, g->col, g->val, Pin, E.Q,
                                                                               E.n, E.Bp, c1, c2, st)));
             HD_CHECK_LAUNCH(ctx);
         } else {
             for (int s = 0; s < E.segK; ++s) {
                 const int32_t* lo = E.seg + (int64_t)s * E.n;
                 HD_DISPATCH_S(E.vl.S, (k_spmm_seg<SS><<<grid, 256, 0, ctx->stream>>>(
-                                          lo, lo + E.n, g->col, g->val, E.P, E.Q, E.n, E.Bp, c1, c2, st, s == 0)));
+                                          lo, lo + E.n, g->col, g->val, Pin, E.Q, E.n, E.Bp, c1, c2, st, s == 0)));
                 HD_CHECK_LAUNCH(ctx);
             }
         }
@@ -1113,30 +1367,39 @@ int engine_iteration(Engine& S_, int (*after_update)(void*), void* arg) {
 // Run `iters` CG iterations as one CUDA graph launch.  The graph is captured
 // on a private stream (the context's stream may be the legacy default stream,
 // which cannot be captured) and re-captured whenever anything the kernels take
-// as an argument differs from the cached capture.
+// as an argument differs from every cached capture.
 static uint64_t fbits(float f) {
     uint32_t u;
     memcpy(&u, &f, sizeof u);
     return u;
 }
 
+// Everything the iteration kernels take as arguments (the run length is added
+// by the caller).
+static std::vector<uint64_t> iteration_key(const Engine& E) {
+    return {(uint64_t)E.g, (uint64_t)E.ts, (uint64_t)(E.ts ? E.ts->off : nullptr), (uint64_t)(E.ts ? E.ts->ci : nullptr),
+            (uint64_t)(E.ts ? E.ts->wv : nullptr), (uint64_t)(E.ts ? E.ts->B : 0), (uint64_t)E.g->row_ptr,
+            (uint64_t)E.g->col, (uint64_t)E.g->val, (uint64_t)E.n, (uint64_t)E.lr.e,
+            (uint64_t)(E.has_lr ? E.lr.e->U : nullptr), (uint64_t)(E.has_lr ? E.lr.e->storage : -1),
+            (uint64_t)(E.has_lr ? E.lr.e->sp_rp : nullptr), (uint64_t)(E.has_lr ? E.lr.e->sp_cp : nullptr),
+            (uint64_t)E.R, (uint64_t)E.P, (uint64_t)E.Q, (uint64_t)E.X, (uint64_t)E.part, (uint64_t)E.st,
+            (uint64_t)E.num_active, (uint64_t)E.lr.part, (uint64_t)E.lr.C, (uint64_t)E.lr.H, (uint64_t)E.lr.Hhi,
+            (uint64_t)E.lr.Hlo, (uint64_t)E.dcoef, (uint64_t)E.opcoef, (uint64_t)E.segK, (uint64_t)E.seg,
+            (uint64_t)E.nch, (uint64_t)E.Bp, (uint64_t)E.vl.S, (uint64_t)E.vl.nblk, (uint64_t)E.vl.slabs,
+            (uint64_t)E.lr.nchunk, (uint64_t)E.lr.rpad, (uint64_t)E.lr.Bp16, (uint64_t)E.has_lr,
+            (uint64_t)E.eff_mode, (uint64_t)E.r, (uint64_t)E.max_iter, fbits(E.c1), fbits(E.c2), fbits(E.xs),
+            (uint64_t)E.ctx->stream};
+}
+
 static int run_iterations_graph(Engine& E, int iters) {
     hd_ctx* ctx = E.ctx;
-    std::vector<uint64_t> key = {
-        (uint64_t)E.g, (uint64_t)E.ts, (uint64_t)(E.ts ? E.ts->off : nullptr), (uint64_t)(E.ts ? E.ts->ci : nullptr),
-        (uint64_t)(E.ts ? E.ts->wv : nullptr), (uint64_t)(E.ts ? E.ts->B : 0), (uint64_t)E.g->row_ptr, (uint64_t)E.g->col, (uint64_t)E.g->val, (uint64_t)E.n, (uint64_t)E.lr.e,
-        (uint64_t)(E.has_lr ? E.lr.e->U : nullptr), (uint64_t)(E.has_lr ? E.lr.e->storage : -1),
-        (uint64_t)(E.has_lr ? E.lr.e->sp_rp : nullptr), (uint64_t)(E.has_lr ? E.lr.e->sp_cp : nullptr), (uint64_t)E.R, (uint64_t)E.P, (uint64_t)E.Q, (uint64_t)E.X,
-        (uint64_t)E.part, (uint64_t)E.st, (uint64_t)E.num_active, (uint64_t)E.lr.part, (uint64_t)E.lr.C,
-        (uint64_t)E.lr.H, (uint64_t)E.lr.Hhi, (uint64_t)E.lr.Hlo, (uint64_t)E.dcoef, (uint64_t)E.opcoef,
-        (uint64_t)E.segK, (uint64_t)E.seg, (uint64_t)E.nch, (uint64_t)E.Bp, (uint64_t)E.vl.S, (uint64_t)E.vl.nblk, (uint64_t)E.vl.slabs, (uint64_t)E.lr.nchunk,
-        (uint64_t)E.lr.rpad, (uint64_t)E.lr.Bp16, (uint64_t)E.has_lr, (uint64_t)E.eff_mode, (uint64_t)E.r,
-        (uint64_t)E.max_iter, (uint64_t)iters, fbits(E.c1), fbits(E.c2),
-        fbits(E.xs), (uint64_t)ctx->stream};
-    if (!ctx->iter_exec || key != ctx->iter_key) {
-        if (ctx->iter_exec) {
-            cudaGraphExecDestroy(ctx->iter_exec);
-            ctx->iter_exec = nullptr;
+    std::vector<uint64_t> key = iteration_key(E);
+    key.push_back((uint64_t)iters);
+    auto it = ctx->iter_graphs.find(key);
+    if (it == ctx->iter_graphs.end()) {
+        if (ctx->iter_graphs.size() >= 8) {
+            for (auto& kv : ctx->iter_graphs) cudaGraphExecDestroy(kv.second.exec);
+            ctx->iter_graphs.clear();
         }
         if (!ctx->cap_stream) HD_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
         cudaStream_t user = ctx->stream;
@@ -1158,18 +1421,16 @@ static int run_iterations_graph(Engine& E, int iters) {
             cudaGetLastError();
             return hd_fail(ctx, HD_ERR_CUDA, "iteration graph capture: %s", cudaGetErrorString(e));
         }
-        e = cudaGraphInstantiate(&ctx->iter_exec, graph, 0);
+        hd_ctx::IterGraph ig;
+        e = cudaGraphInstantiate(&ig.exec, graph, 0);
         cudaGraphDestroy(graph);
-        if (e != cudaSuccess) {
-            ctx->iter_exec = nullptr;
-            return hd_fail(ctx, HD_ERR_CUDA, "iteration graph instantiate: %s", cudaGetErrorString(e));
-        }
-        ctx->iter_launches = ctx->launches - l0;
+        if (e != cudaSuccess) return hd_fail(ctx, HD_ERR_CUDA, "iteration graph instantiate: %s", cudaGetErrorString(e));
+        ig.launches = ctx->launches - l0;
         ctx->launches = l0;
-        ctx->iter_key = key;
+        it = ctx->iter_graphs.emplace(key, ig).first;
     }
-    HD_CUDA(ctx, cudaGraphLaunch(ctx->iter_exec, ctx->stream));
-    ctx->launches += ctx->iter_launches;
+    HD_CUDA(ctx, cudaGraphLaunch(it->second.exec, ctx->stream));
+    ctx->launches += it->second.launches;
     return HD_OK;
 }
 
@@ -1183,24 +1444,162 @@ static bool graphs_enabled(hd_ctx* ctx) {
 }
 
 extern "C" int hd_query_batch(hd_ctx* ctx, const hd_graph* g, const hd_eig* eig, int mode, int32_t B,
-                              const int32_t* y_ptr, const int32_t* y_idx, const float* y_val, float alpha,
+                              const int32_t* y_ptr, const int32_t* y_idx, const float* y_val, double alpha,
                               const float* tol, int32_t max_iter, float* X, int32_t ldx, int32_t* iters,
                               float* relres, int32_t* status) {
     return hd_query_impl(ctx, g, nullptr, eig, mode, B, y_ptr, y_idx, y_val, alpha, tol, max_iter, X, ldx, iters,
                          relres, status);
 }
 
+// Iterate until no column is active: runs of iterations (CUDA graphs when
+// enabled), each followed by a poll of the active count and of the
+// tensor-core kernels' wait flags.  The first run is as long as the previous
+// solve with the same key took (at most 8), later runs 2, 4, 8, then 16
+// iterations, so a repeated workload polls once and launches no idle
+// iterations.  `ran` accumulates the iterations launched.
+static int iterate_until_stopped(Engine& E, int& ran) {
+    hd_ctx* ctx = E.ctx;
+    const std::vector<uint64_t> hkey = iteration_key(E);
+    const int first = (ctx->hint_key == hkey && ctx->iter_hint > 0) ? std::min(ctx->iter_hint, 8) : 4;
+    int run = 0, next = 2;
+    int active = 1;
+    int rc;
+    // every active column stops within max_iter iterations of its own; the
+    // bound only guards the host loop
+    const int64_t cap = (int64_t)(MAX_CONFIRM + 1) * E.max_iter + 8;
+    while (active > 0 && ran < cap) {
+        int todo = first;
+        if (run > 0) {
+            todo = next;
+            next = std::min(2 * next, 16);
+        }
+        if (graphs_enabled(ctx)) {
+            if ((rc = run_iterations_graph(E, todo))) return rc;
+        } else {
+            for (int t = 0; t < todo; ++t)
+                if ((rc = engine_iteration(E, nullptr, nullptr))) return rc;
+        }
+        ran += todo;
+        ++run;
+        HD_CUDA(ctx, cudaMemcpyAsync(ctx->h_poll, E.num_active, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+        HD_CUDA(ctx, cudaMemcpyAsync(ctx->h_poll + 8, ctx->d_flags + 2, 2 * sizeof(int), cudaMemcpyDeviceToHost,
+                                     ctx->stream));
+        HD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        active = ctx->h_poll[0];
+        if (ctx->h_poll[8] || ctx->h_poll[9]) return lr_tc_check_flags(ctx);
+    }
+    return HD_OK;
+}
+
+// T = b - A x into Q for every column (A the operator the solve iterates on,
+// applied to X; b = y, or y - U C_y for the projected form) and the partials
+// of ||T||^2 in E.part.  X holds the temporal term alone at this point.
+static int true_residual(Engine& E, double alpha) {
+    hd_ctx* ctx = E.ctx;
+    const int64_t n = E.n;
+    const int32_t Bp = E.Bp;
+    const double c1d = 1.0 / (1.0 - alpha), c2d = alpha / (1.0 - alpha);
+    const float c1 = (float)c1d, c2 = (float)c2d;
+    int rc;
+    dim3 grid(E.vl.nblk, E.vl.slabs);
+    if (E.ts) {
+        // Q = -L_a(W_j) x column by column (truncated systems), in two words
+        HD_PROF(ctx, "resid");
+        HD_DISPATCH_S(E.vl.S, (k_resid_cols<SS><<<grid, 256, 0, ctx->stream>>>(E.ts->off, E.ts->ci, E.ts->wv, E.ts->B,
+                                                                                E.X, E.Q, n, Bp, c1, c2)));
+        HD_CHECK_LAUNCH(ctx);
+    } else {
+        // Q = -L_a(W) x: the fp32 SpMM when its rounding bound is small against
+        // every column's tolerance, else the two-word kernel (k_resid_pick)
+        const hd_graph* g = E.g;
+        const double u = 1.0 / 16777216.0;
+        const double m = (double)g->max_row + 1.0;
+        const double gamma = m * u / (1.0 - m * u);
+        int* pick = E.num_active + 2;
+        if ((rc = launch_colsq(E, E.X))) return rc;
+        {
+            HD_PROF(ctx, "scalar");
+            HD_CUDA(ctx, cudaMemsetAsync(pick, 0, sizeof(int), ctx->stream));
+            k_resid_pick<<<Bp, 128, 0, ctx->stream>>>(E.part, (int)E.nch, Bp, E.B, E.st, gamma, c1d, c2d, pick);
+        }
+        HD_CHECK_LAUNCH(ctx);
+        HD_PROF(ctx, "resid");
+        HD_DISPATCH_S(E.vl.S, (k_spmm<SS><<<grid, 256, 0, ctx->stream>>>(g->row_ptr, g->col, g->val, E.X, E.Q, n, Bp,
+                                                                          -c1, -c2, nullptr, pick)));
+        HD_CHECK_LAUNCH(ctx);
+        HD_DISPATCH_S(E.vl.S, (k_resid<SS><<<grid, 256, 0, ctx->stream>>>(g->row_ptr, g->col, g->val, E.X, E.Q, n, Bp,
+                                                                           c1, c2, pick)));
+        HD_CHECK_LAUNCH(ctx);
+    }
+    if (E.has_lr && E.eff_mode != HD_MODE_PCG) {
+        // deflated operator: Q -= (a / (1 - a)) U (Lambda (U^T x))
+        if ((rc = lr_reduce(ctx, E.lr, E.X, n, Bp))) return rc;
+        if ((rc = lr_finish(ctx, E.lr, Bp, E.negop))) return rc;
+        if ((rc = lr_expand(ctx, E.lr, EXP_ADD_Q, E.Q, nullptr, nullptr, n, Bp, nullptr))) return rc;
+        if (E.eff_mode == HD_MODE_PROJ) {
+            // b = y - U (U^T y)
+            if ((rc = lr_coef(ctx, E.lr, Bp, E.ones, E.Cy))) return rc;
+            if ((rc = lr_expand(ctx, E.lr, EXP_SUB_R, E.Q, nullptr, nullptr, n, Bp, nullptr))) return rc;
+        }
+    }
+    k_scatter_y<<<ceil_div(E.B, 128), 128, 0, ctx->stream>>>(E.yp, E.yi, E.yv, E.B, n, Bp, E.Q, E.err);
+    HD_CHECK_LAUNCH(ctx);
+    return launch_colsq(E, E.Q);
+}
+
+// Restart the columns k_fin_confirm reactivated: r := T (in Q), a fresh
+// direction from it (p = M^-1 r with the preconditioner, p = r otherwise), and
+// for the deflated forms C = U^T p for the next operator application.
+static int restart_columns(Engine& E) {
+    hd_ctx* ctx = E.ctx;
+    const int64_t n = E.n;
+    const int32_t Bp = E.Bp;
+    int rc;
+    k_restart_copy<<<ceil_div(n * (Bp / 4), 256), 256, 0, ctx->stream>>>(E.R, E.Q, n, Bp, E.st);
+    HD_CHECK_LAUNCH(ctx);
+    if (E.eff_mode == HD_MODE_PCG) {
+        if ((rc = lr_reduce(ctx, E.lr, E.R, n, Bp))) return rc;
+        if ((rc = lr_finish(ctx, E.lr, Bp, E.dcoef))) return rc;
+        {
+            HD_PROF(ctx, "scalar");
+            k_fin_restart<<<Bp, 128, 0, ctx->stream>>>(E.st, E.lr.C, E.dcoef, E.r);
+        }
+        HD_CHECK_LAUNCH(ctx);
+        return lr_expand(ctx, E.lr, EXP_DIRECTION, E.P, E.R, E.P, n, Bp, E.st);
+    }
+    {
+        HD_PROF(ctx, "scalar");
+        k_fin_restart<<<Bp, 128, 0, ctx->stream>>>(E.st, nullptr, nullptr, 0);
+    }
+    HD_CHECK_LAUNCH(ctx);
+    {
+        HD_PROF(ctx, "direction");
+        dim3 grid(E.vl.nblk, E.vl.slabs);
+        HD_DISPATCH_S(E.vl.S, (k_direction<SS><<<grid, 256, 0, ctx->stream>>>(E.P, E.R, n, Bp, E.st)));
+        HD_CHECK_LAUNCH(ctx);
+    }
+    if (E.has_lr) {
+        if ((rc = lr_reduce(ctx, E.lr, E.P, n, Bp))) return rc;
+        if ((rc = lr_finish(ctx, E.lr, Bp, E.opcoef))) return rc;
+    }
+    return HD_OK;
+}
+
 // The solve behind hd_query_batch; with `ts` the operator is the per-column
 // truncated system (rows = shortlist positions) instead of the graph.
 int hd_query_impl(hd_ctx* ctx, const hd_graph* g, const TruncSys* ts, const hd_eig* eig, int mode, int32_t B,
-                  const int32_t* y_ptr, const int32_t* y_idx, const float* y_val, float alpha, const float* tol,
+                  const int32_t* y_ptr, const int32_t* y_idx, const float* y_val, double alpha, const float* tol,
                   int32_t max_iter, float* X, int32_t ldx, int32_t* iters, float* relres, int32_t* status) {
     if (!ctx || !g || !y_ptr || !tol || !X) return HD_ERR_INVALID_ARG;
     if (ts && eig) return hd_fail(ctx, HD_ERR_INVALID_ARG, "truncated systems take no eigenpairs");
     if (B <= 0 || ldx < B) return hd_fail(ctx, HD_ERR_INVALID_ARG, "B=%d ldx=%d", B, ldx);
-    if (!(alpha >= 0.0f && alpha < 1.0f)) return hd_fail(ctx, HD_ERR_INVALID_ARG, "alpha=%g not in [0,1)", alpha);
+    if (!(alpha >= 0.0 && alpha < 1.0)) return hd_fail(ctx, HD_ERR_INVALID_ARG, "alpha=%g not in [0,1)", alpha);
+    const bool temporal_only = (mode & HD_MODE_TEMPORAL_ONLY) != 0;
+    mode &= ~HD_MODE_TEMPORAL_ONLY;
     if (mode != HD_MODE_PAPER && mode != HD_MODE_PROJ && mode != HD_MODE_PCG)
         return hd_fail(ctx, HD_ERR_INVALID_ARG, "mode %d", mode);
+    if (temporal_only && mode == HD_MODE_PCG)
+        return hd_fail(ctx, HD_ERR_INVALID_ARG, "HD_MODE_TEMPORAL_ONLY needs the paper's or the projected form");
     if (max_iter < 0) return hd_fail(ctx, HD_ERR_INVALID_ARG, "max_iter %d", max_iter);
     if (eig && eig->n != g->n) return hd_fail(ctx, HD_ERR_INVALID_ARG, "eigenpairs for n=%lld, graph n=%lld",
                                               (long long)eig->n, (long long)g->n);
@@ -1245,8 +1644,8 @@ int hd_query_impl(hd_ctx* ctx, const hd_graph* g, const TruncSys* ts, const hd_e
                    ws_size(Bp * sizeof(ColState)) + ws_size(64) + ws_size((B + 1) * 4) + 2 * ws_size(nnz_y * 4 + 4) +
                    ws_size(B * 4);
     if (lr_on)
-        bytes += ws_size((size_t)nchunk * rpad * Bp * 4) + ws_size((size_t)rpad * Bp * 8) +
-                 ws_size((size_t)rpad * Bp * 4) + 2 * ws_size((size_t)Bp16 * rpad * 2) + 5 * ws_size(rpad * 8);
+        bytes += ws_size((size_t)nchunk * rpad * Bp * 4) + 2 * ws_size((size_t)rpad * Bp * 8) +
+                 ws_size((size_t)rpad * Bp * 4) + 2 * ws_size((size_t)Bp16 * rpad * 2) + 6 * ws_size(rpad * 8);
     void* ws;
     int rc = hd_ws_reserve(ctx, bytes, &ws);
     if (rc) return rc;
@@ -1268,6 +1667,9 @@ int hd_query_impl(hd_ctx* ctx, const hd_graph* g, const TruncSys* ts, const hd_e
     if ((rc = hd_stage_in(ctx, y_idx, (size_t)nnz_y * 4, d_yidx, &yi))) return rc;
     if ((rc = hd_stage_in(ctx, y_val, (size_t)nnz_y * 4, d_yval, &yv))) return rc;
     if ((rc = hd_stage_in(ctx, tol, (size_t)B * 4, d_tol, &tl))) return rc;
+    S_.yp = (const int32_t*)yp;
+    S_.yi = (const int32_t*)yi;
+    S_.yv = (const float*)yv;
     if (lr_on) {
         S_.lr.e = eig;
         S_.lr.rpad = rpad;
@@ -1275,6 +1677,7 @@ int hd_query_impl(hd_ctx* ctx, const hd_graph* g, const TruncSys* ts, const hd_e
         S_.lr.Bp16 = Bp16;
         S_.lr.part = cv.take<float>((size_t)nchunk * rpad * Bp);
         S_.lr.C = cv.take<double>((size_t)rpad * Bp);
+        S_.Cy = cv.take<double>((size_t)rpad * Bp);
         S_.lr.H = cv.take<float>((size_t)rpad * Bp);
         S_.lr.Hhi = cv.take<__nv_bfloat16>((size_t)Bp16 * rpad);
         S_.lr.Hlo = cv.take<__nv_bfloat16>((size_t)Bp16 * rpad);
@@ -1283,7 +1686,8 @@ int hd_query_impl(hd_ctx* ctx, const hd_graph* g, const TruncSys* ts, const hd_e
         S_.opcoef = cv.take<double>(rpad);
         S_.dcoef = cv.take<double>(rpad);
         S_.ones = cv.take<double>(rpad);
-        std::vector<double> gc(rpad, 0.0), hc(rpad, 0.0), oc(rpad, 0.0), dc(rpad, 0.0), on(rpad, 0.0);
+        S_.negop = cv.take<double>(rpad);
+        std::vector<double> gc(rpad, 0.0), hc(rpad, 0.0), oc(rpad, 0.0), dc(rpad, 0.0), on(rpad, 0.0), ng(rpad, 0.0);
         const double a = alpha;
         const double c3 = mode == HD_MODE_PROJ ? a : a / (1.0 - a);
         for (int k = 0; k < r; ++k) {
@@ -1294,17 +1698,29 @@ int hd_query_impl(hd_ctx* ctx, const hd_graph* g, const TruncSys* ts, const hd_e
             double lt = l > 0.0 ? l : 0.0;
             dc[k] = a * lt / (1.0 - a * lt);
             on[k] = 1.0;
+            ng[k] = -a / (1.0 - a) * l;
         }
         HD_CUDA(ctx, cudaMemcpyAsync(S_.gcoef, gc.data(), rpad * 8, cudaMemcpyHostToDevice, ctx->stream));
         HD_CUDA(ctx, cudaMemcpyAsync(S_.hcoef, hc.data(), rpad * 8, cudaMemcpyHostToDevice, ctx->stream));
         HD_CUDA(ctx, cudaMemcpyAsync(S_.opcoef, oc.data(), rpad * 8, cudaMemcpyHostToDevice, ctx->stream));
         HD_CUDA(ctx, cudaMemcpyAsync(S_.dcoef, dc.data(), rpad * 8, cudaMemcpyHostToDevice, ctx->stream));
         HD_CUDA(ctx, cudaMemcpyAsync(S_.ones, on.data(), rpad * 8, cudaMemcpyHostToDevice, ctx->stream));
+        HD_CUDA(ctx, cudaMemcpyAsync(S_.negop, ng.data(), rpad * 8, cudaMemcpyHostToDevice, ctx->stream));
         HD_CUDA(ctx, cudaMemsetAsync(S_.lr.Hhi, 0, (size_t)Bp16 * rpad * 2, ctx->stream));
         HD_CUDA(ctx, cudaMemsetAsync(S_.lr.Hlo, 0, (size_t)Bp16 * rpad * 2, ctx->stream));
     }
 
     // ---------------- setup
+    if (!ts && g->max_row < 0) {
+        // the longest row bounds the rounding of the true residual (k_resid_pick)
+        HD_CUDA(ctx, cudaMemsetAsync(S_.num_active, 0, sizeof(int), ctx->stream));
+        k_max_row<<<std::min<int64_t>(ceil_div(n, 256), (int64_t)ctx->num_sms * 8), 256, 0, ctx->stream>>>(
+            g->row_ptr, n, S_.num_active);
+        HD_CHECK_LAUNCH(ctx);
+        HD_CUDA(ctx, cudaMemcpyAsync(ctx->h_poll, S_.num_active, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+        HD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        g->max_row = ctx->h_poll[0];
+    }
     S_.vl = vec_launch(ctx, n, Bp, ts ? pick_slab(Bp) : tune_slab(ctx, g, Bp, S_.P, S_.Q));
     if (!ts && (rc = tune_segments(ctx, S_))) return rc;
     const int eff_mode = lr_on ? mode : HD_MODE_PAPER;
@@ -1312,12 +1728,14 @@ int hd_query_impl(hd_ctx* ctx, const hd_graph* g, const TruncSys* ts, const hd_e
     float c1, c2, xs = 1.0f;
     if (eff_mode == HD_MODE_PROJ) {
         c1 = 1.0f;
-        c2 = alpha;
+        c2 = (float)a;
         xs = (float)(1.0 - a);
     } else {
         c1 = (float)(1.0 / (1.0 - a));
         c2 = (float)(a / (1.0 - a));
     }
+    // X accumulates the temporal term alone; the spectral term is added after
+    // the true-residual confirmation
     HD_CUDA(ctx, cudaMemsetAsync(S_.R, 0, vec, ctx->stream));
     HD_CUDA(ctx, cudaMemsetAsync(S_.X, 0, vec, ctx->stream));
     HD_CUDA(ctx, cudaMemsetAsync(S_.err, 0, sizeof(int), ctx->stream));
@@ -1325,6 +1743,7 @@ int hd_query_impl(hd_ctx* ctx, const hd_graph* g, const TruncSys* ts, const hd_e
                                                            B, n, Bp, S_.R, S_.err);
     HD_CHECK_LAUNCH(ctx);
     const double* Cd = lr_on ? S_.lr.C : nullptr;
+    const size_t cbytes = (size_t)rpad * Bp * sizeof(double);
     if (eff_mode == HD_MODE_PAPER) {
         if ((rc = launch_colsq(S_, S_.R))) return rc;
         HD_CUDA(ctx, cudaMemsetAsync(S_.num_active, 0, sizeof(int), ctx->stream));
@@ -1333,17 +1752,16 @@ int hd_query_impl(hd_ctx* ctx, const hd_graph* g, const TruncSys* ts, const hd_e
         HD_CHECK_LAUNCH(ctx);
         HD_CUDA(ctx, cudaMemcpyAsync(S_.P, S_.R, vec, cudaMemcpyDeviceToDevice, ctx->stream));
         if (lr_on) {
-            // x^s = U g(Lambda) U^T y (Eq. 18); C = U^T P for the first operator
+            // C = U^T y: kept for x^s = U g(Lambda) C (Eq. 18), and U^T P for the first operator
             if ((rc = lr_reduce(ctx, S_.lr, S_.R, n, Bp))) return rc;
-            if ((rc = lr_finish(ctx, S_.lr, Bp, S_.gcoef))) return rc;
-            if ((rc = lr_expand(ctx, S_.lr, EXP_SET_X, S_.X, nullptr, nullptr, n, Bp, S_.st))) return rc;
             if ((rc = lr_finish(ctx, S_.lr, Bp, S_.opcoef))) return rc;
+            HD_CUDA(ctx, cudaMemcpyAsync(S_.Cy, S_.lr.C, cbytes, cudaMemcpyDeviceToDevice, ctx->stream));
         }
     } else if (eff_mode == HD_MODE_PROJ) {
+        // C = U^T y (kept); b = y - U C
         if ((rc = lr_reduce(ctx, S_.lr, S_.R, n, Bp))) return rc;
-        if ((rc = lr_finish(ctx, S_.lr, Bp, S_.hcoef))) return rc;
-        if ((rc = lr_expand(ctx, S_.lr, EXP_SET_X, S_.X, nullptr, nullptr, n, Bp, S_.st))) return rc;
         if ((rc = lr_finish(ctx, S_.lr, Bp, S_.ones))) return rc;
+        HD_CUDA(ctx, cudaMemcpyAsync(S_.Cy, S_.lr.C, cbytes, cudaMemcpyDeviceToDevice, ctx->stream));
         if ((rc = lr_expand(ctx, S_.lr, EXP_SUB_R, S_.R, nullptr, nullptr, n, Bp, S_.st))) return rc;
         if ((rc = launch_colsq(S_, S_.R))) return rc;
         HD_CUDA(ctx, cudaMemsetAsync(S_.num_active, 0, sizeof(int), ctx->stream));
@@ -1365,53 +1783,62 @@ int hd_query_impl(hd_ctx* ctx, const hd_graph* g, const TruncSys* ts, const hd_e
         if ((rc = lr_expand(ctx, S_.lr, EXP_DIRECTION, S_.P, S_.R, S_.P, n, Bp, S_.st))) return rc;
     }
 
-    // ---------------- iterations
+    // ---------------- iterations, then confirmation by the true residual
     S_.eff_mode = eff_mode;
     S_.c1 = c1;
     S_.c2 = c2;
     S_.xs = xs;
     S_.r = r;
     S_.max_iter = max_iter;
-    const int poll_every = 4;
-    int it = 0;
     HD_CUDA(ctx, cudaMemcpyAsync(ctx->h_poll, S_.num_active, 2 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     HD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     if (ctx->h_poll[1])
         return hd_fail(ctx, HD_ERR_INVALID_ARG, "bad observation: index out of range, non-finite value or bad y_ptr");
     int active = ctx->h_poll[0];
-    while (active > 0 && it < max_iter) {
-        const int todo = std::min(poll_every, max_iter - it);
-        if (todo == poll_every && graphs_enabled(ctx)) {
-            if ((rc = run_iterations_graph(S_, todo))) return rc;
-        } else {
-            for (int t = 0; t < todo; ++t)
-                if ((rc = engine_iteration(S_, nullptr, nullptr))) return rc;
+    int ran = 0, first_ran = -1;
+    std::vector<ColState> hs(B);
+    for (int round = 0; round <= MAX_CONFIRM; ++round) {
+        if (active > 0 && max_iter > 0 && (rc = iterate_until_stopped(S_, ran))) return rc;
+        if (first_ran < 0) first_ran = ran;
+        if ((rc = true_residual(S_, a))) return rc;
+        {
+            HD_PROF(ctx, "scalar");
+            HD_CUDA(ctx, cudaMemsetAsync(S_.num_active, 0, sizeof(int), ctx->stream));
+            k_fin_confirm<<<Bp, 128, 0, ctx->stream>>>(S_.part, (int)S_.nch, Bp, B, S_.st, max_iter, S_.num_active);
         }
-        it += todo;
+        HD_CHECK_LAUNCH(ctx);
         HD_CUDA(ctx, cudaMemcpyAsync(ctx->h_poll, S_.num_active, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-        // the tensor-core kernels' wait flags ride along with the poll
-        HD_CUDA(ctx, cudaMemcpyAsync(ctx->h_poll + 8, ctx->d_flags + 2, 2 * sizeof(int), cudaMemcpyDeviceToHost,
-                                     ctx->stream));
+        HD_CUDA(ctx, cudaMemcpyAsync(hs.data(), S_.st, B * sizeof(ColState), cudaMemcpyDeviceToHost, ctx->stream));
         HD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
         active = ctx->h_poll[0];
-        if (ctx->h_poll[8] || ctx->h_poll[9]) return lr_tc_check_flags(ctx);
+        if (active == 0) break;
+        if ((rc = restart_columns(S_))) return rc;
+    }
+    // the next solve with the same key polls first after as many iterations as
+    // this one's columns took before any restart (without restarts the
+    // columns' own count, else the iterations launched)
+    int most = 0;
+    for (int j = 0; j < B; ++j) most = std::max(most, hs[j].iters);
+    ctx->hint_key = iteration_key(S_);
+    ctx->iter_hint = ran == first_ran ? most : first_ran;
+    for (int j = 0; j < B; ++j) {
+        if (iters && !hd_is_device_ptr(iters)) iters[j] = hs[j].iters;
+        if (relres && !hd_is_device_ptr(relres)) relres[j] = hs[j].bb > 0 ? (float)std::sqrt(hs[j].rr / hs[j].bb) : 0.f;
+        if (status && !hd_is_device_ptr(status)) status[j] = hs[j].status;
+    }
+    // ---------------- spectral term (Eq. 17-18): X += U g(Lambda) U^T y, or U h(Lambda) U^T y (projected form)
+    if (lr_on && eff_mode != HD_MODE_PCG && !temporal_only) {
+        if ((rc = lr_coef(ctx, S_.lr, Bp, eff_mode == HD_MODE_PAPER ? S_.gcoef : S_.hcoef, S_.Cy))) return rc;
+        if ((rc = lr_expand(ctx, S_.lr, EXP_ADD_Q, S_.X, nullptr, nullptr, n, Bp, nullptr))) return rc;
     }
 
     // ---------------- outputs
-    k_outputs<<<ceil_div(B, 128), 128, 0, ctx->stream>>>(S_.st, B, hd_is_device_ptr(iters) ? iters : nullptr,
-                                                         hd_is_device_ptr(relres) ? relres : nullptr,
-                                                         hd_is_device_ptr(status) ? status : nullptr);
-    HD_CHECK_LAUNCH(ctx);
-    if ((iters && !hd_is_device_ptr(iters)) || (relres && !hd_is_device_ptr(relres)) ||
-        (status && !hd_is_device_ptr(status))) {
-        std::vector<ColState> hs(B);
-        HD_CUDA(ctx, cudaMemcpyAsync(hs.data(), S_.st, B * sizeof(ColState), cudaMemcpyDeviceToHost, ctx->stream));
-        HD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-        for (int j = 0; j < B; ++j) {
-            if (iters && !hd_is_device_ptr(iters)) iters[j] = hs[j].iters;
-            if (relres && !hd_is_device_ptr(relres)) relres[j] = hs[j].bb > 0 ? (float)std::sqrt(hs[j].rr / hs[j].bb) : 0.f;
-            if (status && !hd_is_device_ptr(status)) status[j] = hs[j].status;
-        }
+    if ((iters && hd_is_device_ptr(iters)) || (relres && hd_is_device_ptr(relres)) ||
+        (status && hd_is_device_ptr(status))) {
+        k_outputs<<<ceil_div(B, 128), 128, 0, ctx->stream>>>(S_.st, B, hd_is_device_ptr(iters) ? iters : nullptr,
+                                                             hd_is_device_ptr(relres) ? relres : nullptr,
+                                                             hd_is_device_ptr(status) ? status : nullptr);
+        HD_CHECK_LAUNCH(ctx);
     }
     if (!x_direct) {
         if (hd_is_device_ptr(X)) {
@@ -1423,6 +1850,7 @@ int hd_query_impl(hd_ctx* ctx, const hd_graph* g, const TruncSys* ts, const hd_e
             HD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
         }
     }
+    if (lr_on && lr_use_tensor_cores(eig)) return lr_tc_check_flags(ctx);
     return HD_OK;
 }
 

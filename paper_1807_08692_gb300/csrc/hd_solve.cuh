@@ -16,6 +16,8 @@ struct ColState {
     int status;
     int fresh;      // 1: the column was just (re)admitted; the update resets it and
                     // the next scalar step starts its iteration from r0 = y (bb given)
+    int confirms;   // residual replacements so far (true residual above tol at a stop)
+    int restart;    // 1: r was just replaced by b - A x; the direction restarts from it
 };
 
 // Low-rank product helpers (storage-specific implementations).
@@ -99,6 +101,12 @@ struct Engine {
     ColState* st = nullptr;
     int* num_active = nullptr;
     int* err = nullptr;
+    // the staged observations (device), scattered again for the true residual
+    const int32_t* yp = nullptr;
+    const int32_t* yi = nullptr;
+    const float* yv = nullptr;
+    double* Cy = nullptr;       // U^T y [rpad][Bp] (paper and projected forms: x^s and b)
+    double* negop = nullptr;    // -(a / (1 - a)) lambda: the deflation term of -L_a(W_r)
     LowRank lr{};
     bool has_lr = false;
     double *gcoef = nullptr, *hcoef = nullptr, *opcoef = nullptr, *dcoef = nullptr, *ones = nullptr;
@@ -121,5 +129,5 @@ int engine_iteration(Engine& E, int (*after_update)(void*), void* arg);
 int reduction_chunk_rows(int64_t n);
 void engine_set_reduction(Engine& E);
 int hd_query_impl(hd_ctx* ctx, const hd_graph* g, const TruncSys* ts, const hd_eig* eig, int mode, int32_t B,
-                  const int32_t* y_ptr, const int32_t* y_idx, const float* y_val, float alpha, const float* tol,
+                  const int32_t* y_ptr, const int32_t* y_idx, const float* y_val, double alpha, const float* tol,
                   int32_t max_iter, float* X, int32_t ldx, int32_t* iters, float* relres, int32_t* status);

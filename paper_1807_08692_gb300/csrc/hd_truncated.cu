@@ -179,7 +179,7 @@ __global__ void k_scan_apply(const int32_t* in, int64_t count, const int64_t* bo
 
 extern "C" int hd_temporal_truncated(hd_ctx* ctx, const hd_graph* g, int32_t B, const int32_t* sl_ptr,
                                      const int32_t* sl_idx, const int32_t* y_ptr, const int32_t* y_idx,
-                                     const float* y_val, float alpha, const float* tol, int32_t max_iter, float* X,
+                                     const float* y_val, double alpha, const float* tol, int32_t max_iter, float* X,
                                      int32_t ldx, int32_t* iters, float* relres, int32_t* status) {
     if (!ctx || !g || !sl_ptr || !sl_idx || !y_ptr || !tol || !X || B <= 0 || B > 4096) return HD_ERR_INVALID_ARG;
     HD_CUDA(ctx, cudaSetDevice(ctx->device));

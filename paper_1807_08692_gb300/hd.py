@@ -26,9 +26,11 @@ PENDING = -6
 F32, BF16, FP8 = 0, 1, 2
 SYM_UNION, SYM_MUTUAL = 0, 1
 MODE_PAPER, MODE_PROJ, MODE_PCG = 0, 1, 2
-COL_CONVERGED, COL_MAX_ITER, COL_BREAKDOWN, COL_EMPTY = 0, 1, 2, 3
+MODE_TEMPORAL_ONLY = 0x100
+COL_CONVERGED, COL_MAX_ITER, COL_BREAKDOWN, COL_EMPTY, COL_CANCELLED, COL_STAGNATED = 0, 1, 2, 3, 4, 5
 
-MODES = {"paper": MODE_PAPER, "proj": MODE_PROJ, "pcg": MODE_PCG}
+MODES = {"paper": MODE_PAPER, "proj": MODE_PROJ, "pcg": MODE_PCG,
+         "paper_temporal": MODE_PAPER | MODE_TEMPORAL_ONLY, "proj_temporal": MODE_PROJ | MODE_TEMPORAL_ONLY}
 STORAGES = {"f32": F32, "bf16": BF16, "fp8": FP8}
 
 _lib = None
@@ -41,6 +43,7 @@ _SIGS = {
     "hd_destroy": (C.c_int, [vp]),
     "hd_last_error": (C.c_char_p, [vp]),
     "hd_launch_count": (i64, [vp]),
+    "hd_workspace_bytes": (C.c_int, [vp, C.POINTER(C.c_size_t)]),
     "hd_num_sms": (C.c_int, [vp]),
     "hd_profile_enable": (C.c_int, [vp, C.c_int]),
     "hd_profile_read": (C.c_int, [vp, C.c_char_p, C.POINTER(i64), C.POINTER(f64), C.POINTER(i64)]),
@@ -57,6 +60,7 @@ _SIGS = {
     "hd_spectrum_min": (C.c_int, [vp, vp, f64, i32, u64, C.POINTER(f64)]),
     "hd_cg_bound": (C.c_int, [C.c_int, f64, f64, f64, f64, C.POINTER(f64), C.POINTER(i32), C.POINTER(i32)]),
     "hd_eig_info": (C.c_int, [vp, C.POINTER(i32), C.POINTER(C.c_int)]),
+    "hd_eig_restarts": (C.c_int, [vp, C.POINTER(i32)]),
     "hd_eig_sparsify": (C.c_int, [vp, vp, f64, C.POINTER(vp)]),
     "hd_filter_poly": (C.c_int, [vp, vp, vp, i32, vp, vp, vp, vp, i32, vp, i32]),
     "hd_selftest_wait": (C.c_int, [vp, C.c_uint32, vp]),
@@ -64,15 +68,15 @@ _SIGS = {
     "hd_graph_load": (C.c_int, [vp, C.c_char_p, C.POINTER(vp)]),
     "hd_eig_save": (C.c_int, [vp, vp, C.c_char_p]),
     "hd_eig_load": (C.c_int, [vp, C.c_char_p, C.POINTER(vp)]),
-    "hd_temporal_truncated": (C.c_int, [vp, vp, i32, vp, vp, vp, vp, vp, f32, vp, i32, vp, i32, vp, vp, vp]),
+    "hd_temporal_truncated": (C.c_int, [vp, vp, i32, vp, vp, vp, vp, vp, f64, vp, i32, vp, i32, vp, vp, vp]),
     "hd_eig_nnz": (C.c_int, [vp, C.POINTER(C.c_int64)]),
     "hd_eig_export": (C.c_int, [vp, vp, vp, vp]),
     "hd_eig_destroy": (C.c_int, [vp]),
-    "hd_query_batch": (C.c_int, [vp, vp, vp, C.c_int, i32, vp, vp, vp, f32, vp, i32, vp, i32, vp, vp, vp]),
+    "hd_query_batch": (C.c_int, [vp, vp, vp, C.c_int, i32, vp, vp, vp, f64, vp, i32, vp, i32, vp, vp, vp]),
     "hd_rank": (C.c_int, [vp, vp, i64, i32, i32, vp, i32, i32, vp, vp]),
     "hd_eig_project": (C.c_int, [vp, vp, vp, i32, vp]),
     "hd_rank_static": (C.c_int, [vp, vp, i64, i32, i32, vp, i32, vp, vp]),
-    "hd_serve_open": (C.c_int, [vp, vp, vp, C.c_int, f32, i32, C.c_size_t, i32, i32, C.POINTER(vp)]),
+    "hd_serve_open": (C.c_int, [vp, vp, vp, C.c_int, f64, i32, C.c_size_t, i32, i32, C.POINTER(vp)]),
     "hd_serve_slots": (C.c_int, [vp]),
     "hd_serve_submit": (C.c_int, [vp, i32, vp, vp, f32, i32, C.POINTER(u64)]),
     "hd_serve_step": (C.c_int, [vp, i32, C.POINTER(i32)]),
@@ -172,6 +176,12 @@ class Context:
     def launches(self) -> int:
         return int(lib().hd_launch_count(self._h))
 
+    def workspace_bytes(self) -> int:
+        """Device workspace the context holds (hd_workspace_bytes)."""
+        b = C.c_size_t()
+        self.check(lib().hd_workspace_bytes(self._h, C.byref(b)), "hd_workspace_bytes")
+        return int(b.value)
+
     def num_sms(self) -> int:
         return int(lib().hd_num_sms(self._h))
 
@@ -253,6 +263,13 @@ class Eig:
     @property
     def handle(self):
         return self._h
+
+    @property
+    def restarts(self) -> int:
+        """Thick restarts of the Lanczos run that computed these eigenpairs (-1 otherwise)."""
+        v = i32()
+        lib().hd_eig_restarts(self._h, C.byref(v))
+        return v.value
 
     @property
     def nnz(self) -> int:

@@ -24,13 +24,26 @@ def test_truncated_matches_oracle(gpu_ctx, cfg1_data):
     sizes = [300, 150, 2000, 17, 64, 1000, 500, 300, 10, 700, 300, 301, 299, 1500, 250, 128][:B]
     sls, sl_ptr, sl_idx = _case(cfg1_data, sizes)
     args = y_arrays(cfg1_data["yp"], cfg1_data["yi"], cfg1_data["yv"])
-    Xg, it, rr, st = hd.temporal_truncated(gpu_ctx, g, sl_ptr, sl_idx, *args, 0.99, 1e-6, 1000)
-    assert np.all(st == 0)
+    tol = 1e-6
+    Xg, it, rr, st = hd.temporal_truncated(gpu_ctx, g, sl_ptr, sl_idx, *args, 0.99, tol, 1000)
     Xg = Xg.cpu().numpy().astype(np.float64)
     for j in range(B):
         s = sizes[j]
         ref, _ = T.temporal_truncated(cfg1_data["A"], sls[j], cfg1_data["Y"][:, j], 0.99, 1e-12, 5000)
         assert rel_l2_cols(Xg[:s, j:j + 1], ref[:, None]).max() <= 1e-4, j
+        # A column stops when its true residual meets tol.  On a small subgraph
+        # x is about as large as y, and the exact solution rounded to fp32
+        # already leaves a residual near c1 u ||x|| (~1e-6 of ||y||): there the
+        # solver reports STAGNATED, and only where fp32 cannot do much better.
+        W_S, _ = T.subsystem(cfg1_data["A"], sls[j])
+        y_S = cfg1_data["Y"][sls[j], j]
+        xr = ref.astype(np.float32).astype(np.float64)
+        floor = np.linalg.norm(y_S - (xr - 0.99 * (W_S @ xr)) / 0.01) / np.linalg.norm(y_S)
+        if st[j] == hd.hd.COL_CONVERGED:
+            assert rr[j] <= tol, (j, rr[j])
+        else:
+            assert st[j] == hd.hd.COL_STAGNATED and floor > 0.3 * tol, (j, st[j], rr[j], floor)
+            assert rr[j] <= 10 * floor, (j, rr[j], floor)
         assert np.all(Xg[s:, j] == 0.0)
         if s == 2000:
             # the whole graph: plain temporal filtering, in shortlist order
