@@ -66,9 +66,10 @@ def parse():
     ap.add_argument("--shortlist", type=int, default=75000, help="Temporal† shortlist size (0: skip the leg)")
     ap.add_argument("--sweep-r400", type=int, default=1, help="add an r=400 leg (its own Lanczos) to the sweep")
     ap.add_argument("--trunc-iters", type=int, default=20, help="Temporal† CG iterations (Table 1: 20)")
-    ap.add_argument("--converged-restarts", type=int, default=0,
-                    help="with N > 0: a second Lanczos run to residual 1e-5 (at most N restarts) and the paper's "
-                         "form on its fp32 eigenpairs")
+    ap.add_argument("--converged-r", type=int, default=1,
+                    help="rank of the eigenpairs converged to residual 1e-5 for the paper's-form leg (0: skip)")
+    ap.add_argument("--converged-restarts", type=int, default=30,
+                    help="restart limit of that Lanczos run")
     return ap.parse_args()
 
 
@@ -308,8 +309,8 @@ def e2e_leg(ctx, wl, eig, mode, tol, alpha, K, B, topk):
 # k_spmm<32> on a 1M-node k=50 graph (d=256 descriptors, nnz 62,097,728), B=64.
 # Scaled to another graph by nnz (the gathered rows dominate); reported only
 # while the kernel source still hashes to the value the counters were taken on.
-SPMM_NCU = {"dram_bytes": 8462809472, "nnz": 62097728, "n": 1000000, "B": 64, "slab": 32,
-            "src_sha1": "55339a05c6f234407debb153ac0af3e0791dc770"}
+SPMM_NCU = {"dram_bytes": 8459339520, "nnz": 62097728, "n": 1000000, "B": 64, "slab": 32,
+            "src_sha1": "d01dab0cce2e78da4f6fc10ddfbd1c6150778947"}
 
 
 def spmm_source_sha1():
@@ -478,7 +479,7 @@ def sweep_leg(ctx, wl, args, alpha):
             e = hd.eig_from_host(ctx, g, lam, U32, st)
             run(f"pcg r={r} {st}", e, "pcg", args.batch, r=r, storage=st)
             e.close()
-        for r2 in sorted({min(50, r), min(100, r)}):
+        for r2 in sorted({1, min(50, r), min(100, r)}):
             if r2 == r:
                 continue
             e = hd.eig_from_host(ctx, g, lam[:r2], np.ascontiguousarray(U32[:, :r2]), "bf16")
@@ -501,18 +502,21 @@ def sweep_leg(ctx, wl, args, alpha):
         run(f"paper r={r} {args.storage} sparse 0.99", es, "paper", args.batch, r=r, storage=args.storage,
             sparsity=0.99, u_nnz=es.nnz)
         es.close()
-        if args.converged_restarts > 0:
+        rc_ = args.converged_r
+        if rc_ > 0:
             # Theorem 1 (Eq. 15) holds for exact eigenpairs: the paper's form on
-            # eigenpairs converged to ||W u - l u|| <= 1e-5, stored in fp32
+            # eigenpairs converged to ||W u - l u|| <= 1e-5, stored in fp32.  On
+            # this graph only lambda_1 = 1 is isolated (lambda_2 .. lambda_200 lie
+            # within 0.002 of each other), so the default rank is 1.
             t0 = time.time()
-            ec, lamc, resc, convc = hd.eigendecompose(ctx, g, r, block=32, tol=1e-5,
+            ec, lamc, resc, convc = hd.eigendecompose(ctx, g, rc_, block=32, tol=1e-5,
                                                       max_restarts=args.converged_restarts, storage="f32")
             t_c = time.time() - t0
-            info = dict(r=r, storage="f32", lanczos_s=round(t_c, 1), lanczos_restarts=ec.restarts,
+            info = dict(r=rc_, storage="f32", lanczos_s=round(t_c, 1), lanczos_restarts=ec.restarts,
                         lanczos_converged=bool(convc), lanczos_max_resid=float(np.max(resc)),
                         lambda_r=round(float(lamc[-1]), 5))
-            run(f"paper r={r} f32 converged", ec, "paper", args.batch, **info)
-            run(f"pcg r={r} f32 converged", ec, "pcg", args.batch, **info)
+            run(f"paper r={rc_} f32 converged", ec, "paper", args.batch, **info)
+            run(f"pcg r={rc_} f32 converged", ec, "pcg", args.batch, **info)
             ec.close()
     for b in [int(x) for x in args.sweep_batches.split(",") if x]:
         run(f"{args.mode} r={args.r} B={b}", wl["eig"], args.mode, b, r=args.r, storage=args.storage)

@@ -398,7 +398,8 @@ typedef struct hd_req_stats {
     double done_s;      /* when its ranking had been copied to the host */
     int32_t iters;      /* CG iterations the request used */
     int32_t status;     /* HD_COL_* */
-    float relres;       /* final relative residual ||r|| / ||y|| */
+    float relres;       /* final relative residual ||r|| / ||y|| of the recursion: a served
+                           column stops on it (no separate b - A x pass per retirement) */
     int32_t slot;       /* batch column it ran in (narrow-lane columns follow the wide ones) */
 } hd_req_stats;
 

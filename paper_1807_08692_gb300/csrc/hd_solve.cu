@@ -370,7 +370,7 @@ __global__ void k_seg_bounds(const int32_t* __restrict__ rp, const int32_t* __re
 // in one range of the nodes, so that range stays in L2 for the pass.  The
 // first segment writes Q, the others subtract into it.
 template <int S>
-__global__ void __launch_bounds__(256) k_spmm_seg(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
+__global__ void __launch_bounds__(256, 8) k_spmm_seg(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
                                                   const int32_t* __restrict__ ci, const float* __restrict__ wv,
                                                   const float* __restrict__ P, float* __restrict__ Q, int64_t n,
                                                   int32_t ld, float c1, float c2, const ColState* __restrict__ st,
@@ -402,11 +402,23 @@ __global__ void __launch_bounds__(256) k_spmm_seg(const int32_t* __restrict__ lo
                 FMA4(s2, w[u + 1], v[u + 1]);
             }
         }
-        for (; t < e; ++t) {
-            const int32_t j0 = __ldg(ci + t);
-            const float w0 = __ldg(wv + t);
-            const float4 v0 = ld4(P + (int64_t)j0 * ld + col);
-            FMA4(s, w0, v0);
+        // the last e - t < 8 entries as in k_spmm (a row's part in one node
+        // range is short, ~nnz/(n K) entries, so this tail is a large share)
+        for (; t < e; t += 4) {
+            const int m = e - t;
+            float4 v[4];
+            float w[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                w[u] = u < m ? __ldg(wv + t + u) : 0.f;
+                v[u] = u < m ? ld4(P + (int64_t)__ldg(ci + t + u) * ld + col) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (u < m) {
+                    FMA4(s, w[u], v[u]);
+                }
+            }
         }
         s.x += s2.x;
         s.y += s2.y;
