@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--shortlist", type=int, default=75000, help="Temporal† shortlist size (0: skip the leg)")
     ap.add_argument("--sweep-r400", type=int, default=1, help="add an r=400 leg (its own Lanczos) to the sweep")
     ap.add_argument("--trunc-iters", type=int, default=20, help="Temporal† CG iterations (Table 1: 20)")
+    ap.add_argument("--small-leg", type=int, default=1,
+                    help="time the 2,000-node clustered workload (d=128; r=50 against r=0) as well")
     ap.add_argument("--converged-r", type=int, default=1,
                     help="rank of the eigenpairs converged to residual 1e-5 for the paper's-form leg (0: skip)")
     ap.add_argument("--converged-restarts", type=int, default=30,
@@ -524,6 +526,51 @@ def sweep_leg(ctx, wl, args, alpha):
     return out
 
 
+def small_leg(ctx, args, alpha):
+    """The 2,000-node workload (d=128, 20 vMF components, k=30, 16 queries, top-10
+    observations): real clusters, so lambda_2 .. lambda_20 sit near 0.6-0.7 and the
+    hybrid's rank matters.  Graph on the device, eigenpairs by Lanczos; both legs
+    calibrated against the oracle's fp64 CG like the headline."""
+    import torch
+    import paper_1807_08692_gb300 as hd
+    import synth
+    from oracle import diffusion, observe
+    c = synth.get_config("cfg1")
+    X, _ = synth.database(c.seed, c.n, c.d, c.ncl, c.kappa_lo, c.kappa_hi, c.sizes)
+    Q = synth.queries(c.seed, 2 * c.batch, c.d, c.ncl, c.kappa_lo, c.kappa_hi, c.sizes)
+    Xt = torch.from_numpy(np.ascontiguousarray(X, np.float32)).cuda()
+    Qt = torch.from_numpy(np.ascontiguousarray(Q, np.float32)).cuda()
+    g = hd.build_graph(ctx, Xt, c.k, c.gamma)
+    yp, yi, yv = hd.observe(ctx, Xt, Qt, c.k_y, c.gamma)
+    B = c.batch
+    sub = {"n": c.n, "g": g, "pool": 0, "yall": (yp, yi, yv), "bmax": B}
+    sub["cal"], sub["tim"] = split_batches(sub["yall"], B, B)
+    rp, col, val, _ = g.export()
+    import scipy.sparse as sp
+    W = sp.csr_matrix((val.astype(np.float64), col, rp), shape=(c.n, c.n))
+
+    def dense(batch):
+        p, i, v = batch
+        return observe.dense(c.n, p, i, v.astype(np.float64))
+
+    Y = np.hstack([dense(sub["cal"]), dense(sub["tim"])])
+    Xr, _, _ = diffusion.cg_columns(diffusion.laplacian_op(W, alpha), Y, 1e-12, 5000)
+    sub["ref_cal"], sub["ref_tim"] = Xr[:, :B], Xr[:, B:]
+    eig, lam, res, conv = hd.eigendecompose(ctx, g, 50, block=16, tol=1e-5, max_restarts=50, storage="bf16")
+    out = {"workload": f"{c.name}: n={c.n}, d={c.d}, k={c.k}, nnz={g.nnz}, B={B}", "lambda_2": round(float(lam[1]), 4),
+           "lambda_50": round(float(lam[-1]), 4), "lanczos_converged": bool(conv)}
+    for label, e, mode in (("hybrid PCG r=50 bf16", eig, "pcg"), ("pure CG r=0", None, "paper")):
+        tol, err, _ = calibrate(ctx, sub, e, mode, alpha)
+        leg = time_leg(ctx, sub, e, mode, tol, alpha, 50, 5, B, 10, False)
+        ms = leg["total_ms"] / 50
+        acc = accuracy(sub, leg["X"], leg["idx"], leg["sc"], 10)
+        out[label] = {"tol": tol, "iters_max": int(leg["iters"].max()), "ms_per_batch": round(ms, 4),
+                      "qps": round(B / ms * 1e3, 1), "timed_rel_l2_max": acc["oracle_rel_l2_max"],
+                      "top10_valid": acc["top10_valid"]}
+    eig.close()
+    return out
+
+
 def truncated_leg(ctx, wl, args, alpha, tol_ref):
     """Temporal† (Sec. 3.1; Table 1: 20 iterations, 75k shortlist): CG on each
     query's shortlist subgraph.  The shortlists (top-s database items by
@@ -778,6 +825,8 @@ def main():
     trunc = None
     if not args.quick and args.shortlist > 0 and not wl["pool"]:
         trunc = truncated_leg(ctx, wl, args, alpha, 1e-7)
+    # ---- the 2,000-node clustered workload, where the hybrid's rank matters
+    small = small_leg(ctx, args, alpha) if (args.small_leg and not args.quick and rank == 0) else None
     # ---- convergence analysis (Eq. 21-23) against the measured iteration counts
     conv = None
     if not args.quick and wl["lam"] is not None:
@@ -875,7 +924,7 @@ def main():
                    "setup_s": {"gen": round(wl["t_gen"], 1), "graph": round(wl["t_graph"], 1),
                                "eig": round(wl["t_eig"], 1)}},
         "p50_ms": round(float(np.percentile(hyb["ms"], 50)), 4), "p99_ms": round(float(np.percentile(hyb["ms"], 99)), 4),
-        "cg_r0": cg, "sweep": sweep, "temporal_truncated": trunc, "convergence": conv, "serving": serving, "e2e": e2e, "gpu_launches": int(hyb["launches"]), "roofline": roofline, "cpu_baseline": cpu,
+        "cg_r0": cg, "sweep": sweep, "small_workload": small, "temporal_truncated": trunc, "convergence": conv, "serving": serving, "e2e": e2e, "gpu_launches": int(hyb["launches"]), "roofline": roofline, "cpu_baseline": cpu,
         "clocks": clocks, "wall_s_timed": round(t_wall, 3),
     }
     if rank == 0:

@@ -1258,6 +1258,7 @@ int tune_segments(hd_ctx* ctx, Engine& E) {
     auto it = g->seg_cache.find(E.Bp);
     if (forced >= 1) {
         K = forced;
+        g->seg_cache[E.Bp] = K;  // reported by hd_graph_tuning
     } else if (it != g->seg_cache.end()) {
         K = it->second;
     } else if ((int64_t)g->n * E.Bp * 4 > (int64_t)64 << 20) {
