@@ -223,7 +223,8 @@ def calibrate(ctx, wl, eig, mode, alpha, cal=None):
 
 
 # ------------------------------------------------------------------ timed legs
-FAMILIES = ["spmm", "resid", "dot", "update", "direction", "colsq", "lr_reduce", "lr_expand", "scalar", "rank"]
+FAMILIES = ["spmm", "spmm_h", "to_half", "resid", "dot", "update", "direction", "colsq", "lr_reduce", "lr_expand",
+            "scalar", "rank"]
 
 
 def time_leg(ctx, wl, eig, mode, tol, alpha, K, W, B, topk, profile, tim=None):
@@ -345,6 +346,8 @@ def algorithmic_bytes(wl, B, eig):
     return {
         "spmm": 8 * nnz + 4 * (n + 1) + 2 * vec,      # W (col + val), row_ptr, P once, Q
         "resid": 8 * nnz + 4 * (n + 1) + 2 * vec,     # the same for b - A x (X once, T)
+        "spmm_h": 8 * nnz + 4 * (n + 1) + vec // 2 + 2 * vec,  # fp16 copy of P once, own rows of P, Q
+        "to_half": 2 * vec + vec // 2,                 # max |P_j| (read P), convert (read P, write the copy)
         "dot": 2 * vec,                                 # read P, Q (P^T Q partials)
         "update": 6 * vec,                              # read X, R, P, Q; write X, R
         "direction": 3 * vec,                           # read R, P; write P

@@ -97,9 +97,10 @@ int hd_num_sms(const hd_ctx* ctx);
 /* Per-kernel device timing: while enabled, every launch of the library's
  * main kernels is bracketed by CUDA events on the context's stream.
  * hd_profile_read synchronises the stream and returns, for the kernel family
- * `name` ("spmm", "resid" (the true-residual SpMM), "dot", "update",
- * "direction", "colsq", "lr_reduce", "lr_expand", "scalar", "rank", "knn",
- * "trunc_build"), the number of
+ * `name` ("spmm", "spmm_h" (the SpMM on the fp16 copy of P), "to_half" (making
+ * that copy), "resid" (the true-residual SpMM), "dot", "update", "direction",
+ * "colsq", "lr_reduce", "lr_expand", "scalar", "rank", "knn", "trunc_build"),
+ * the number of
  * launches and their summed duration since the
  * last read, then clears that family.  busy_launches (may be NULL) counts the
  * launches that took at least 5% of the family's longest one: kernels of an

@@ -21,6 +21,8 @@
 #include <cstdio>
 #include <vector>
 
+#include <cuda_fp16.h>
+
 #include "hd_solve.cuh"
 
 // ------------------------------------------------------------------ helpers
@@ -180,6 +182,158 @@ __global__ void __launch_bounds__(256) k_spmm_w4(const int32_t* rp, const int32_
             q.w = c1 * own.w - c2 * s.w;
             st4(Q + row * ld + col, q);
         }
+    }
+}
+
+// ---- a 16-bit copy of P for the SpMM gathers of late iterations
+// Inexact Krylov methods (Simoncini and Szyld, SIAM J. Sci. Comput. 2003; van
+// den Eshof and Sleijpen, SIAM J. Matrix Anal. Appl. 2004): the operator may be
+// applied less accurately as the residual shrinks; the gap between recursive
+// and true residual grows by |a_k| ||E_k p_k|| per iteration.  Here E_k p =
+// c2 W (p~ - p) with p~ the fp16 copy (relative rounding u16 = 2^-11 per
+// entry), and |a_k| ||p_k|| = ||x_{k+1} - x_k|| <= 2 ||r_k|| (L_a(W) >= I), so
+// the gap added by an fp16 iteration is at most 2 c2 u16 ||W (p~ - p)|| / u16
+// ||p|| times ||r_k||: 0.1 ||r_k|| in the worst case, ~0.008 ||r_k|| for rounding
+// errors of random sign over ~54 neighbours.  The next SpMM gathers the fp16
+// copy once every active column has ||r|| <= HALF_THETA tol ||b||, which keeps
+// the typical gap near a quarter of tol ||b||; the true-residual confirmation
+// certifies the result either way.  Each column is scaled by a power of two so
+// that its largest entry lies in [2^13, 2^14) (exact, no overflow); the own-row
+// term c1 p, the dot products and the updates stay fp32.
+constexpr double HALF_THETA = 25.0;
+
+// per-column max |P| (the bits of a non-negative float order like the value);
+// runs when the next SpMM gathers the fp16 copy and some column is active
+__global__ void __launch_bounds__(256) k_colmax(const float* __restrict__ P, int64_t n, int32_t ld,
+                                                unsigned* __restrict__ mx, const int* __restrict__ use_half,
+                                                const int* __restrict__ num_active) {
+    if (!*use_half || !*num_active) return;
+    __shared__ unsigned bmax[256];  // per column of this block (ld <= 256)
+    const int nq = ld >> 2;
+    const int rpb = blockDim.x / nq;  // rows per block step
+    for (int c = threadIdx.x; c < ld; c += blockDim.x) bmax[c] = 0u;
+    __syncthreads();
+    if ((int)threadIdx.x < rpb * nq) {
+        const int q = threadIdx.x % nq;
+        float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f;
+        for (int64_t row = (int64_t)blockIdx.x * rpb + threadIdx.x / nq; row < n; row += (int64_t)gridDim.x * rpb) {
+            const float4 v = ld4(P + row * ld + 4 * q);
+            m0 = fmaxf(m0, fabsf(v.x));
+            m1 = fmaxf(m1, fabsf(v.y));
+            m2 = fmaxf(m2, fabsf(v.z));
+            m3 = fmaxf(m3, fabsf(v.w));
+        }
+        // one global atomic per column and block: same-address atomics from
+        // every thread would serialise in the one L2 slice holding mx
+        atomicMax(bmax + 4 * q, __float_as_uint(m0));
+        atomicMax(bmax + 4 * q + 1, __float_as_uint(m1));
+        atomicMax(bmax + 4 * q + 2, __float_as_uint(m2));
+        atomicMax(bmax + 4 * q + 3, __float_as_uint(m3));
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < ld; c += blockDim.x) atomicMax(mx + c, bmax[c]);
+}
+
+// 2^k with max|P_j| 2^k in [2^13, 2^14) (1 for a zero column), and its inverse
+__device__ __forceinline__ float half_scale(unsigned mbits, bool inverse) {
+    const float m = __uint_as_float(mbits);
+    if (!(m > 0.f)) return 1.f;
+    int ex;
+    frexpf(m, &ex);  // m = f 2^ex, f in [0.5, 1)
+    return ldexpf(1.f, inverse ? ex - 14 : 14 - ex);
+}
+
+// P16 = fp16(P_j 2^k_j) column by column
+__global__ void __launch_bounds__(256) k_to_half(const float* __restrict__ P, int64_t n, int32_t ld,
+                                                 const unsigned* __restrict__ mx, __half* __restrict__ P16,
+                                                 const int* __restrict__ use_half,
+                                                 const int* __restrict__ num_active) {
+    if (!*use_half || !*num_active) return;
+    const int nq = ld >> 2;
+    const int rpb = blockDim.x / nq;
+    if ((int)threadIdx.x >= rpb * nq) return;
+    const int q = threadIdx.x % nq;
+    const float s0 = half_scale(mx[4 * q], false), s1 = half_scale(mx[4 * q + 1], false);
+    const float s2 = half_scale(mx[4 * q + 2], false), s3 = half_scale(mx[4 * q + 3], false);
+    for (int64_t row = (int64_t)blockIdx.x * rpb + threadIdx.x / nq; row < n; row += (int64_t)gridDim.x * rpb) {
+        const float4 v = ld4(P + row * ld + 4 * q);
+        const __half2 a = __floats2half2_rn(v.x * s0, v.y * s1);
+        const __half2 b = __floats2half2_rn(v.z * s2, v.w * s3);
+        uint2 o;
+        o.x = *reinterpret_cast<const unsigned*>(&a);
+        o.y = *reinterpret_cast<const unsigned*>(&b);
+        *reinterpret_cast<uint2*>(P16 + row * ld + 4 * q) = o;
+    }
+}
+
+#define FMA8H(acc_, wt_, raw_)                                                    \
+    {                                                                             \
+        const __half2* h_ = reinterpret_cast<const __half2*>(&(raw_));            \
+        _Pragma("unroll") for (int k_ = 0; k_ < 4; ++k_) {                        \
+            const float2 f_ = __half22float2(h_[k_]);                             \
+            acc_[2 * k_] = fmaf(wt_, f_.x, acc_[2 * k_]);                         \
+            acc_[2 * k_ + 1] = fmaf(wt_, f_.y, acc_[2 * k_ + 1]);                 \
+        }                                                                         \
+    }
+
+// Q = c1 P - c2 W P with the W P gathers from the fp16 copy (S columns per
+// slab, 8 per lane: a row's slab is S 2 bytes); the sums are fp32, unscaled by
+// the column's power of two at the end.  Runs when *use_half is set.
+template <int S>
+__global__ void __launch_bounds__(256, 4) k_spmm_h(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                                   const float* __restrict__ wv, const __half* __restrict__ P16,
+                                                   const unsigned* __restrict__ mx, const float* __restrict__ P,
+                                                   float* __restrict__ Q, int64_t n, int32_t ld, float c1, float c2,
+                                                   const ColState* st, const int* __restrict__ use_half) {
+    constexpr int L = S / 8;
+    constexpr int RPB = 256 / L;
+    if (!*use_half) return;
+    if (!slab_has_work<S>(st, false)) return;
+    const int g = (threadIdx.x & 31) % L;
+    const int col = blockIdx.y * S + 8 * g;
+    float inv[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) inv[c] = half_scale(mx[col + c], true);
+    for (int64_t row = (int64_t)blockIdx.x * RPB + threadIdx.x / L; row < n; row += (int64_t)gridDim.x * RPB) {
+        const int32_t b = rp[row], e = rp[row + 1];
+        float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        int32_t t = b;
+        for (; t + 8 <= e; t += 8) {
+            int32_t j[8];
+            float w[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                j[u] = __ldg(ci + t + u);
+                w[u] = __ldg(wv + t + u);
+            }
+            uint4 v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = __ldg(reinterpret_cast<const uint4*>(P16 + (int64_t)j[u] * ld + col));
+#pragma unroll
+            for (int u = 0; u < 8; ++u) FMA8H(acc, w[u], v[u]);
+        }
+        for (; t < e; t += 4) {
+            const int m = e - t;
+            uint4 v[4];
+            float w[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                w[u] = u < m ? __ldg(wv + t + u) : 0.f;
+                v[u] = u < m ? __ldg(reinterpret_cast<const uint4*>(P16 + (int64_t)__ldg(ci + t + u) * ld + col))
+                             : make_uint4(0u, 0u, 0u, 0u);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (u < m) FMA8H(acc, w[u], v[u]);
+            }
+        }
+        const float4 o0 = ld4(P + row * ld + col), o1 = ld4(P + row * ld + col + 4);
+        const float own[8] = {o0.x, o0.y, o0.z, o0.w, o1.x, o1.y, o1.z, o1.w};
+        float q[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) q[c] = c1 * own[c] - c2 * (acc[c] * inv[c]);
+        st4(Q + row * ld + col, make_float4(q[0], q[1], q[2], q[3]));
+        st4(Q + row * ld + col + 4, make_float4(q[4], q[5], q[6], q[7]));
     }
 }
 
@@ -691,8 +845,11 @@ __global__ void k_fin_sigma(const float2* part, int nblk, int32_t Bp, ColState* 
 
 // After the update: rr, convergence, beta.  With C: PCG rho' = rr + sum_k coef_k C_k^2.
 // num_active must be zero before the launch.
+// use_half (may be null; 1 before the launch): cleared when a column that stays
+// active has ||r||^2 > theta2 tol^2 ||b||^2 (the next SpMM then gathers fp32).
 __global__ void k_fin_rr(const float2* part, int nblk, int32_t Bp, ColState* st, int32_t max_iter,
-                         const double* C, const double* coef, int32_t r, int* num_active) {
+                         const double* C, const double* coef, int32_t r, int* num_active, int* use_half = nullptr,
+                         double theta2 = 0.0) {
     const int j = blockIdx.x;
     ColState& s = st[j];
     const bool fresh = s.fresh, active = s.active;
@@ -743,6 +900,7 @@ __global__ void k_fin_rr(const float2* part, int nblk, int32_t Bp, ColState* st,
         s.status = HD_COL_MAX_ITER;
     } else {
         atomicAdd(num_active, 1);
+        if (use_half && !(rr <= theta2 * s.tol2)) atomicExch(use_half, 0);
     }
 }
 
@@ -1204,6 +1362,47 @@ static int launch_spmm(Engine& E, float c1, float c2, float2* part, const ColSta
     const hd_graph* g = E.g;
     const float* Pin = V ? V : E.P;
     dim3 grid(E.vl.nblk, E.vl.slabs);
+    if (!V && E.use_half) {
+        // the iteration's SpMM: an fp16 copy of P is gathered when *use_half
+        // (columns 8 per lane; 64-column slabs make a row's slab 128 bytes)
+        const int S16 = E.Bp % 64 == 0 ? 64 : E.Bp % 32 == 0 ? 32 : E.Bp % 16 == 0 ? 16 : 8;
+        const int nq = E.Bp / 4;
+        const int rpb = 256 / nq;
+        const dim3 gc((unsigned)std::min<int64_t>(ceil_div(E.n, rpb), (int64_t)ctx->num_sms * 8));
+        const int rpb16 = 256 / (S16 / 8);
+        const dim3 gh((unsigned)std::min<int64_t>(ceil_div(E.n, rpb16), (int64_t)ctx->num_sms * 4),
+                      (unsigned)(E.Bp / S16));
+        {
+            HD_PROF(ctx, "to_half");
+            HD_CUDA(ctx, cudaMemsetAsync(E.p16_max, 0, (size_t)E.Bp * sizeof(unsigned), ctx->stream));
+            k_colmax<<<gc, 256, 0, ctx->stream>>>(E.P, E.n, E.Bp, E.p16_max, E.use_half, E.num_active);
+            HD_CHECK_LAUNCH(ctx);
+            k_to_half<<<gc, 256, 0, ctx->stream>>>(E.P, E.n, E.Bp, E.p16_max, E.P16, E.use_half, E.num_active);
+            HD_CHECK_LAUNCH(ctx);
+        }
+        {
+            HD_PROF(ctx, "spmm");
+            HD_DISPATCH_S(E.vl.S, (k_spmm<SS><<<grid, 256, 0, ctx->stream>>>(g->row_ptr, g->col, g->val, E.P, E.Q, E.n,
+                                                                              E.Bp, c1, c2, st, E.use_half)));
+            HD_CHECK_LAUNCH(ctx);
+        }
+        {
+            HD_PROF(ctx, "spmm_h");
+            switch (S16) {
+                case 64: k_spmm_h<64><<<gh, 256, 0, ctx->stream>>>(g->row_ptr, g->col, g->val, E.P16, E.p16_max, E.P,
+                                                                    E.Q, E.n, E.Bp, c1, c2, st, E.use_half); break;
+                case 32: k_spmm_h<32><<<gh, 256, 0, ctx->stream>>>(g->row_ptr, g->col, g->val, E.P16, E.p16_max, E.P,
+                                                                    E.Q, E.n, E.Bp, c1, c2, st, E.use_half); break;
+                case 16: k_spmm_h<16><<<gh, 256, 0, ctx->stream>>>(g->row_ptr, g->col, g->val, E.P16, E.p16_max, E.P,
+                                                                    E.Q, E.n, E.Bp, c1, c2, st, E.use_half); break;
+                default: k_spmm_h<8><<<gh, 256, 0, ctx->stream>>>(g->row_ptr, g->col, g->val, E.P16, E.p16_max, E.P,
+                                                                   E.Q, E.n, E.Bp, c1, c2, st, E.use_half); break;
+            }
+            HD_CHECK_LAUNCH(ctx);
+        }
+        if (part) return launch_dot(E, part, st);
+        return HD_OK;
+    }
     {
         HD_PROF(ctx, "spmm");
         if (E.segK <= 1 && E.vl.S == 4 && E.warp_rows) {
@@ -1341,8 +1540,9 @@ int engine_iteration(Engine& S_, int (*after_update)(void*), void* arg) {
         if ((rc = lr_finish(ctx, S_.lr, Bp, S_.dcoef))) return rc;
         { HD_PROF(ctx, "scalar");
         HD_CUDA(ctx, cudaMemsetAsync(S_.num_active, 0, sizeof(int), ctx->stream));
+        if (S_.use_half) HD_CUDA(ctx, cudaMemsetAsync(S_.use_half, 0xff, sizeof(int), ctx->stream));
         k_fin_rr<<<Bp, 128, 0, ctx->stream>>>(S_.part, (int)S_.nch, Bp, S_.st, max_iter, Cd, S_.dcoef, r,
-                                             S_.num_active); }
+                                             S_.num_active, S_.use_half, HALF_THETA * HALF_THETA); }
         HD_CHECK_LAUNCH(ctx);
         if ((rc = lr_expand(ctx, S_.lr, EXP_DIRECTION, S_.P, S_.R, S_.P, n, Bp, S_.st, S_.num_active))) return rc;
     } else {
@@ -1365,8 +1565,9 @@ int engine_iteration(Engine& S_, int (*after_update)(void*), void* arg) {
     if (after_update && (rc = after_update(arg))) return rc;
         { HD_PROF(ctx, "scalar");
         HD_CUDA(ctx, cudaMemsetAsync(S_.num_active, 0, sizeof(int), ctx->stream));
+        if (S_.use_half) HD_CUDA(ctx, cudaMemsetAsync(S_.use_half, 0xff, sizeof(int), ctx->stream));
         k_fin_rr<<<Bp, 128, 0, ctx->stream>>>(S_.part, (int)S_.nch, Bp, S_.st, max_iter, nullptr, nullptr, 0,
-                                             S_.num_active); }
+                                             S_.num_active, S_.use_half, HALF_THETA * HALF_THETA); }
         HD_CHECK_LAUNCH(ctx);
         LAUNCH_VEC(k_direction, S_.P, S_.R, n, Bp, S_.st);
         if (lr_on) {
@@ -1401,7 +1602,7 @@ static std::vector<uint64_t> iteration_key(const Engine& E) {
             (uint64_t)E.nch, (uint64_t)E.Bp, (uint64_t)E.vl.S, (uint64_t)E.vl.nblk, (uint64_t)E.vl.slabs,
             (uint64_t)E.lr.nchunk, (uint64_t)E.lr.rpad, (uint64_t)E.lr.Bp16, (uint64_t)E.has_lr,
             (uint64_t)E.eff_mode, (uint64_t)E.r, (uint64_t)E.max_iter, fbits(E.c1), fbits(E.c2), fbits(E.xs),
-            (uint64_t)E.ctx->stream};
+            (uint64_t)E.P16, (uint64_t)E.p16_max, (uint64_t)E.use_half, (uint64_t)E.ctx->stream};
 }
 
 static int run_iterations_graph(Engine& E, int iters) {
@@ -1445,6 +1646,16 @@ static int run_iterations_graph(Engine& E, int iters) {
     HD_CUDA(ctx, cudaGraphLaunch(it->second.exec, ctx->stream));
     ctx->launches += it->second.launches;
     return HD_OK;
+}
+
+// HD_NO_HALF=1: every SpMM of the iterations gathers fp32
+static bool half_gathers_off() {
+    static int off = -1;
+    if (off < 0) {
+        const char* s = getenv("HD_NO_HALF");
+        off = (s && atoi(s)) ? 1 : 0;
+    }
+    return off != 0;
 }
 
 static bool graphs_enabled(hd_ctx* ctx) {
@@ -1570,6 +1781,7 @@ static int restart_columns(Engine& E) {
     int rc;
     k_restart_copy<<<ceil_div(n * (Bp / 4), 256), 256, 0, ctx->stream>>>(E.R, E.Q, n, Bp, E.st);
     HD_CHECK_LAUNCH(ctx);
+    if (E.use_half) HD_CUDA(ctx, cudaMemsetAsync(E.use_half, 0, sizeof(int), ctx->stream));
     if (E.eff_mode == HD_MODE_PCG) {
         if ((rc = lr_reduce(ctx, E.lr, E.R, n, Bp))) return rc;
         if ((rc = lr_finish(ctx, E.lr, Bp, E.dcoef))) return rc;
@@ -1659,6 +1871,9 @@ int hd_query_impl(hd_ctx* ctx, const hd_graph* g, const TruncSys* ts, const hd_e
     if (lr_on)
         bytes += ws_size((size_t)nchunk * rpad * Bp * 4) + 2 * ws_size((size_t)rpad * Bp * 8) +
                  ws_size((size_t)rpad * Bp * 4) + 2 * ws_size((size_t)Bp16 * rpad * 2) + 6 * ws_size(rpad * 8);
+    // the fp16 gather copy of P: graph solves with 8 <= Bp <= 256 columns in multiples of 8
+    const bool half_ok = !ts && Bp % 8 == 0 && Bp <= 256;
+    if (half_ok) bytes += ws_size((size_t)n * Bp * 2) + ws_size((size_t)Bp * 4);
     void* ws;
     int rc = hd_ws_reserve(ctx, bytes, &ws);
     if (rc) return rc;
@@ -1683,6 +1898,8 @@ int hd_query_impl(hd_ctx* ctx, const hd_graph* g, const TruncSys* ts, const hd_e
     S_.yp = (const int32_t*)yp;
     S_.yi = (const int32_t*)yi;
     S_.yv = (const float*)yv;
+    __half* p16 = half_ok ? cv.take<__half>((size_t)n * Bp) : nullptr;
+    unsigned* p16_max = half_ok ? cv.take<unsigned>(Bp) : nullptr;
     if (lr_on) {
         S_.lr.e = eig;
         S_.lr.rpad = rpad;
@@ -1736,6 +1953,12 @@ int hd_query_impl(hd_ctx* ctx, const hd_graph* g, const TruncSys* ts, const hd_e
     }
     S_.vl = vec_launch(ctx, n, Bp, ts ? pick_slab(Bp) : tune_slab(ctx, g, Bp, S_.P, S_.Q));
     if (!ts && (rc = tune_segments(ctx, S_))) return rc;
+    if (half_ok && S_.segK == 1 && !half_gathers_off()) {
+        S_.P16 = p16;
+        S_.p16_max = p16_max;
+        S_.use_half = S_.num_active + 3;  // 0: the first iteration gathers fp32
+        HD_CUDA(ctx, cudaMemsetAsync(S_.use_half, 0, sizeof(int), ctx->stream));
+    }
     const int eff_mode = lr_on ? mode : HD_MODE_PAPER;
     const double a = alpha;
     float c1, c2, xs = 1.0f;

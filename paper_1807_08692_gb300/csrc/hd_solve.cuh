@@ -1,5 +1,7 @@
 // Shared declarations of the online query path (Eq. 17-20).
 #pragma once
+#include <cuda_fp16.h>
+
 #include "hd_internal.cuh"
 
 // Per-column CG state, fp64 scalars.
@@ -106,6 +108,13 @@ struct Engine {
     const int32_t* yi = nullptr;
     const float* yv = nullptr;
     double* Cy = nullptr;       // U^T y [rpad][Bp] (paper and projected forms: x^s and b)
+    // fp16 copy of P for the SpMM gathers of late iterations (hd_query_batch
+    // only: the decision covers the whole batch, so a column's bits would
+    // depend on its neighbours, which the server avoids)
+    bool allow_half = false;
+    __half* P16 = nullptr;      // n x Bp
+    unsigned* p16_max = nullptr;  // [Bp] max |P_j| as float bits
+    int* use_half = nullptr;    // 1: the next SpMM gathers P16
     double* negop = nullptr;    // -(a / (1 - a)) lambda: the deflation term of -L_a(W_r)
     LowRank lr{};
     bool has_lr = false;
