@@ -395,7 +395,7 @@ int hd_rank_static(hd_ctx* ctx, const float* X, int64_t n, int32_t B, int32_t ld
 
 typedef struct hd_req_stats {
     double submit_s;    /* host steady clock (s) at hd_serve_submit */
-    double admit_s;     /* when the request got a column of the batch */
+    double admit_s;     /* end of the step in which a column took the request */
     double done_s;      /* when its ranking had been copied to the host */
     int32_t iters;      /* CG iterations the request used */
     int32_t status;     /* HD_COL_* */
@@ -426,10 +426,19 @@ int hd_serve_slots(const hd_server* s);
  * Copies the arrays; returns a ticket.  Errors: HD_ERR_INVALID_ARG. */
 int hd_serve_submit(hd_server* s, int32_t nnz_y, const int32_t* idx, const float* val, float tol,
                     int32_t K, uint64_t* ticket);
-/* Admit queued requests into free columns, run `iters` CG iterations of the
- * whole batch, then retire every column that stopped (converged, max_iter,
- * breakdown, empty): its top-K is ranked on the device and copied to the host.
- * *busy (may be NULL) receives the number of queued plus running requests. */
+/* One step of the server: stage up to a batch's width of queued requests
+ * (their observations and, with eigenpairs, U^T y), run `iters` CG
+ * iterations of the whole batch, then retire every column that stopped
+ * (converged, max_iter, breakdown): its top-K is ranked on the device and
+ * copied to the host.  Admission happens inside the last iteration: in its
+ * scalar step a column whose request stops there, or a free column, takes the
+ * next staged request, and the same iteration's direction forms the new
+ * request's p0 = M^-1 y, so no column spends an iteration between two requests
+ * (a request's first update comes in the next step).  Staged requests no
+ * column took go back to the front of the queue.  A request with y = 0 or
+ * tol >= 1 finishes at staging (x = 0, ids 0 .. K-1 with score 0).
+ * iters = 0 with requests queued runs one iteration.  *busy (may be NULL)
+ * receives the number of queued plus running requests. */
 int hd_serve_step(hd_server* s, int32_t iters, int32_t* busy);
 /* HD_PENDING while the request runs; then copies its K ids / scores (host)
  * and stats, forgets the ticket and returns HD_OK.  HD_ERR_NOT_FOUND for an

@@ -354,11 +354,17 @@ __global__ void __launch_bounds__(THREADS + (SU ? CONV : 0), 1)
                 const int j = a.c0 + c0 * 16 + 4 * ch;
                 const bool colok = c0 + (ch >> 2) < ce && j < a.Bp;
                 float b0 = 0.f, b1 = 0.f, b2 = 0.f, b3 = 0.f;
+                bool f0 = false, f1 = false, f2 = false, f3 = false;
                 if (colok && a.op == EXP_DIRECTION) {
                     b0 = (float)a.st[j].beta;
                     b1 = (float)a.st[j + 1].beta;
                     b2 = (float)a.st[j + 2].beta;
                     b3 = (float)a.st[j + 3].beta;
+                    // a served column that just took a new request drops r (p0 = U D U^T y + y)
+                    f0 = a.st[j].refill;
+                    f1 = a.st[j + 1].refill;
+                    f2 = a.st[j + 2].refill;
+                    f3 = a.st[j + 3].refill;
                 }
 #pragma unroll
                 for (int k = 0; k < 8; ++k) {
@@ -377,10 +383,10 @@ __global__ void __launch_bounds__(THREADS + (SU ? CONV : 0), 1)
                         w.x += acc.x; w.y += acc.y; w.z += acc.z; w.w += acc.w;
                     } else {
                         const float4 r4 = g1[k], p4 = g2[k];
-                        w.x = r4.x + acc.x + (b0 == 0.0f ? 0.0f : b0 * p4.x);
-                        w.y = r4.y + acc.y + (b1 == 0.0f ? 0.0f : b1 * p4.y);
-                        w.z = r4.z + acc.z + (b2 == 0.0f ? 0.0f : b2 * p4.z);
-                        w.w = r4.w + acc.w + (b3 == 0.0f ? 0.0f : b3 * p4.w);
+                        w.x = (f0 ? 0.0f : r4.x) + acc.x + (b0 == 0.0f ? 0.0f : b0 * p4.x);
+                        w.y = (f1 ? 0.0f : r4.y) + acc.y + (b1 == 0.0f ? 0.0f : b1 * p4.y);
+                        w.z = (f2 ? 0.0f : r4.z) + acc.z + (b2 == 0.0f ? 0.0f : b2 * p4.z);
+                        w.w = (f3 ? 0.0f : r4.w) + acc.w + (b3 == 0.0f ? 0.0f : b3 * p4.w);
                     }
                     *reinterpret_cast<float4*>(a.out + row_g * a.Bp + j) = w;
                 }

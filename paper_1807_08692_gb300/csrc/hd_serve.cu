@@ -2,21 +2,24 @@
 //
 // A server owns persistent batches ("lanes") of columns (R, P, Q, X of n x Bp):
 // the wide lane of `slots` columns and, when there is room, a narrow lane of
-// four.  Requests queue on the host; at each step free columns take queued
-// requests (admission: the column is marked fresh, the next CG update resets it
-// and its observation is scattered in, and the scalar step starts its
-// iteration), every column of a running lane advances the same CG iterations,
-// and columns whose residual met their own tolerance retire: their top-K is
-// ranked and copied out and the column is free again.
+// four.  Requests queue on the host.  Before each step the host stages queued
+// requests (their observations and U^T y); inside the step's scalar kernel a
+// column whose request stops there -- or a free column -- claims the next
+// staged request, so the same iteration's direction already forms the new
+// request's p0 = M^-1 y and a column never spends an iteration idle between two
+// requests.  The stopped request's x stays in the column until the next update,
+// which starts the new one from scratch; between the two the host ranks it
+// (top-K copied out).  Staged requests that found no column go back to the
+// front of the queue.
 //
 // A lightly loaded server (wide lane idle, queue no longer than the narrow
-// lane's free columns) admits into the narrow lane: its rows are 16 bytes
+// lane's free columns) stages into the narrow lane: its rows are 16 bytes
 // instead of 4 x slots bytes, so one request moves far fewer bytes per
 // iteration.  Otherwise requests go to the wide lane.  A column's arithmetic
 // never depends on its lane, slot or the other columns (per-element SpMM order
 // is the same for every slab width, reductions are chunked by rows, the
-// tensor-core products treat columns independently), so a request gets the
-// same bits alone or in a mix.
+// tensor-core products treat columns independently, every request starts the
+// same way), so a request gets the same bits alone or in a mix.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -49,43 +52,59 @@ struct Req {
     std::vector<float> out_score;
 };
 
-struct AdmitRec {
-    int32_t slot;
-    int32_t off;    // into the staged index/value arrays
-    int32_t cnt;
-    float tol;
-    double bb;
-};
-
-__global__ void k_admit_mark(const AdmitRec* recs, int nrec, ColState* st, int* num_active) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nrec) return;
-    const AdmitRec a = recs[t];
-    ColState& s = st[a.slot];
-    s.fresh = 1;
-    s.active = 0;
-    s.a = 0.0;
-    s.beta = 0.0;
-    s.bb = a.bb;
-    s.tol2 = (double)a.tol * (double)a.tol * a.bb;
-    atomicAdd(num_active, 1);  // admitted columns are work for this iteration's gated kernels
+// U^T y of each staged request (fp64, in entry order; zero beyond r): the
+// spectral part of its first preconditioned residual z0 = y + U D U^T y.
+// One block per request, threads over the eigen-index k.
+template <typename T>
+__device__ __forceinline__ double u_entry(const T* U, const float* scale, int64_t i, int ldu, int k);
+template <>
+__device__ __forceinline__ double u_entry<float>(const float* U, const float*, int64_t i, int ldu, int k) {
+    return (double)U[i * ldu + k];
+}
+template <>
+__device__ __forceinline__ double u_entry<__nv_bfloat16>(const __nv_bfloat16* U, const float*, int64_t i, int ldu,
+                                                         int k) {
+    return (double)__bfloat162float(U[i * ldu + k]);
+}
+template <>
+__device__ __forceinline__ double u_entry<__nv_fp8_e4m3>(const __nv_fp8_e4m3* U, const float* scale, int64_t i,
+                                                         int ldu, int k) {
+    return (double)(float(U[i * ldu + k]) * scale[i]);
 }
 
-// a cancelled request's column: inactive from the next kernel on
+template <typename T>
+__global__ void k_stage_c(const T* U, const float* scale, int ldu, int r, int rpad, const int32_t* off,
+                          const int32_t* yidx, const float* yval, double* C) {
+    const int s = blockIdx.x;
+    for (int k = threadIdx.x; k < rpad; k += blockDim.x) {
+        double c = 0.0;
+        if (k < r)
+            for (int32_t t = off[s]; t < off[s + 1]; ++t) c += (double)yval[t] * u_entry<T>(U, scale, yidx[t], ldu, k);
+        C[(int64_t)s * rpad + k] = c;
+    }
+}
+
+// the same from a sparsified U (rows in CSR): one thread per request
+__global__ void k_stage_c_sparse(const int64_t* rp, const int32_t* col, const float* val, int rpad, int nstage,
+                                 const int32_t* off, const int32_t* yidx, const float* yval, double* C) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nstage) return;
+    double* c = C + (int64_t)s * rpad;
+    for (int k = 0; k < rpad; ++k) c[k] = 0.0;
+    for (int32_t t = off[s]; t < off[s + 1]; ++t) {
+        const int64_t i = yidx[t];
+        for (int64_t q = rp[i]; q < rp[i + 1]; ++q) c[col[q]] += (double)yval[t] * (double)val[q];
+    }
+}
+
+// a cancelled request's column: inactive and free from the next kernel on
 __global__ void k_cancel_col(ColState* st, int j) {
     st[j].active = 0;
-    st[j].fresh = 0;
+    st[j].refill = 0;
+    st[j].free_col = 1;
     st[j].a = 0.0;
     st[j].beta = 0.0;
     st[j].status = HD_COL_CANCELLED;
-}
-
-__global__ void k_admit_scatter(const AdmitRec* recs, int nrec, const int32_t* yidx, const float* yval, float* R,
-                                int32_t ld) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nrec) return;
-    const AdmitRec a = recs[t];
-    for (int e = 0; e < a.cnt; ++e) R[(int64_t)yidx[a.off + e] * ld + a.slot] += yval[a.off + e];
 }
 
 }  // namespace
@@ -94,20 +113,30 @@ __global__ void k_admit_scatter(const AdmitRec* recs, int nrec, const int32_t* y
 // One persistent batch of columns and everything it needs on both sides.
 struct Lane {
     Engine E;
+    Refill rf;              // device pointers of the staging below (E.refill points here)
     int32_t slots = 0;
     int32_t slot_base = 0;  // reported slot number of column 0
     int S_full = 4;         // SpMM slab width measured for the whole lane
     void* dev = nullptr;
-    // admission staging
-    AdmitRec* d_rec = nullptr;
-    int32_t* d_yidx = nullptr;
-    float* d_yval = nullptr;
-    AdmitRec* h_rec = nullptr;
-    int32_t* h_yidx = nullptr;
-    float* h_yval = nullptr;
-    int32_t cap_nnz = 0;
-    int nrec = 0;
     hd_ctx* ctx = nullptr;
+    // staging for the next step: device arrays and their pinned host sources
+    int32_t cap_nnz = 0;
+    int32_t *d_off = nullptr, *d_yidx = nullptr;
+    float* d_yval = nullptr;
+    double *d_bb = nullptr, *d_tol2 = nullptr, *d_C = nullptr;
+    int* d_ctl = nullptr;   // [0] requests claimable this iteration, [1] next one for a stopping column
+    int32_t* d_pre = nullptr;  // [Bp] staged request assigned to a free column (-1: none)
+    int32_t* h_pre = nullptr;
+    int32_t *h_off = nullptr, *h_yidx = nullptr;
+    float* h_yval = nullptr;
+    double *h_bb = nullptr, *h_tol2 = nullptr;
+    int* h_ctl = nullptr;
+    // what the step's scalar kernels recorded
+    int32_t* h_assign = nullptr;
+    int32_t* h_ret_iters = nullptr;
+    int32_t* h_ret_status = nullptr;
+    double* h_ret_rr = nullptr;
+    std::vector<Req*> staged;
     // ranking outputs
     int32_t* d_idx = nullptr;
     float* d_sc = nullptr;
@@ -143,12 +172,10 @@ struct hd_server {
 static void lane_free(hd_ctx* ctx, Lane& L) {
     if (ctx) cudaStreamSynchronize(ctx->stream);
     cudaFree(L.dev);
-    cudaFreeHost(L.h_rec);
-    cudaFreeHost(L.h_yidx);
-    cudaFreeHost(L.h_yval);
-    cudaFreeHost(L.h_idx);
-    cudaFreeHost(L.h_sc);
-    cudaFreeHost(L.h_st);
+    for (void* h : {(void*)L.h_off, (void*)L.h_yidx, (void*)L.h_yval, (void*)L.h_bb, (void*)L.h_tol2,
+                    (void*)L.h_ctl, (void*)L.h_pre, (void*)L.h_assign, (void*)L.h_ret_iters, (void*)L.h_ret_status,
+                    (void*)L.h_ret_rr, (void*)L.h_idx, (void*)L.h_sc, (void*)L.h_st})
+        cudaFreeHost(h);
     L = Lane();
 }
 
@@ -159,15 +186,10 @@ static void server_free(hd_server* s) {
     delete s;
 }
 
-static int admit_cb(void* arg) {
-    Lane* L = (Lane*)arg;
-    if (!L->nrec) return HD_OK;
-    hd_ctx* ctx = L->ctx;
-    k_admit_scatter<<<ceil_div(L->nrec, 64), 64, 0, ctx->stream>>>(L->d_rec, L->nrec, L->d_yidx, L->d_yval, L->E.R,
-                                                                   L->E.Bp);
-    HD_CHECK_LAUNCH(ctx);
-    L->nrec = 0;
-    return HD_OK;
+// after the update: a column that took a request at the last scalar step gets
+// its y (r = y - a q) and the exact correction of ||r||^2
+static int refill_cb(void* arg) {
+    return launch_refill_r(((Lane*)arg)->E);
 }
 
 // Buffers and engine of one lane of `slots` columns.
@@ -188,8 +210,8 @@ static int lane_open(hd_ctx* ctx, const hd_graph* g, const hd_eig* eig, double a
     E.has_lr = lr_on;
     E.r = lr_on ? eig->r : 0;
     E.eff_mode = lr_on ? HD_MODE_PCG : HD_MODE_PAPER;
-    E.c1 = (float)(1.0 / (1.0 - (double)alpha));
-    E.c2 = (float)((double)alpha / (1.0 - (double)alpha));
+    E.c1 = (float)(1.0 / (1.0 - alpha));
+    E.c2 = (float)(alpha / (1.0 - alpha));
     E.xs = 1.0f;
     E.max_iter = max_iter;
     // one SpMM order in every lane: thread-per-row sums, a single pass
@@ -200,11 +222,16 @@ static int lane_open(hd_ctx* ctx, const hd_graph* g, const hd_eig* eig, double a
     const int rpad = lr_on ? (eig->r + 63) / 64 * 64 : 0;
     const int Bp16 = (Bp + 15) / 16 * 16;
     const int nchunk = lr_on ? lr_nchunk(ctx, eig, Bp) : 0;
-    L.cap_nnz = Bp * 512;
+    L.cap_nnz = Bp * REFILL_MAX_NNZ;
     const size_t vec = (size_t)n * Bp * 4;
     size_t bytes = 4 * ws_size(vec) + ws_size((size_t)E.nch * Bp * 8) + ws_size(Bp * sizeof(ColState)) +
-                   ws_size(64) + ws_size(Bp * sizeof(AdmitRec)) + 2 * ws_size((size_t)L.cap_nnz * 4) +
-                   2 * ws_size((size_t)Bp * Kmax * 4);
+                   ws_size(64) + 2 * ws_size((size_t)Bp * Kmax * 4) +
+                   // staging: offsets, entries, bb, tol2, U^T y, control; per column: assignment,
+                   // retired statistics, the installed request's y
+                   ws_size((Bp + 1) * 4) + 2 * ws_size((size_t)L.cap_nnz * 4) + 2 * ws_size(Bp * 8) +
+                   ws_size((size_t)Bp * std::max(rpad, 1) * 8) + ws_size(64) + 3 * ws_size(Bp * 4) +
+                   ws_size(Bp * 8) + ws_size(Bp * 4) + 2 * ws_size((size_t)Bp * REFILL_MAX_NNZ * 4) +
+                   ws_size(Bp * 4);
     if (lr_on)
         bytes += ws_size((size_t)nchunk * rpad * Bp * 4) + ws_size((size_t)rpad * Bp * 8) +
                  ws_size((size_t)rpad * Bp * 4) + 2 * ws_size((size_t)Bp16 * rpad * 2) + ws_size(rpad * 8);
@@ -225,11 +252,36 @@ static int lane_open(hd_ctx* ctx, const hd_graph* g, const hd_eig* eig, double a
     E.err = E.num_active + 1;
     E.vl = vec_launch(ctx, n, Bp, tune_slab(ctx, g, Bp, E.P, E.Q));
     L.S_full = E.vl.S;
-    L.d_rec = cv.take<AdmitRec>(Bp);
-    L.d_yidx = cv.take<int32_t>(L.cap_nnz);
-    L.d_yval = cv.take<float>(L.cap_nnz);
     L.d_idx = cv.take<int32_t>((size_t)Bp * Kmax);
     L.d_sc = cv.take<float>((size_t)Bp * Kmax);
+    L.d_off = cv.take<int32_t>(Bp + 1);
+    L.d_yidx = cv.take<int32_t>(L.cap_nnz);
+    L.d_yval = cv.take<float>(L.cap_nnz);
+    L.d_bb = cv.take<double>(Bp);
+    L.d_tol2 = cv.take<double>(Bp);
+    L.d_C = cv.take<double>((size_t)Bp * std::max(rpad, 1));
+    L.d_ctl = cv.take<int>(16);
+    Refill& rf = L.rf;
+    rf.off = L.d_off;
+    rf.yidx = L.d_yidx;
+    rf.yval = L.d_yval;
+    rf.bb = L.d_bb;
+    rf.tol2 = L.d_tol2;
+    rf.C = lr_on ? L.d_C : nullptr;
+    rf.nstage = L.d_ctl;
+    rf.next = L.d_ctl + 1;
+    rf.assign = cv.take<int32_t>(Bp);
+    rf.ret_iters = cv.take<int32_t>(Bp);
+    rf.ret_status = cv.take<int32_t>(Bp);
+    rf.ret_rr = cv.take<double>(Bp);
+    rf.col_cnt = cv.take<int32_t>(Bp);
+    rf.col_idx = cv.take<int32_t>((size_t)Bp * REFILL_MAX_NNZ);
+    rf.col_val = cv.take<float>((size_t)Bp * REFILL_MAX_NNZ);
+    L.d_pre = cv.take<int32_t>(Bp);
+    rf.pre = L.d_pre;
+    rf.rpad = rpad;
+    rf.live = slots;
+    E.refill = &L.rf;
     if (lr_on) {
         E.lr.e = eig;
         E.lr.rpad = rpad;
@@ -244,7 +296,7 @@ static int lane_open(hd_ctx* ctx, const hd_graph* g, const hd_eig* eig, double a
         std::vector<double> dc(rpad, 0.0);
         for (int k = 0; k < eig->r; ++k) {
             const double l = std::max(0.0, eig->lambda_h[k]);
-            dc[k] = (double)alpha * l / (1.0 - (double)alpha * l);
+            dc[k] = alpha * l / (1.0 - alpha * l);
         }
         HD_CUDA(ctx, cudaMemcpyAsync(E.dcoef, dc.data(), rpad * 8, cudaMemcpyHostToDevice, ctx->stream));
         HD_CUDA(ctx, cudaMemsetAsync(E.lr.Hhi, 0, (size_t)Bp16 * rpad * 2, ctx->stream));
@@ -252,72 +304,130 @@ static int lane_open(hd_ctx* ctx, const hd_graph* g, const hd_eig* eig, double a
     }
     HD_CUDA(ctx, cudaMemsetAsync(L.dev, 0, 4 * ws_size(vec), ctx->stream));
     HD_CUDA(ctx, cudaMemsetAsync(E.num_active, 0, 16 * sizeof(int), ctx->stream));
+    HD_CUDA(ctx, cudaMemsetAsync(L.d_ctl, 0, 16 * sizeof(int), ctx->stream));
+    HD_CUDA(ctx, cudaMemsetAsync(rf.assign, 0xff, Bp * sizeof(int32_t), ctx->stream));
+    HD_CUDA(ctx, cudaMemsetAsync(L.d_pre, 0xff, Bp * sizeof(int32_t), ctx->stream));
     std::vector<ColState> st0(Bp);
-    for (auto& c : st0) {
-        memset(&c, 0, sizeof c);
-        c.status = HD_COL_EMPTY;
+    for (int j = 0; j < Bp; ++j) {
+        memset(&st0[j], 0, sizeof st0[j]);
+        st0[j].status = HD_COL_EMPTY;
+        st0[j].free_col = j < slots ? 1 : 0;
     }
     HD_CUDA(ctx, cudaMemcpyAsync(E.st, st0.data(), Bp * sizeof(ColState), cudaMemcpyHostToDevice, ctx->stream));
-    if (cudaMallocHost(&L.h_rec, Bp * sizeof(AdmitRec)) || cudaMallocHost(&L.h_yidx, (size_t)L.cap_nnz * 4) ||
-        cudaMallocHost(&L.h_yval, (size_t)L.cap_nnz * 4) || cudaMallocHost(&L.h_idx, (size_t)Bp * Kmax * 4) ||
-        cudaMallocHost(&L.h_sc, (size_t)Bp * Kmax * 4) || cudaMallocHost(&L.h_st, Bp * sizeof(ColState))) {
+    if (cudaMallocHost(&L.h_off, (Bp + 1) * 4) || cudaMallocHost(&L.h_yidx, (size_t)L.cap_nnz * 4) ||
+        cudaMallocHost(&L.h_yval, (size_t)L.cap_nnz * 4) || cudaMallocHost(&L.h_bb, Bp * 8) ||
+        cudaMallocHost(&L.h_tol2, Bp * 8) || cudaMallocHost(&L.h_ctl, 16 * sizeof(int)) ||
+        cudaMallocHost(&L.h_pre, Bp * 4) ||
+        cudaMallocHost(&L.h_assign, Bp * 4) || cudaMallocHost(&L.h_ret_iters, Bp * 4) ||
+        cudaMallocHost(&L.h_ret_status, Bp * 4) || cudaMallocHost(&L.h_ret_rr, Bp * 8) ||
+        cudaMallocHost(&L.h_idx, (size_t)Bp * Kmax * 4) || cudaMallocHost(&L.h_sc, (size_t)Bp * Kmax * 4) ||
+        cudaMallocHost(&L.h_st, Bp * sizeof(ColState))) {
         cudaGetLastError();
         return hd_fail(ctx, HD_ERR_OOM, "pinned host buffers");
     }
     return HD_OK;
 }
 
-// Move queued requests into free columns of lane L (lowest free slot first).
-static int lane_admit(hd_server* s, Lane& L, int32_t& iters) {
+// A request that needs no iteration (y = 0, or tol >= 1 so that x = 0
+// already meets it) finishes on the host: its x is 0, ranked as ids 0 .. K-1.
+static void finish_trivial(hd_server* s, Req* r, double now) {
+    r->iters = 0;
+    r->status = r->bb == 0.0 ? HD_COL_EMPTY : HD_COL_CONVERGED;
+    r->relres = r->bb == 0.0 ? 0.f : 1.f;
+    r->out_idx.resize(r->K);
+    r->out_score.assign(r->K, 0.f);
+    for (int32_t k = 0; k < r->K; ++k) r->out_idx[k] = k < s->g->n ? k : -1;
+    r->admit_s = r->done_s = now;
+    r->done = true;
+    s->finished.push_back(r->ticket);
+}
+
+// Stage up to a lane's width of queued requests for its next step: their
+// observations and ||y||^2, tol^2 ||y||^2, and U^T y on the device.
+static int lane_stage(hd_server* s, Lane& L) {
     hd_ctx* ctx = s->ctx;
-    L.nrec = 0;
+    L.staged.clear();
     int32_t off = 0;
-    for (int j = 0; j < L.slots && !s->queue.empty(); ++j) {
-        if (L.slot_req[j]) continue;
+    const double now = now_s();
+    while (!s->queue.empty() && (int32_t)L.staged.size() < L.slots) {
         Req* r = s->queue.front();
         if (off + (int32_t)r->idx.size() > L.cap_nnz) break;
         s->queue.pop_front();
-        r->slot = L.slot_base + j;
-        r->admit_s = now_s();
-        L.slot_req[j] = r;
-        AdmitRec& a = L.h_rec[L.nrec++];
-        a.slot = j;
-        a.off = off;
-        a.cnt = (int32_t)r->idx.size();
-        a.tol = r->tol;
-        a.bb = r->bb;
+        if (r->bb == 0.0 || r->bb <= (double)r->tol * r->tol * r->bb) {
+            finish_trivial(s, r, now);
+            continue;
+        }
+        const int c = (int)L.staged.size();
+        L.staged.push_back(r);
+        L.h_off[c] = off;
+        L.h_bb[c] = r->bb;
+        L.h_tol2[c] = (double)r->tol * (double)r->tol * r->bb;
         std::copy(r->idx.begin(), r->idx.end(), L.h_yidx + off);
         std::copy(r->val.begin(), r->val.end(), L.h_yval + off);
-        off += a.cnt;
+        off += (int32_t)r->idx.size();
     }
-    if (L.nrec) {
-        HD_CUDA(ctx, cudaMemcpyAsync(L.d_rec, L.h_rec, L.nrec * sizeof(AdmitRec), cudaMemcpyHostToDevice, ctx->stream));
-        HD_CUDA(ctx, cudaMemcpyAsync(L.d_yidx, L.h_yidx, (size_t)off * 4, cudaMemcpyHostToDevice, ctx->stream));
-        HD_CUDA(ctx, cudaMemcpyAsync(L.d_yval, L.h_yval, (size_t)off * 4, cudaMemcpyHostToDevice, ctx->stream));
-        k_admit_mark<<<ceil_div(L.nrec, 64), 64, 0, ctx->stream>>>(L.d_rec, L.nrec, L.E.st, L.E.num_active);
+    const int ns = (int)L.staged.size();
+    if (!ns) return HD_OK;
+    L.h_off[ns] = off;
+    HD_CUDA(ctx, cudaMemcpyAsync(L.d_off, L.h_off, (ns + 1) * 4, cudaMemcpyHostToDevice, ctx->stream));
+    HD_CUDA(ctx, cudaMemcpyAsync(L.d_yidx, L.h_yidx, (size_t)off * 4, cudaMemcpyHostToDevice, ctx->stream));
+    HD_CUDA(ctx, cudaMemcpyAsync(L.d_yval, L.h_yval, (size_t)off * 4, cudaMemcpyHostToDevice, ctx->stream));
+    HD_CUDA(ctx, cudaMemcpyAsync(L.d_bb, L.h_bb, ns * 8, cudaMemcpyHostToDevice, ctx->stream));
+    HD_CUDA(ctx, cudaMemcpyAsync(L.d_tol2, L.h_tol2, ns * 8, cudaMemcpyHostToDevice, ctx->stream));
+    const hd_eig* e = s->eig;
+    if (L.E.has_lr) {
+        const int rpad = L.rf.rpad;
+        if (e->sparse) {
+            k_stage_c_sparse<<<ceil_div(ns, 32), 32, 0, ctx->stream>>>(e->sp_rp, e->sp_col, e->sp_val, rpad, ns,
+                                                                       L.d_off, L.d_yidx, L.d_yval, L.d_C);
+        } else if (e->storage == HD_F32) {
+            k_stage_c<float><<<ns, 128, 0, ctx->stream>>>((const float*)e->U, e->scale, e->ldu, e->r, rpad, L.d_off,
+                                                          L.d_yidx, L.d_yval, L.d_C);
+        } else if (e->storage == HD_BF16) {
+            k_stage_c<__nv_bfloat16><<<ns, 128, 0, ctx->stream>>>((const __nv_bfloat16*)e->U, e->scale, e->ldu, e->r,
+                                                                  rpad, L.d_off, L.d_yidx, L.d_yval, L.d_C);
+        } else {
+            k_stage_c<__nv_fp8_e4m3><<<ns, 128, 0, ctx->stream>>>((const __nv_fp8_e4m3*)e->U, e->scale, e->ldu, e->r,
+                                                                  rpad, L.d_off, L.d_yidx, L.d_yval, L.d_C);
+        }
         HD_CHECK_LAUNCH(ctx);
-        if (iters < 1) iters = 1;  // the admission completes inside the next iteration
     }
     return HD_OK;
 }
 
-// `iters` CG iterations of lane L, then retirement of its stopped columns.
+// `iters` CG iterations of lane L; staged requests may be taken at the last
+// one's scalar step; then retirement: the rankings of the requests that
+// stopped, copied to the host.
 static int lane_step(hd_server* s, Lane& L, int32_t iters) {
     hd_ctx* ctx = s->ctx;
     Engine& E = L.E;
     const int32_t Bp = E.Bp;
-    const bool running = L.nrec > 0 || L.running();
-    if (!running) return HD_OK;
-    // the tensor-core products skip the columns above the highest occupied slot
-    // (admission fills the lowest free slots); per-column arithmetic is unchanged
-    int32_t live = 0;
+    const int ns = (int)L.staged.size();
+    if (!L.running() && ns == 0) return HD_OK;
+    if (ns > 0 && iters < 1) iters = 1;
+    // staged requests go first to the lowest free columns (assigned here), the
+    // rest to columns that stop in the last iteration; the tensor-core products
+    // skip the columns above `live`, the highest column that can be occupied
+    // (per-column arithmetic is unchanged)
+    int32_t live = 0, npre = 0;
     for (int j = 0; j < L.slots; ++j)
         if (L.slot_req[j]) live = j + 1;
+    if (ns > 0) {
+        for (int j = 0; j < Bp; ++j) {
+            L.h_pre[j] = -1;
+            if (j < L.slots && !L.slot_req[j] && npre < ns) {
+                L.h_pre[j] = npre++;
+                live = std::max(live, j + 1);
+            }
+        }
+        HD_CUDA(ctx, cudaMemcpyAsync(L.d_pre, L.h_pre, Bp * 4, cudaMemcpyHostToDevice, ctx->stream));
+    }
     E.lr.live = live;
-    // the narrowest slab that holds every occupied column (at most the width
-    // measured for the full lane): a lightly loaded lane gathers less per SpMM
-    // row.  Results do not depend on it: the reductions are chunked by rows,
-    // and every slab width sums a row's entries in the same order.
+    L.rf.live = live;
+    // the narrowest slab that holds every column that can be occupied (at most
+    // the width measured for the full lane): a lightly loaded lane gathers less
+    // per SpMM row.  Results do not depend on it: the reductions are chunked by
+    // rows, and every slab width sums a row's entries in the same order.
     int S = L.S_full;
     for (int c : {4, 8, 16, 32, 64, 128})
         if (c >= live && c <= L.S_full && Bp % c == 0) {
@@ -325,26 +435,64 @@ static int lane_step(hd_server* s, Lane& L, int32_t iters) {
             break;
         }
     if (S != E.vl.S) E.vl = vec_launch(ctx, E.n, Bp, S);
+    HD_CUDA(ctx, cudaMemsetAsync(L.rf.assign, 0xff, Bp * sizeof(int32_t), ctx->stream));
+    HD_CUDA(ctx, cudaMemsetAsync(L.d_ctl, 0, 2 * sizeof(int), ctx->stream));
     for (int t = 0; t < iters; ++t) {
-        int rc = engine_iteration(E, admit_cb, &L);
+        if (t == iters - 1 && ns > 0) {
+            // staged requests can be taken at the last iteration only: a column's
+            // stopped x must reach the host's ranking before an update resets it
+            L.h_ctl[0] = ns;
+            L.h_ctl[1] = npre;
+            HD_CUDA(ctx, cudaMemcpyAsync(L.d_ctl, L.h_ctl, 2 * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+        }
+        int rc = engine_iteration(E, refill_cb, &L);
         if (rc) return rc;
     }
     // ---- poll and retire
     HD_CUDA(ctx, cudaMemcpyAsync(L.h_st, E.st, Bp * sizeof(ColState), cudaMemcpyDeviceToHost, ctx->stream));
+    HD_CUDA(ctx, cudaMemcpyAsync(L.h_assign, L.rf.assign, Bp * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    HD_CUDA(ctx, cudaMemcpyAsync(L.h_ret_iters, L.rf.ret_iters, Bp * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    HD_CUDA(ctx, cudaMemcpyAsync(L.h_ret_status, L.rf.ret_status, Bp * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    HD_CUDA(ctx, cudaMemcpyAsync(L.h_ret_rr, L.rf.ret_rr, Bp * 8, cudaMemcpyDeviceToHost, ctx->stream));
     HD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     if (E.has_lr && lr_use_tensor_cores(E.lr.e)) {
         const int frc = lr_tc_check_flags(ctx);
         if (frc) return frc;
     }
+    const double t_step = now_s();
     std::vector<int32_t> Kc(Bp, 0);
-    std::vector<int> fin;
+    std::vector<std::pair<int, Req*>> fin;  // (column, request that stopped there)
+    std::vector<char> taken(ns, 0);
     for (int j = 0; j < L.slots; ++j) {
-        Req* r = L.slot_req[j];
-        if (r && !L.h_st[j].active && !L.h_st[j].fresh) {
-            Kc[j] = r->K;
-            fin.push_back(j);
+        Req* old = L.slot_req[j];
+        const int a = L.h_assign[j];
+        if (a >= 0 && a < ns) {
+            if (old) {
+                old->iters = L.h_ret_iters[j];
+                old->status = L.h_ret_status[j];
+                old->relres = old->bb > 0 ? (float)std::sqrt(L.h_ret_rr[j] / old->bb) : 0.f;
+                Kc[j] = old->K;
+                fin.push_back({j, old});
+            }
+            Req* r = L.staged[a];
+            r->slot = L.slot_base + j;
+            r->admit_s = t_step;
+            L.slot_req[j] = r;
+            taken[a] = 1;
+        } else if (old && !L.h_st[j].active) {
+            const ColState& c = L.h_st[j];
+            old->iters = c.iters;
+            old->status = c.status;
+            old->relres = c.bb > 0 ? (float)std::sqrt(c.rr / c.bb) : 0.f;
+            Kc[j] = old->K;
+            fin.push_back({j, old});
+            L.slot_req[j] = nullptr;
         }
     }
+    // staged requests no column took go back to the front of the queue, in order
+    for (int a = ns - 1; a >= 0; --a)
+        if (!taken[a]) s->queue.push_front(L.staged[a]);
+    L.staged.clear();
     if (fin.empty()) return HD_OK;
     int rc;
     {
@@ -352,7 +500,8 @@ static int lane_step(hd_server* s, Lane& L, int32_t iters) {
         rc = hd_rank_impl(ctx, E.X, E.n, Bp, Bp, Kc.data(), s->Kmax, 0, L.d_idx, L.d_sc);
     }
     if (rc) return rc;
-    for (int j : fin) {
+    for (auto& f : fin) {
+        const int j = f.first;
         HD_CUDA(ctx, cudaMemcpyAsync(L.h_idx + (size_t)j * s->Kmax, L.d_idx + (size_t)j * s->Kmax,
                                      (size_t)s->Kmax * 4, cudaMemcpyDeviceToHost, ctx->stream));
         HD_CUDA(ctx, cudaMemcpyAsync(L.h_sc + (size_t)j * s->Kmax, L.d_sc + (size_t)j * s->Kmax,
@@ -360,34 +509,30 @@ static int lane_step(hd_server* s, Lane& L, int32_t iters) {
     }
     HD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     const double t_done = now_s();
-    for (int j : fin) {
-        Req* r = L.slot_req[j];
-        const ColState& c = L.h_st[j];
-        r->iters = c.iters;
-        r->status = c.status;
-        r->relres = c.bb > 0 ? (float)std::sqrt(c.rr / c.bb) : 0.f;
+    for (auto& f : fin) {
+        const int j = f.first;
+        Req* r = f.second;
         r->out_idx.assign(L.h_idx + (size_t)j * s->Kmax, L.h_idx + (size_t)j * s->Kmax + r->K);
         r->out_score.assign(L.h_sc + (size_t)j * s->Kmax, L.h_sc + (size_t)j * s->Kmax + r->K);
         r->done_s = t_done;
         r->done = true;
         s->finished.push_back(r->ticket);
-        L.slot_req[j] = nullptr;
     }
     return HD_OK;
 }
 
 // Launch, once, every kernel a lane can use later (one iteration per slab
-// width with no column active, so every kernel returns at once, and a ranking
-// with K = 0): the first launch of a kernel loads its module, which would
-// otherwise stall the first steps that need it; the ranking also reserves its
-// workspace at the lane's size here.
+// width with no column active and nothing staged, so every kernel returns at
+// once, and a ranking with K = 0): the first launch of a kernel loads its
+// module, which would otherwise stall the first steps that need it; the
+// ranking also reserves its workspace at the lane's size here.
 static int lane_warm(hd_server* s, Lane& L) {
     hd_ctx* ctx = s->ctx;
     Engine& E = L.E;
     for (int c : {4, 8, 16, 32, 64, 128}) {
         if (c > L.S_full || E.Bp % c) continue;
         E.vl = vec_launch(ctx, E.n, E.Bp, c);
-        int rc = engine_iteration(E, nullptr, nullptr);
+        int rc = engine_iteration(E, refill_cb, &L);
         if (rc) return rc;
     }
     E.vl = vec_launch(ctx, E.n, E.Bp, L.S_full);
@@ -482,16 +627,15 @@ int hd_serve_step(hd_server* s, int32_t iters, int32_t* busy) {
     if (!s || iters < 0) return HD_ERR_INVALID_ARG;
     Lane& W = s->lanes[0];
     Lane& N = s->lanes[1];
-    int32_t it[2] = {iters, iters};
-    // admission: a lightly loaded server uses the narrow lane
+    // staging: a lightly loaded server uses the narrow lane
     if (!s->queue.empty()) {
         const bool narrow = N.slots > 0 && !W.running() && (int32_t)s->queue.size() <= N.free_slots();
-        int rc = narrow ? lane_admit(s, N, it[1]) : lane_admit(s, W, it[0]);
+        int rc = lane_stage(s, narrow ? N : W);
         if (rc) return rc;
     }
     for (int l = 0; l < 2; ++l) {
         if (s->lanes[l].slots == 0) continue;
-        int rc = lane_step(s, s->lanes[l], it[l]);
+        int rc = lane_step(s, s->lanes[l], iters);
         if (rc) return rc;
     }
     if (busy) {

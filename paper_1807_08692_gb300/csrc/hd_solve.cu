@@ -17,6 +17,7 @@
 // restarted from x with r := b - A x (residual replacement, at most
 // MAX_CONFIRM times), and the true value is what the solve reports.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <vector>
@@ -52,16 +53,13 @@ __global__ void k_scatter_y(const int32_t* y_ptr, const int32_t* y_idx, const fl
     }
 }
 
-// True when some column of this block's S-column slab is active (or being
-// (re)admitted); with st == nullptr every slab works.
+// True when some column of this block's S-column slab is active; with
+// st == nullptr every slab works.
 template <int S>
-__device__ __forceinline__ bool slab_has_work(const ColState* st, bool include_fresh) {
+__device__ __forceinline__ bool slab_has_work(const ColState* st) {
     if (!st) return true;
     int w = 0;
-    if (threadIdx.x < S) {
-        const ColState& c = st[blockIdx.y * S + threadIdx.x];
-        w = c.active || (include_fresh && c.fresh);
-    }
+    if (threadIdx.x < S) w = st[blockIdx.y * S + threadIdx.x].active;
     return __syncthreads_or(w) != 0;
 }
 
@@ -84,7 +82,7 @@ __global__ void __launch_bounds__(256, 8) k_spmm(const int32_t* rp, const int32_
     constexpr int L = S / 4;
     constexpr int RPB = 256 / L;
     if (skip && *skip) return;
-    if (!slab_has_work<S>(st, false)) return;
+    if (!slab_has_work<S>(st)) return;
     const int g = (threadIdx.x & 31) % L;
     const int col = blockIdx.y * S + 4 * g;
     for (int64_t row = (int64_t)blockIdx.x * RPB + threadIdx.x / L; row < n; row += (int64_t)gridDim.x * RPB) {
@@ -147,7 +145,7 @@ __global__ void __launch_bounds__(256, 8) k_spmm(const int32_t* rp, const int32_
 __global__ void __launch_bounds__(256) k_spmm_w4(const int32_t* rp, const int32_t* ci, const float* wv,
                                                  const float* P, float* Q, int64_t n, int32_t ld, float c1, float c2,
                                                  const ColState* st) {
-    if (!slab_has_work<4>(st, false)) return;
+    if (!slab_has_work<4>(st)) return;
     const int lane = threadIdx.x & 31;
     const int col = blockIdx.y * 4;
     const int64_t nw = (int64_t)gridDim.x * 8;
@@ -288,7 +286,7 @@ __global__ void __launch_bounds__(256, 4) k_spmm_h(const int32_t* __restrict__ r
     constexpr int L = S / 8;
     constexpr int RPB = 256 / L;
     if (!*use_half) return;
-    if (!slab_has_work<S>(st, false)) return;
+    if (!slab_has_work<S>(st)) return;
     const int g = (threadIdx.x & 31) % L;
     const int col = blockIdx.y * S + 8 * g;
     float inv[8];
@@ -436,7 +434,7 @@ __global__ void __launch_bounds__(256) k_spmm_cols(const int64_t* __restrict__ o
                                                    const ColState* __restrict__ st) {
     constexpr int L = S / 4;
     constexpr int RPB = 256 / L;
-    if (!slab_has_work<S>(st, false)) return;
+    if (!slab_has_work<S>(st)) return;
     const int g = (threadIdx.x & 31) % L;
     const int col = blockIdx.y * S + 4 * g;
     for (int64_t row = (int64_t)blockIdx.x * RPB + threadIdx.x / L; row < n; row += (int64_t)gridDim.x * RPB) {
@@ -531,7 +529,7 @@ __global__ void __launch_bounds__(256, 8) k_spmm_seg(const int32_t* __restrict__
                                                   int first) {
     constexpr int L = S / 4;
     constexpr int RPB = 256 / L;
-    if (!slab_has_work<S>(st, false)) return;
+    if (!slab_has_work<S>(st)) return;
     const int g = (threadIdx.x & 31) % L;
     const int col = blockIdx.y * S + 4 * g;
     for (int64_t row = (int64_t)blockIdx.x * RPB + threadIdx.x / L; row < n; row += (int64_t)gridDim.x * RPB) {
@@ -614,8 +612,8 @@ int reduction_chunk_rows(int64_t n) {
 }
 
 // thread -> (chunk = blockIdx.x, quad, g); false when the quad has no column to work on
-__device__ __forceinline__ bool red_thread(int64_t n, int32_t ld, int rch, const ColState* st, bool include_fresh,
-                                           int64_t& r0, int64_t& r1, int& col, int& g) {
+__device__ __forceinline__ bool red_thread(int64_t n, int32_t ld, int rch, const ColState* st, int64_t& r0,
+                                           int64_t& r1, int& col, int& g) {
     const int nq = ld >> 2;
     const int qpb = nq < RQ ? nq : RQ;
     const int quad = blockIdx.y * RQ + (int)threadIdx.x % qpb;
@@ -627,7 +625,7 @@ __device__ __forceinline__ bool red_thread(int64_t n, int32_t ld, int rch, const
     if (!st) return true;
     bool w = false;
 #pragma unroll
-    for (int c = 0; c < 4; ++c) w |= st[col + c].active || (include_fresh && st[col + c].fresh);
+    for (int c = 0; c < 4; ++c) w |= st[col + c].active;
     return w;
 }
 
@@ -659,7 +657,7 @@ __global__ void __launch_bounds__(1024) k_colsq(const float* __restrict__ V, int
                                                 float2* __restrict__ part) {
     int64_t r0, r1;
     int col, g;
-    const bool work = red_thread(n, ld, rch, nullptr, false, r0, r1, col, g);
+    const bool work = red_thread(n, ld, rch, nullptr, r0, r1, col, g);
     KSum acc[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
     if (work)
         for (int64_t row = r0; row < r1; row += RG) {
@@ -678,7 +676,7 @@ __global__ void __launch_bounds__(1024) k_dot(const float* __restrict__ P, const
                                               const ColState* __restrict__ st) {
     int64_t r0, r1;
     int col, g;
-    const bool work = red_thread(n, ld, rch, st, false, r0, r1, col, g);
+    const bool work = red_thread(n, ld, rch, st, r0, r1, col, g);
     KSum acc[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
     if (work)
         for (int64_t row = r0; row < r1; row += RG) {
@@ -698,27 +696,28 @@ __global__ void __launch_bounds__(1024) k_update(float* __restrict__ X, float* _
                                                  float2* __restrict__ part) {
     int64_t r0, r1;
     int col, g;
-    const bool work = red_thread(n, ld, rch, st, true, r0, r1, col, g);
+    const bool work = red_thread(n, ld, rch, st, r0, r1, col, g);
     KSum acc[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
     if (work) {
         const float a0 = (float)st[col].a, a1 = (float)st[col + 1].a, a2 = (float)st[col + 2].a,
                     a3 = (float)st[col + 3].a;
         const float x0 = xs * a0, x1 = xs * a1, x2 = xs * a2, x3 = xs * a3;
-        // a column being (re)admitted starts from x = 0, r = 0 (its y is scattered next)
-        const bool f0 = st[col].fresh, f1 = st[col + 1].fresh, f2 = st[col + 2].fresh, f3 = st[col + 3].fresh;
-        const bool any_fresh = f0 | f1 | f2 | f3;
+        // a served column that took a new request at the last scalar step starts
+        // from x0 = 0, r0 = y: x = a p, r = -a q here, y is added next
+        const bool f0 = st[col].refill, f1 = st[col + 1].refill, f2 = st[col + 2].refill, f3 = st[col + 3].refill;
+        const bool any_refill = f0 | f1 | f2 | f3;
         for (int64_t row = r0; row < r1; row += RG) {
             const int64_t o = row * ld + col;
             const float4 p = ld4v(P + o), q = ld4v(Q + o);
             float4 x = ld4v(X + o), r = ld4v(R + o);
-            x.x = fmaf(x0, p.x, x.x); x.y = fmaf(x1, p.y, x.y); x.z = fmaf(x2, p.z, x.z); x.w = fmaf(x3, p.w, x.w);
-            r.x = fmaf(-a0, q.x, r.x); r.y = fmaf(-a1, q.y, r.y); r.z = fmaf(-a2, q.z, r.z); r.w = fmaf(-a3, q.w, r.w);
-            if (any_fresh) {
+            if (any_refill) {
                 if (f0) x.x = r.x = 0.0f;
                 if (f1) x.y = r.y = 0.0f;
                 if (f2) x.z = r.z = 0.0f;
                 if (f3) x.w = r.w = 0.0f;
             }
+            x.x = fmaf(x0, p.x, x.x); x.y = fmaf(x1, p.y, x.y); x.z = fmaf(x2, p.z, x.z); x.w = fmaf(x3, p.w, x.w);
+            r.x = fmaf(-a0, q.x, r.x); r.y = fmaf(-a1, q.y, r.y); r.z = fmaf(-a2, q.z, r.z); r.w = fmaf(-a3, q.w, r.w);
             st4(X + o, x);
             st4(R + o, r);
             ksum_add(acc[0], r.x * r.x);
@@ -736,19 +735,21 @@ __global__ void __launch_bounds__(256) k_direction(float* __restrict__ P, const 
                                                    int32_t ld, const ColState* __restrict__ st) {
     constexpr int L = S / 4;
     constexpr int RPB = 256 / L;
-    if (!slab_has_work<S>(st, false)) return;
+    if (!slab_has_work<S>(st)) return;
     const int g = (threadIdx.x & 31) % L;
     const int col = blockIdx.y * S + 4 * g;
     const float b0 = (float)st[col].beta, b1 = (float)st[col + 1].beta, b2 = (float)st[col + 2].beta,
                 b3 = (float)st[col + 3].beta;
+    // a served column that just took a new request: p0 = y, added after this
+    const bool f0 = st[col].refill, f1 = st[col + 1].refill, f2 = st[col + 2].refill, f3 = st[col + 3].refill;
     for (int64_t row = (int64_t)blockIdx.x * RPB + threadIdx.x / L; row < n; row += (int64_t)gridDim.x * RPB) {
         const int64_t o = row * ld + col;
         const float4 r = ld4v(R + o);
         float4 p = ld4v(P + o);
-        p.x = b0 == 0.0f ? r.x : fmaf(b0, p.x, r.x);
-        p.y = b1 == 0.0f ? r.y : fmaf(b1, p.y, r.y);
-        p.z = b2 == 0.0f ? r.z : fmaf(b2, p.z, r.z);
-        p.w = b3 == 0.0f ? r.w : fmaf(b3, p.w, r.w);
+        p.x = b0 == 0.0f ? (f0 ? 0.0f : r.x) : fmaf(b0, p.x, r.x);
+        p.y = b1 == 0.0f ? (f1 ? 0.0f : r.y) : fmaf(b1, p.y, r.y);
+        p.z = b2 == 0.0f ? (f2 ? 0.0f : r.z) : fmaf(b2, p.z, r.z);
+        p.w = b3 == 0.0f ? (f3 ? 0.0f : r.w) : fmaf(b3, p.w, r.w);
         st4(P + o, p);
     }
 }
@@ -805,9 +806,11 @@ __global__ void k_fin_setup(const float2* part, int nblk, int32_t Bp, int32_t B,
     s.a = 0.0;
     s.beta = 0.0;
     s.iters = 0;
-    s.fresh = 0;
     s.confirms = 0;
     s.restart = 0;
+    s.refill = 0;
+    s.free_col = 0;
+    s.rr_fix = 0.0;
     if (j >= B || bb == 0.0) {
         s.active = 0;
         s.status = HD_COL_EMPTY;
@@ -852,37 +855,13 @@ __global__ void k_fin_rr(const float2* part, int nblk, int32_t Bp, ColState* st,
                          double theta2 = 0.0) {
     const int j = blockIdx.x;
     ColState& s = st[j];
-    const bool fresh = s.fresh, active = s.active;
-    if (!fresh && !active) {
+    if (!s.active) {
         if (threadIdx.x == 0) s.beta = 0.0;
         return;
     }
-    const double rr = fresh ? 0.0 : col_sum(part, nblk, Bp, j);
+    const double rr = col_sum(part, nblk, Bp, j);
     const double lrt = col_lowrank(C, coef, r, Bp, j);
     if (threadIdx.x != 0) return;
-    if (fresh) {
-        // (re)admitted column: r0 = y with ||y||^2 = bb set at admission
-        s.fresh = 0;
-        s.rr = s.bb;
-        s.rho = s.bb + lrt;
-        s.beta = 0.0;
-        s.a = 0.0;
-        s.iters = 0;
-        s.confirms = 0;
-        s.restart = 0;
-        if (s.bb == 0.0) {
-            s.active = 0;
-            s.status = HD_COL_EMPTY;
-        } else if (s.bb <= s.tol2) {
-            s.active = 0;
-            s.status = HD_COL_CONVERGED;
-        } else {
-            s.active = 1;
-            s.status = HD_COL_MAX_ITER;
-            atomicAdd(num_active, 1);
-        }
-        return;
-    }
     const double rho = rr + lrt;
     s.iters += 1;
     s.rr = rr;
@@ -902,6 +881,169 @@ __global__ void k_fin_rr(const float2* part, int nblk, int32_t Bp, ColState* st,
         atomicAdd(num_active, 1);
         if (use_half && !(rr <= theta2 * s.tol2)) atomicExch(use_half, 0);
     }
+}
+
+// sum_k coef_k c_k^2 for one contiguous row c (block-wide)
+__device__ __forceinline__ double row_lowrank(const double* c, const double* coef, int r) {
+    double v = 0.0;
+    if (c)
+        for (int k = threadIdx.x; k < r; k += blockDim.x) v += coef[k] * c[k] * c[k];
+    return block_sum_f64(v);
+}
+
+// The scalar step of a server lane (k_fin_rr plus admission inside the
+// iteration).  A free column the host assigned (the lowest free ones, so that
+// the occupied columns stay packed) takes its staged request, and a column that
+// stops here claims the next unassigned one: the stopped request's iterations,
+// status and ||r||^2 go to the
+// host, the column restarts as the new request (r0 = y, rho = y^T M^-1 y from
+// the staged U^T y) with `refill` set, so that the direction that follows
+// forms p0 = M^-1 y and the next update starts x and r afresh.  A stopped
+// column that claims nothing becomes free once the host has its ranking.
+// A refilled column's first ||r||^2 adds rr_fix (the y entries, exact).
+__global__ void k_fin_rr_serve(const float2* part, int nblk, int32_t Bp, ColState* st, int32_t max_iter,
+                               const double* C, const double* coef, int32_t r, int* num_active, Refill rf) {
+    __shared__ int claim;
+    const int j = blockIdx.x;
+    ColState& s = st[j];
+    const bool active = s.active, was_free = s.free_col;
+    if (!active && !was_free) {
+        if (threadIdx.x == 0) s.beta = 0.0;
+        return;
+    }
+    double rr = 0.0, lrt = 0.0;
+    if (active) {
+        rr = col_sum(part, nblk, Bp, j);
+        lrt = col_lowrank(C, coef, r, Bp, j);
+    }
+    if (threadIdx.x == 0) {
+        claim = -1;
+        bool stopped = was_free;
+        if (active) {
+            if (s.refill) {
+                rr += s.rr_fix;
+                s.refill = 0;
+            }
+            const double rho = rr + lrt;
+            s.iters += 1;
+            s.rr = rr;
+            s.beta = rho / s.rho;
+            s.rho = rho;
+            stopped = true;
+            if (!isfinite(rr)) {
+                s.active = 0;
+                s.status = HD_COL_BREAKDOWN;
+                s.beta = 0.0;
+            } else if (rr <= s.tol2) {
+                s.active = 0;
+                s.status = HD_COL_CONVERGED;
+            } else if (s.iters >= max_iter) {
+                s.active = 0;
+                s.status = HD_COL_MAX_ITER;
+            } else {
+                stopped = false;
+                atomicAdd(num_active, 1);
+            }
+        }
+        if (stopped) {
+            // a free column the host assigned takes its request; a column that
+            // stops here (or stopped earlier in the step) the next unassigned one
+            const int ns = *rf.nstage;
+            int c = INT_MAX;
+            if (ns > 0) {
+                const int pc = rf.pre[j];
+                c = pc >= 0 ? pc : j < rf.live ? atomicAdd(rf.next, 1) : INT_MAX;
+            }
+            if (c < ns) claim = c;
+            else if (active) s.free_col = 1;
+        }
+    }
+    __syncthreads();
+    const int c = claim;
+    if (c < 0) return;
+    const double lrs = row_lowrank(rf.C ? rf.C + (int64_t)c * rf.rpad : nullptr, coef, r);
+    if (threadIdx.x != 0) return;
+    // the request the column held (stopped here or at an earlier step's
+    // iteration; the host ignores these for a column it holds as free)
+    rf.ret_iters[j] = s.iters;
+    rf.ret_status[j] = s.status;
+    rf.ret_rr[j] = s.rr;
+    rf.assign[j] = c;
+    s.bb = rf.bb[c];
+    s.tol2 = rf.tol2[c];
+    s.rr = s.bb;
+    s.rho = s.bb + lrs;
+    s.beta = 0.0;
+    s.a = 0.0;
+    s.iters = 0;
+    s.confirms = 0;
+    s.restart = 0;
+    s.rr_fix = 0.0;
+    s.active = 1;
+    s.free_col = 0;
+    s.refill = 1;
+    s.status = HD_COL_MAX_ITER;
+    atomicAdd(num_active, 1);
+}
+
+// H = coef o (U^T y) for the columns that took a staged request (the operand
+// of the direction's U H; the other columns keep theirs)
+__global__ void k_refill_h(Refill rf, const double* coef, int rpad, int32_t Bp, float* H, __nv_bfloat16* Hhi,
+                           __nv_bfloat16* Hlo) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= (int64_t)rpad * Bp) return;
+    const int k = (int)(e / Bp), j = (int)(e % Bp);
+    const int c = rf.assign[j];
+    if (c < 0) return;
+    const double h = coef[k] * rf.C[(int64_t)c * rpad + k];
+    H[e] = (float)h;
+    if (Hhi) {
+        const __nv_bfloat16 hi = __double2bfloat16(h);
+        const __nv_bfloat16 lo = __double2bfloat16(h - (double)__bfloat162float(hi));
+        Hhi[(int64_t)j * rpad + k] = hi;
+        Hlo[(int64_t)j * rpad + k] = lo;
+    }
+}
+
+// p0 += y for the columns that took a staged request (the direction left
+// U D U^T y there, or 0 without eigenpairs); y is kept with the column for its
+// first update
+__global__ void k_refill_p(Refill rf, float* P, int32_t Bp) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= Bp) return;
+    const int c = rf.assign[j];
+    if (c < 0) return;
+    const int32_t b = rf.off[c], e = rf.off[c + 1];
+    for (int32_t t = b; t < e; ++t) {
+        const int32_t i = rf.yidx[t];
+        const float v = rf.yval[t];
+        P[(int64_t)i * Bp + j] += v;
+        rf.col_idx[(int64_t)j * REFILL_MAX_NNZ + (t - b)] = i;
+        rf.col_val[(int64_t)j * REFILL_MAX_NNZ + (t - b)] = v;
+    }
+    rf.col_cnt[j] = e - b;
+}
+
+// After the first update of a refilled column (r = -a q): r += y, and rr_fix =
+// sum over y's entries of (r_i + y_i)^2 - r_i^2 (fp64; duplicates in turn)
+__global__ void k_refill_r(Refill rf, float* R, int32_t Bp, ColState* st) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= Bp || !st[j].refill) return;
+    double fix = 0.0;
+    for (int t = 0; t < rf.col_cnt[j]; ++t) {
+        float* a = R + (int64_t)rf.col_idx[(int64_t)j * REFILL_MAX_NNZ + t] * Bp + j;
+        const float v = *a;
+        const float w = v + rf.col_val[(int64_t)j * REFILL_MAX_NNZ + t];
+        *a = w;
+        fix += (double)w * (double)w - (double)v * (double)v;
+    }
+    st[j].rr_fix = fix;
+}
+
+int launch_refill_r(Engine& E) {
+    k_refill_r<<<ceil_div(E.Bp, 128), 128, 0, E.ctx->stream>>>(*E.refill, E.R, E.Bp, E.st);
+    HD_CHECK_LAUNCH(E.ctx);
+    return HD_OK;
 }
 
 // Which residual kernel runs: the fp32 evaluation of b - A x has an error of
@@ -1118,11 +1260,17 @@ __global__ void __launch_bounds__(256) k_lr_expand_simt(const T* __restrict__ U,
     const int col = slab * 16 + cq;
     if (col >= Bp) return;
     float b0 = 0.f, b1 = 0.f, b2 = 0.f, b3 = 0.f;
+    bool f0 = false, f1 = false, f2 = false, f3 = false;
     if (op == EXP_DIRECTION) {
         b0 = (float)st[col].beta;
         b1 = (float)st[col + 1].beta;
         b2 = (float)st[col + 2].beta;
         b3 = (float)st[col + 3].beta;
+        // a served column that just took a new request drops r (p0 = U D U^T y + y)
+        f0 = st[col].refill;
+        f1 = st[col + 1].refill;
+        f2 = st[col + 2].refill;
+        f3 = st[col + 3].refill;
     }
     for (int64_t row = (int64_t)blockIdx.x * 64 + (threadIdx.x >> 2); row < n; row += (int64_t)gridDim.x * 64) {
         float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -1146,10 +1294,10 @@ __global__ void __launch_bounds__(256) k_lr_expand_simt(const T* __restrict__ U,
             v.x += acc.x; v.y += acc.y; v.z += acc.z; v.w += acc.w;
         } else {
             const float4 rr = ld4v(Rv + o), pp = ld4v(Pv + o);
-            v.x = rr.x + acc.x + (b0 == 0.0f ? 0.0f : b0 * pp.x);
-            v.y = rr.y + acc.y + (b1 == 0.0f ? 0.0f : b1 * pp.y);
-            v.z = rr.z + acc.z + (b2 == 0.0f ? 0.0f : b2 * pp.z);
-            v.w = rr.w + acc.w + (b3 == 0.0f ? 0.0f : b3 * pp.w);
+            v.x = (f0 ? 0.0f : rr.x) + acc.x + (b0 == 0.0f ? 0.0f : b0 * pp.x);
+            v.y = (f1 ? 0.0f : rr.y) + acc.y + (b1 == 0.0f ? 0.0f : b1 * pp.y);
+            v.z = (f2 ? 0.0f : rr.z) + acc.z + (b2 == 0.0f ? 0.0f : b2 * pp.z);
+            v.w = (f3 ? 0.0f : rr.w) + acc.w + (b3 == 0.0f ? 0.0f : b3 * pp.w);
         }
         st4(out + o, v);
     }
@@ -1515,6 +1663,33 @@ int tune_segments(hd_ctx* ctx, Engine& E) {
     } while (0)
 
 
+// The scalar step after the update (rr, convergence, beta; C / coef: the PCG
+// term): k_fin_rr, or for a server lane k_fin_rr_serve, which also installs
+// staged requests, followed by their U^T y into H for the direction.
+static int launch_fin_rr(Engine& S_, const double* C, const double* coef, int r) {
+    hd_ctx* ctx = S_.ctx;
+    const int32_t Bp = S_.Bp;
+    HD_PROF(ctx, "scalar");
+    HD_CUDA(ctx, cudaMemsetAsync(S_.num_active, 0, sizeof(int), ctx->stream));
+    if (S_.refill) {
+        k_fin_rr_serve<<<Bp, 128, 0, ctx->stream>>>(S_.part, (int)S_.nch, Bp, S_.st, S_.max_iter, C, coef, r,
+                                                   S_.num_active, *S_.refill);
+        HD_CHECK_LAUNCH(ctx);
+        if (S_.has_lr && S_.eff_mode == HD_MODE_PCG) {
+            const int64_t tot = (int64_t)S_.lr.rpad * Bp;
+            k_refill_h<<<ceil_div(tot, 256), 256, 0, ctx->stream>>>(*S_.refill, S_.dcoef, S_.lr.rpad, Bp, S_.lr.H,
+                                                                     S_.lr.Hhi, S_.lr.Hlo);
+            HD_CHECK_LAUNCH(ctx);
+        }
+        return HD_OK;
+    }
+    if (S_.use_half) HD_CUDA(ctx, cudaMemsetAsync(S_.use_half, 0xff, sizeof(int), ctx->stream));
+    k_fin_rr<<<Bp, 128, 0, ctx->stream>>>(S_.part, (int)S_.nch, Bp, S_.st, S_.max_iter, C, coef, r, S_.num_active,
+                                         S_.use_half, HALF_THETA * HALF_THETA);
+    HD_CHECK_LAUNCH(ctx);
+    return HD_OK;
+}
+
 // One CG iteration of every column (Eq. 20 operator, CG update, direction).
 // `after_update`, if given, runs right after the X/R update (the serving loop
 // scatters newly admitted observations there).
@@ -1538,13 +1713,12 @@ int engine_iteration(Engine& S_, int (*after_update)(void*), void* arg) {
     if (after_update && (rc = after_update(arg))) return rc;
         if ((rc = lr_reduce(ctx, S_.lr, S_.R, n, Bp, S_.num_active))) return rc;
         if ((rc = lr_finish(ctx, S_.lr, Bp, S_.dcoef))) return rc;
-        { HD_PROF(ctx, "scalar");
-        HD_CUDA(ctx, cudaMemsetAsync(S_.num_active, 0, sizeof(int), ctx->stream));
-        if (S_.use_half) HD_CUDA(ctx, cudaMemsetAsync(S_.use_half, 0xff, sizeof(int), ctx->stream));
-        k_fin_rr<<<Bp, 128, 0, ctx->stream>>>(S_.part, (int)S_.nch, Bp, S_.st, max_iter, Cd, S_.dcoef, r,
-                                             S_.num_active, S_.use_half, HALF_THETA * HALF_THETA); }
-        HD_CHECK_LAUNCH(ctx);
+        if ((rc = launch_fin_rr(S_, Cd, S_.dcoef, r))) return rc;
         if ((rc = lr_expand(ctx, S_.lr, EXP_DIRECTION, S_.P, S_.R, S_.P, n, Bp, S_.st, S_.num_active))) return rc;
+        if (S_.refill) {
+            k_refill_p<<<ceil_div(Bp, 128), 128, 0, ctx->stream>>>(*S_.refill, S_.P, Bp);
+            HD_CHECK_LAUNCH(ctx);
+        }
     } else {
         if (S_.ts)
         {
@@ -1563,13 +1737,12 @@ int engine_iteration(Engine& S_, int (*after_update)(void*), void* arg) {
         HD_CHECK_LAUNCH(ctx);
         if ((rc = launch_update(S_))) return rc;
     if (after_update && (rc = after_update(arg))) return rc;
-        { HD_PROF(ctx, "scalar");
-        HD_CUDA(ctx, cudaMemsetAsync(S_.num_active, 0, sizeof(int), ctx->stream));
-        if (S_.use_half) HD_CUDA(ctx, cudaMemsetAsync(S_.use_half, 0xff, sizeof(int), ctx->stream));
-        k_fin_rr<<<Bp, 128, 0, ctx->stream>>>(S_.part, (int)S_.nch, Bp, S_.st, max_iter, nullptr, nullptr, 0,
-                                             S_.num_active, S_.use_half, HALF_THETA * HALF_THETA); }
-        HD_CHECK_LAUNCH(ctx);
+        if ((rc = launch_fin_rr(S_, nullptr, nullptr, 0))) return rc;
         LAUNCH_VEC(k_direction, S_.P, S_.R, n, Bp, S_.st);
+        if (S_.refill) {
+            k_refill_p<<<ceil_div(Bp, 128), 128, 0, ctx->stream>>>(*S_.refill, S_.P, Bp);
+            HD_CHECK_LAUNCH(ctx);
+        }
         if (lr_on) {
             if ((rc = lr_reduce(ctx, S_.lr, S_.P, n, Bp, S_.num_active))) return rc;
             if ((rc = lr_finish(ctx, S_.lr, Bp, S_.opcoef))) return rc;

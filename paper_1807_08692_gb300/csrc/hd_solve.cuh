@@ -16,11 +16,41 @@ struct ColState {
     int active;
     int iters;
     int status;
-    int fresh;      // 1: the column was just (re)admitted; the update resets it and
-                    // the next scalar step starts its iteration from r0 = y (bb given)
     int confirms;   // residual replacements so far (true residual above tol at a stop)
     int restart;    // 1: r was just replaced by b - A x; the direction restarts from it
+    // serving (continuous batching inside the iteration):
+    int refill;     // 1: a request was installed at the last scalar step; the direction
+                    // that follows drops R (p0 = M^-1 y), the next update starts x, r afresh
+    int free_col;   // 1: no request holds the column (it may take a staged one)
+    double rr_fix;  // ||y - a q||^2 - ||a q||^2 of a refilled column's first update (exact)
 };
+
+// Requests staged for a server lane's next scalar step: a column that stops
+// there (or is free) takes the next one (atomic claim), its old request's
+// statistics are kept for the host, and the iteration's direction forms the
+// new request's p0 = M^-1 y.  Device pointers; all null outside the server.
+struct Refill {
+    const int32_t* off = nullptr;     // staged request s: entries off[s] .. off[s + 1]
+    const int32_t* yidx = nullptr;    // of yidx / yval
+    const float* yval = nullptr;
+    const double* bb = nullptr;       // ||y_s||^2
+    const double* tol2 = nullptr;     // tol_s^2 ||y_s||^2
+    const double* C = nullptr;        // [nstage][rpad] U^T y_s (with eigenpairs)
+    const int* nstage = nullptr;
+    const int32_t* pre = nullptr;     // [Bp] staged request given to a free column by the host (-1: none)
+    int* next = nullptr;              // the next staged request for a column that stops (starts after
+                                      // the host's assignments)
+    int32_t* assign = nullptr;        // [Bp] staged request installed in column j (-1: none)
+    int32_t* ret_iters = nullptr;     // [Bp] iterations / status / ||r||^2 of the request
+    int32_t* ret_status = nullptr;    //      column j gave up for the new one
+    double* ret_rr = nullptr;
+    int32_t* col_cnt = nullptr;       // [Bp] the installed request's y, kept per column
+    int32_t* col_idx = nullptr;       // [Bp][REFILL_MAX_NNZ]
+    float* col_val = nullptr;
+    int32_t rpad = 0;
+    int32_t live = 0;                 // columns at or above this take no request from `next`
+};
+constexpr int REFILL_MAX_NNZ = 512;
 
 // Low-rank product helpers (storage-specific implementations).
 //  reduce: part[c][k][j] = sum over rows of chunk c of U[i][k] * V[i][j]
@@ -112,6 +142,7 @@ struct Engine {
     // only: the decision covers the whole batch, so a column's bits would
     // depend on its neighbours, which the server avoids)
     bool allow_half = false;
+    const Refill* refill = nullptr;   // a server lane: requests installed inside the iteration
     __half* P16 = nullptr;      // n x Bp
     unsigned* p16_max = nullptr;  // [Bp] max |P_j| as float bits
     int* use_half = nullptr;    // 1: the next SpMM gathers P16
@@ -134,6 +165,9 @@ int simt_nchunk(hd_ctx* ctx, int64_t n, int rpad, int Bp);
 // (graph, Bp) over K in {1, 2, 4, 8} (HD_SEGMENTS overrides); sets E.segK / E.seg.
 int tune_segments(hd_ctx* ctx, Engine& E);
 int engine_iteration(Engine& E, int (*after_update)(void*), void* arg);
+// r += y for the columns of a server lane that took a request at the last
+// scalar step (after their first update), with the exact ||r||^2 correction
+int launch_refill_r(Engine& E);
 // rows per reduction chunk for n rows, and the engine's chunk count from it
 int reduction_chunk_rows(int64_t n);
 void engine_set_reduction(Engine& E);

@@ -170,10 +170,12 @@ __global__ void __launch_bounds__(256) k_sp_expand(const int64_t* __restrict__ r
         const float4 rr = ld4c(Rv + o), pp = ld4c(Pv + o);
         const float b0 = (float)st[cq].beta, b1 = (float)st[cq + 1].beta;
         const float b2 = (float)st[cq + 2].beta, b3 = (float)st[cq + 3].beta;
-        v.x = rr.x + acc.x + (b0 == 0.0f ? 0.0f : b0 * pp.x);
-        v.y = rr.y + acc.y + (b1 == 0.0f ? 0.0f : b1 * pp.y);
-        v.z = rr.z + acc.z + (b2 == 0.0f ? 0.0f : b2 * pp.z);
-        v.w = rr.w + acc.w + (b3 == 0.0f ? 0.0f : b3 * pp.w);
+        // a served column that just took a new request drops r (p0 = U D U^T y + y)
+        const bool f0 = st[cq].refill, f1 = st[cq + 1].refill, f2 = st[cq + 2].refill, f3 = st[cq + 3].refill;
+        v.x = (f0 ? 0.0f : rr.x) + acc.x + (b0 == 0.0f ? 0.0f : b0 * pp.x);
+        v.y = (f1 ? 0.0f : rr.y) + acc.y + (b1 == 0.0f ? 0.0f : b1 * pp.y);
+        v.z = (f2 ? 0.0f : rr.z) + acc.z + (b2 == 0.0f ? 0.0f : b2 * pp.z);
+        v.w = (f3 ? 0.0f : rr.w) + acc.w + (b3 == 0.0f ? 0.0f : b3 * pp.w);
     }
     *reinterpret_cast<float4*>(out + o) = v;
 }

@@ -159,9 +159,9 @@ def test_narrow_and_wide_lanes_agree(gpu_ctx, served):
 
 
 def test_served_request_equals_batch_solve(gpu_ctx, served):
-    # a request alone takes one admission iteration (its column is reset, y is
-    # scattered in and z0 = M^-1 y formed) and then the batch solver's PCG
-    # iterations for the same y, with the same ranking
+    # a request alone is taken by a free column at the scalar step of one
+    # iteration (whose direction forms z0 = M^-1 y) and then runs the batch
+    # solver's PCG iterations for the same y, with the same ranking
     import paper_1807_08692_gb300 as hd
     g, eig, reqs = served
     srv = hd.Server(gpu_ctx, g, eig, "pcg", 0.99, max_slots=8, max_iter=500, Kmax=20)
@@ -180,6 +180,57 @@ def test_served_request_equals_batch_solve(gpu_ctx, served):
         x = X[:, 0].cpu().numpy().astype(np.float64)
         ref, _ = ORank.topk(x, 20)
         assert ORank.ranks_match(res[0], ref, x, 1e-5 * x.max(), scores=res[1], x=x, score_tol=1e-3)
+    srv.close()
+
+
+def test_stopping_column_takes_the_next_request(gpu_ctx, served):
+    # one column: the request queued behind another is taken at the scalar step
+    # of the iteration where its predecessor stops, so the column never idles
+    # between them, and its result is the same bits as alone
+    import paper_1807_08692_gb300 as hd
+    g, eig, reqs = served
+    srv = hd.Server(gpu_ctx, g, eig, "pcg", 0.99, max_slots=1, max_iter=500, Kmax=20)
+    assert srv.slots == 1
+    alone = _run(srv, [(0, *reqs[21], 1e-6, 20)], iters=1)[0]
+    srv.completed()
+    ta = srv.submit(*reqs[20], 1e-4, 20)
+    tb = srv.submit(*reqs[21], 1e-6, 20)
+    done, step = {}, 0
+    while len(done) < 2 and step < 300:
+        srv.step(1)
+        step += 1
+        for tk in srv.completed():
+            done[tk] = (step, srv.poll(tk, 20))
+    (sa, ra), (sb, rb) = done[ta], done[tb]
+    assert ra[2]["status"] == 0 and rb[2]["status"] == 0
+    assert sa == ra[2]["iters"] + 1
+    assert sb == sa + rb[2]["iters"]
+    assert ra[2]["slot"] == rb[2]["slot"] == 0
+    assert np.array_equal(rb[0], alone[0])
+    assert np.array_equal(rb[1].view(np.uint32), alone[1].view(np.uint32))
+    assert rb[2]["iters"] == alone[2]["iters"]
+    srv.close()
+
+
+def test_requests_that_need_no_iteration(gpu_ctx, served):
+    # y = 0 and tol >= 1 finish at staging with x = 0: ids 0 .. K-1, score 0
+    import paper_1807_08692_gb300 as hd
+    g, eig, reqs = served
+    srv = hd.Server(gpu_ctx, g, eig, "pcg", 0.99, max_slots=4, max_iter=500, Kmax=20)
+    t0 = srv.submit(np.zeros(0, np.int32), np.zeros(0, np.float32), 1e-6, 5)
+    t1 = srv.submit(np.array([3, 3], np.int32), np.array([1.0, -1.0], np.float32), 1e-6, 5)
+    t2 = srv.submit(*reqs[4], 1.0, 5)
+    t3 = srv.submit(*reqs[4], 1e-4, 5)
+    srv.step(1)
+    for t, status in ((t0, hd.COL_EMPTY), (t1, hd.COL_EMPTY), (t2, hd.COL_CONVERGED)):
+        ids, sc, st = srv.poll(t, 5)
+        assert st["status"] == status and st["iters"] == 0
+        assert list(ids) == [0, 1, 2, 3, 4] and not sc.any()
+    assert srv.poll(t3, 5) is None
+    while srv.step(1):
+        pass
+    ids, sc, st = srv.poll(t3, 5)
+    assert st["status"] == 0 and st["iters"] > 0
     srv.close()
 
 
