@@ -214,8 +214,8 @@ static int lane_open(hd_ctx* ctx, const hd_graph* g, const hd_eig* eig, double a
     E.c2 = (float)(alpha / (1.0 - alpha));
     E.xs = 1.0f;
     E.max_iter = max_iter;
-    // one SpMM order in every lane: thread-per-row sums, a single pass
-    E.warp_rows = false;
+    // one SpMM order in every lane: k_spmm's thread-per-row sums, one pass
+    E.narrow4 = false;
     E.segK = 1;
     E.seg = nullptr;
     const int32_t Bp = E.Bp;

@@ -124,10 +124,10 @@ struct Engine {
     int rch = 64;                      // rows per reduction chunk (depends on n only)
     int64_t nch = 0;                   // reduction chunks: column partials are [nch][Bp]
     int segK = 1;                      // SpMM node-range segments (1: one pass)
-    // 4-column slabs may use the warp-per-row SpMM (its sums run in another
-    // order than the other slab widths'; the server keeps one order throughout)
-    bool warp_rows = true;
     const int32_t* seg = nullptr;      // their row bounds [segK + 1][n]
+    // a 4-column batch may use k_spmm_n4 (its sums run in another order than
+    // k_spmm's; the server keeps one order at every lane width)
+    bool narrow4 = true;
     float *R = nullptr, *P = nullptr, *Q = nullptr, *X = nullptr;
     float2* part = nullptr;
     ColState* st = nullptr;

@@ -336,15 +336,23 @@ def test_small_batches(gpu_ctx, g1, cfg1_data, B):
 
 
 def test_results_independent_of_slab_width(gpu_ctx, cfg1_data, tmp_path):
-    # column sums are chunked by rows, so the slab width of the vector kernels
-    # (HD_SLAB caps it) leaves every score bit-for-bit unchanged
+    # the SpMM sums a row in the same order at every slab width (each lane
+    # over the whole row), and column sums are chunked by rows, so the slab
+    # width (HD_SLAB caps it) leaves every score bit-for-bit unchanged; 32
+    # columns (the observations twice, the second copy halved) so that 4-, 16-
+    # and 32-column slabs are all possible
     import os
     import subprocess
     import sys
     here = os.path.dirname(os.path.abspath(__file__))
     rp, col, val = csr_of(cfg1_data["A"])
-    np.savez(tmp_path / "case.npz", rp=rp, col=col, val=val, yp=cfg1_data["yp"], yi=cfg1_data["yi"],
-             yv=cfg1_data["yv"], lam=cfg1_data["lam"][:30], U=cfg1_data["U"][:, :30])
+    yp0, yi0, yv0 = cfg1_data["yp"], cfg1_data["yi"], cfg1_data["yv"]
+    yp = np.concatenate([yp0, yp0[1:] + yp0[-1]])
+    yi = np.concatenate([yi0, yi0])
+    yv = np.concatenate([yv0, np.float32(0.5) * yv0])
+    assert len(yp) - 1 == 32
+    np.savez(tmp_path / "case.npz", rp=rp, col=col, val=val, yp=yp, yi=yi, yv=yv, lam=cfg1_data["lam"][:30],
+             U=cfg1_data["U"][:, :30])
     script = (
         "import sys, numpy as np\n"
         f"sys.path.insert(0, {os.path.dirname(here)!r}); sys.path.insert(0, {here!r})\n"
@@ -357,12 +365,13 @@ def test_results_independent_of_slab_width(gpu_ctx, cfg1_data, tmp_path):
         "X, it, rr, st = hd.query_batch(ctx, g, eig, 'pcg', *y_arrays(z['yp'], z['yi'], z['yv']), 0.99, 1e-6, 500)\n"
         "np.save(sys.argv[1], X.cpu().numpy())\n")
     out = []
-    for S in (8, 16):
+    for S in (4, 16, 32):
         env = dict(os.environ, HD_SLAB=str(S))
         f = tmp_path / f"x{S}.npy"
         subprocess.run([sys.executable, "-c", script, str(f)], env=env, check=True, timeout=300)
         out.append(np.load(f))
-    assert np.array_equal(out[0].view(np.uint32), out[1].view(np.uint32))
+    for o in out[1:]:
+        assert np.array_equal(out[0].view(np.uint32), o.view(np.uint32))
 
 
 def test_half_gathers_in_late_iterations(gpu_ctx, cfg1_data, tmp_path):
