@@ -99,6 +99,11 @@ class Clocks:
             return
         self.thread = threading.Thread(target=self._read, daemon=True)
         self.thread.start()
+        # nvidia-smi's start-up (driver queries) must not overlap the timed
+        # steps: wait for its first sample (at most 3 s)
+        t0 = time.time()
+        while not self.samples and time.time() - t0 < 3.0 and self.proc.poll() is None:
+            time.sleep(0.01)
 
     def _read(self):
         for line in self.proc.stdout:

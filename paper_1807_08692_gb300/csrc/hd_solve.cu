@@ -69,11 +69,97 @@ __device__ __forceinline__ bool slab_has_work(const ColState* st) {
     acc_.z = fmaf(wt_, vec_.z, acc_.z);       \
     acc_.w = fmaf(wt_, vec_.w, acc_.w)
 
-// Q = c1 P - c2 W P for the S-column slab blockIdx.y.  The P^T Q partials of
-// CG come from k_dot below: kept out of this kernel, its register count allows
-// eight 256-thread blocks per SM, and the extra warps keep more of the random
-// row gathers in flight (measured on the 1M-node graph: 1.58 ms + 0.08 ms for
-// the separate pass against 2.06 ms with the partials fused).
+// 4-column slabs: two lanes per row, which compute the same two chains as a
+// thread per row (chain s: entries 8c + {0, 2, 4, 6} of the full chunks of 8,
+// then every tail entry in order; chain s2: entries 8c + {1, 3, 5, 7}; the row
+// sum s + s2), so the bits do not change; the pairs halve each lane's serial
+// gathers and read the row's indices two at a time (0.28 ms against 0.38 ms
+// on the 1M-node graph, the same bits).  128 rows per block step.
+__device__ __forceinline__ void spmm_rows_pair4(const int32_t* rp, const int32_t* ci, const float* wv,
+                                                const float* P, float* Q, int64_t n, int32_t ld, float c1, float c2) {
+    const int lane = threadIdx.x & 31, h = lane & 1;
+    const int col = blockIdx.y * 4;
+    // rows advance warp-uniformly (the shuffle needs every lane); a lane past
+    // the last row works on an empty row and writes nothing
+    for (int64_t r0 = (int64_t)blockIdx.x * 128 + (threadIdx.x >> 5) * 16; r0 < n; r0 += (int64_t)gridDim.x * 128) {
+        const int64_t row = r0 + (lane >> 1);
+        const bool ok = row < n;
+        const int32_t b = ok ? rp[row] : 0, e = ok ? rp[row + 1] : 0;
+        const int32_t full = b + (e - b) / 8 * 8;
+        float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+        int32_t t = b;
+        for (; t + 16 <= full; t += 16) {  // two chunks: this lane's 8 entries
+            float w[8];
+            float4 v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int32_t k = t + 2 * u + h;
+                w[u] = __ldg(wv + k);
+                v[u] = ld4(P + (int64_t)__ldg(ci + k) * ld + col);
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                FMA4(s, w[u], v[u]);
+            }
+        }
+        if (t < full) {  // one chunk left
+            float w[4];
+            float4 v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int32_t k = t + 2 * u + h;
+                w[u] = __ldg(wv + k);
+                v[u] = ld4(P + (int64_t)__ldg(ci + k) * ld + col);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                FMA4(s, w[u], v[u]);
+            }
+            t += 8;
+        }
+        if (h == 0) {  // the tail belongs to chain s, in masked batches of 4
+            for (; t < e; t += 4) {
+                const int m = e - t;
+                float4 v[4];
+                float w[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    w[u] = u < m ? __ldg(wv + t + u) : 0.f;
+                    v[u] = u < m ? ld4(P + (int64_t)__ldg(ci + t + u) * ld + col) : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (u < m) {
+                        FMA4(s, w[u], v[u]);
+                    }
+                }
+            }
+        }
+        const float ox = __shfl_xor_sync(0xffffffffu, s.x, 1), oy = __shfl_xor_sync(0xffffffffu, s.y, 1);
+        const float oz = __shfl_xor_sync(0xffffffffu, s.z, 1), ow = __shfl_xor_sync(0xffffffffu, s.w, 1);
+        if (ok && h == 0) {
+            s.x += ox;
+            s.y += oy;
+            s.z += oz;
+            s.w += ow;
+            const float4 own = ld4(P + row * ld + col);
+            float4 q;
+            q.x = c1 * own.x - c2 * s.x;
+            q.y = c1 * own.y - c2 * s.y;
+            q.z = c1 * own.z - c2 * s.z;
+            q.w = c1 * own.w - c2 * s.w;
+            st4(Q + row * ld + col, q);
+        }
+    }
+}
+
+// Q = c1 P - c2 W P for the S-column slab blockIdx.y: S/4 threads per row, each
+// over all of the row's entries (chains as above), 8 gathers in flight.  The
+// P^T Q partials of CG come from k_dot below: kept out of this kernel, its
+// register count allows eight 256-thread blocks per SM, and the extra warps
+// keep more of the random row gathers in flight (measured on the 1M-node graph:
+// 1.58 ms + 0.08 ms for the separate pass against 2.06 ms with the partials
+// fused).  The summation order is the same at every slab width.
 // `skip` (may be null): the launch returns at once when *skip is not 0.
 template <int S>
 __global__ void __launch_bounds__(256, 8) k_spmm(const int32_t* rp, const int32_t* ci, const float* wv, const float* P,
@@ -83,6 +169,10 @@ __global__ void __launch_bounds__(256, 8) k_spmm(const int32_t* rp, const int32_
     constexpr int RPB = 256 / L;
     if (skip && *skip) return;
     if (!slab_has_work<S>(st)) return;
+    if constexpr (S == 4) {
+        spmm_rows_pair4(rp, ci, wv, P, Q, n, ld, c1, c2);
+        return;
+    }
     const int g = (threadIdx.x & 31) % L;
     const int col = blockIdx.y * S + 4 * g;
     for (int64_t row = (int64_t)blockIdx.x * RPB + threadIdx.x / L; row < n; row += (int64_t)gridDim.x * RPB) {
