@@ -896,7 +896,12 @@ def main():
                 "profiled_launches_per_step": round(hprof["launches"] / prof_steps, 1),
                 "families_ms": {f: round(v[1], 3) for f, v in fam.items()},
                 "families_launches": {f: v[0] for f, v in fam.items()},
-                "families_busy_launches": {f: v[2] for f, v in fam.items()}}
+                "families_busy_launches": {f: v[2] for f, v in fam.items()},
+                # each iteration launches the fp32 and the fp16-gather SpMM and
+                # one of them returns at once (the choice is made on the
+                # device): busy launches of both per CG iteration run
+                "spmm_busy_per_iteration": round((fam["spmm"][2] + fam["spmm_h"][2])
+                                                 / max(1, int(hprof["iters"].max()) * prof_steps), 3)}
     # ---- CPU baseline: the oracle on host cores, bounded sample
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:

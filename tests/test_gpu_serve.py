@@ -287,3 +287,56 @@ def test_non_finite_observations_rejected(gpu_ctx, served):
     # the context stays usable
     X, it, rr, st = hd.query_batch(gpu_ctx, g, eig, "pcg", y_ptr, i, v, 0.99, 1e-6, 500)
     assert st[0] == 0
+
+
+def test_random_traffic_with_cancellations(gpu_ctx, served):
+    # 60 requests at seeded random steps with mixed tolerances and K, a queue
+    # longer than the free columns at times (staged requests that no column
+    # takes go back to the queue), 1 or 3 iterations per step, and 8 requests
+    # cancelled while queued or running: every ticket is reported once, the
+    # cancelled ones with status CANCELLED, and every other request gets the
+    # bits it gets alone
+    import paper_1807_08692_gb300 as hd
+    g, eig, reqs = served
+    rng = np.random.default_rng(1807)
+    n_req = 60
+    at = np.sort(rng.integers(0, 40, n_req))
+    tols = rng.choice([1e-2, 1e-4, 1e-6], n_req)
+    Ks = rng.choice([5, 20, 50], n_req)
+    which = rng.integers(0, len(reqs), n_req)
+    cancel_at = {int(p): int(at[p] + rng.integers(0, 6)) for p in rng.choice(n_req, 8, replace=False)}
+    srv = hd.Server(gpu_ctx, g, eig, "pcg", 0.99, max_slots=8, max_iter=500, Kmax=50)
+    tickets, out, seen = {}, {}, []
+    step = 0
+    while (len(tickets) < n_req or len(out) < n_req) and step < 3000:
+        for p in range(n_req):
+            if at[p] == step and p not in tickets:
+                tickets[p] = srv.submit(*reqs[which[p]], float(tols[p]), int(Ks[p]))
+        for p, s in cancel_at.items():
+            if s == step and p in tickets and p not in out:
+                srv.cancel(tickets[p])
+        srv.step(1 + 2 * (step % 5 == 4))
+        for t in srv.completed():
+            seen.append(t)
+        for p, t in tickets.items():
+            if p not in out and t in seen:
+                res = srv.poll(t, int(Ks[p]))
+                assert res is not None
+                out[p] = res
+        step += 1
+    assert len(out) == n_req and sorted(seen) == sorted(tickets.values())
+    assert len(set(seen)) == len(seen)
+    srv.close()
+    cancelled = [p for p in range(n_req) if out[p][2]["status"] == hd.COL_CANCELLED]
+    assert set(cancelled) <= set(cancel_at)
+    solo = hd.Server(gpu_ctx, g, eig, "pcg", 0.99, max_slots=8, max_iter=500, Kmax=50)
+    for p in range(n_req):
+        if p in cancelled:
+            continue
+        ids, sc, st = out[p]
+        assert st["status"] == 0
+        a_ids, a_sc, a_st = _run(solo, [(0, *reqs[which[p]], float(tols[p]), int(Ks[p]))], iters=1)[0]
+        assert np.array_equal(ids, a_ids), p
+        assert np.array_equal(sc.view(np.uint32), a_sc.view(np.uint32)), p
+        assert st["iters"] == a_st["iters"], p
+    solo.close()
