@@ -173,8 +173,8 @@ static void lane_free(hd_ctx* ctx, Lane& L) {
     if (ctx) cudaStreamSynchronize(ctx->stream);
     cudaFree(L.dev);
     for (void* h : {(void*)L.h_off, (void*)L.h_yidx, (void*)L.h_yval, (void*)L.h_bb, (void*)L.h_tol2,
-                    (void*)L.h_ctl, (void*)L.h_pre, (void*)L.h_assign, (void*)L.h_ret_iters, (void*)L.h_ret_status,
-                    (void*)L.h_ret_rr, (void*)L.h_idx, (void*)L.h_sc, (void*)L.h_st})
+                    (void*)L.h_ctl, (void*)L.h_pre, (void*)L.h_assign, (void*)L.h_idx, (void*)L.h_sc,
+                    (void*)L.h_st})
         cudaFreeHost(h);
     L = Lane();
 }
@@ -270,10 +270,13 @@ static int lane_open(hd_ctx* ctx, const hd_graph* g, const hd_eig* eig, double a
     rf.C = lr_on ? L.d_C : nullptr;
     rf.nstage = L.d_ctl;
     rf.next = L.d_ctl + 1;
-    rf.assign = cv.take<int32_t>(Bp);
-    rf.ret_iters = cv.take<int32_t>(Bp);
-    rf.ret_status = cv.take<int32_t>(Bp);
-    rf.ret_rr = cv.take<double>(Bp);
+    // assignment and retired statistics in one block (one copy to the host per
+    // step): [assign | ret_iters | ret_status] int32[Bp] each, then ret_rr f64[Bp]
+    uint8_t* ret = cv.take<uint8_t>((size_t)Bp * 20);
+    rf.assign = (int32_t*)ret;
+    rf.ret_iters = rf.assign + Bp;
+    rf.ret_status = rf.ret_iters + Bp;
+    rf.ret_rr = (double*)(rf.ret_status + Bp);
     rf.col_cnt = cv.take<int32_t>(Bp);
     rf.col_idx = cv.take<int32_t>((size_t)Bp * REFILL_MAX_NNZ);
     rf.col_val = cv.take<float>((size_t)Bp * REFILL_MAX_NNZ);
@@ -318,13 +321,15 @@ static int lane_open(hd_ctx* ctx, const hd_graph* g, const hd_eig* eig, double a
         cudaMallocHost(&L.h_yval, (size_t)L.cap_nnz * 4) || cudaMallocHost(&L.h_bb, Bp * 8) ||
         cudaMallocHost(&L.h_tol2, Bp * 8) || cudaMallocHost(&L.h_ctl, 16 * sizeof(int)) ||
         cudaMallocHost(&L.h_pre, Bp * 4) ||
-        cudaMallocHost(&L.h_assign, Bp * 4) || cudaMallocHost(&L.h_ret_iters, Bp * 4) ||
-        cudaMallocHost(&L.h_ret_status, Bp * 4) || cudaMallocHost(&L.h_ret_rr, Bp * 8) ||
+        cudaMallocHost(&L.h_assign, (size_t)Bp * 20) ||
         cudaMallocHost(&L.h_idx, (size_t)Bp * Kmax * 4) || cudaMallocHost(&L.h_sc, (size_t)Bp * Kmax * 4) ||
         cudaMallocHost(&L.h_st, Bp * sizeof(ColState))) {
         cudaGetLastError();
         return hd_fail(ctx, HD_ERR_OOM, "pinned host buffers");
     }
+    L.h_ret_iters = L.h_assign + Bp;
+    L.h_ret_status = L.h_ret_iters + Bp;
+    L.h_ret_rr = (double*)(L.h_ret_status + Bp);
     return HD_OK;
 }
 
@@ -450,10 +455,7 @@ static int lane_step(hd_server* s, Lane& L, int32_t iters) {
     }
     // ---- poll and retire
     HD_CUDA(ctx, cudaMemcpyAsync(L.h_st, E.st, Bp * sizeof(ColState), cudaMemcpyDeviceToHost, ctx->stream));
-    HD_CUDA(ctx, cudaMemcpyAsync(L.h_assign, L.rf.assign, Bp * 4, cudaMemcpyDeviceToHost, ctx->stream));
-    HD_CUDA(ctx, cudaMemcpyAsync(L.h_ret_iters, L.rf.ret_iters, Bp * 4, cudaMemcpyDeviceToHost, ctx->stream));
-    HD_CUDA(ctx, cudaMemcpyAsync(L.h_ret_status, L.rf.ret_status, Bp * 4, cudaMemcpyDeviceToHost, ctx->stream));
-    HD_CUDA(ctx, cudaMemcpyAsync(L.h_ret_rr, L.rf.ret_rr, Bp * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    HD_CUDA(ctx, cudaMemcpyAsync(L.h_assign, L.rf.assign, (size_t)Bp * 20, cudaMemcpyDeviceToHost, ctx->stream));
     HD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     if (E.has_lr && lr_use_tensor_cores(E.lr.e)) {
         const int frc = lr_tc_check_flags(ctx);
@@ -500,13 +502,16 @@ static int lane_step(hd_server* s, Lane& L, int32_t iters) {
         rc = hd_rank_impl(ctx, E.X, E.n, Bp, Bp, Kc.data(), s->Kmax, 0, L.d_idx, L.d_sc);
     }
     if (rc) return rc;
+    // the rankings of the retiring columns: one copy per array, of the rows
+    // from the first to the last retiring column (a few hundred KB at most)
+    int jlo = Bp, jhi = -1;
     for (auto& f : fin) {
-        const int j = f.first;
-        HD_CUDA(ctx, cudaMemcpyAsync(L.h_idx + (size_t)j * s->Kmax, L.d_idx + (size_t)j * s->Kmax,
-                                     (size_t)s->Kmax * 4, cudaMemcpyDeviceToHost, ctx->stream));
-        HD_CUDA(ctx, cudaMemcpyAsync(L.h_sc + (size_t)j * s->Kmax, L.d_sc + (size_t)j * s->Kmax,
-                                     (size_t)s->Kmax * 4, cudaMemcpyDeviceToHost, ctx->stream));
+        jlo = std::min(jlo, f.first);
+        jhi = std::max(jhi, f.first);
     }
+    const size_t off = (size_t)jlo * s->Kmax, cnt = (size_t)(jhi - jlo + 1) * s->Kmax * 4;
+    HD_CUDA(ctx, cudaMemcpyAsync(L.h_idx + off, L.d_idx + off, cnt, cudaMemcpyDeviceToHost, ctx->stream));
+    HD_CUDA(ctx, cudaMemcpyAsync(L.h_sc + off, L.d_sc + off, cnt, cudaMemcpyDeviceToHost, ctx->stream));
     HD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     const double t_done = now_s();
     for (auto& f : fin) {
