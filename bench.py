@@ -99,7 +99,7 @@ class Clocks:
             return
         self.thread = threading.Thread(target=self._read, daemon=True)
         self.thread.start()
-        # nvidia-smi's start-up (driver queries) must not overlap the timed
+        # nvidia-smi's start-up (NVML initialisation) must not overlap the timed
         # steps: wait for its first sample (at most 3 s)
         t0 = time.time()
         while not self.samples and time.time() - t0 < 3.0 and self.proc.poll() is None:
