@@ -289,16 +289,24 @@ def time_leg(ctx, wl, eig, mode, tol, alpha, K, W, B, topk, profile, tim=None):
 
 def e2e_leg(ctx, wl, eig, mode, tol, alpha, K, B, topk):
     """Same metric through the public API with HOST buffers: the observation
-    arrays go host->device and the rankings device->host inside each step."""
+    arrays go host->device and the rankings device->host inside each step, from
+    and into pinned host memory (numpy views of page-locked torch tensors)."""
     import torch
     import paper_1807_08692_gb300 as hd
     g = wl["g"]
-    yp, yi, yv = (np.ascontiguousarray(a) for a in wl["tim"])
-    tolh = np.full(B, tol, np.float32)
+
+    def pinned(a, dtype):
+        t = torch.empty(a.shape if hasattr(a, "shape") else a, dtype=dtype, pin_memory=True)
+        if hasattr(a, "shape"):
+            t.copy_(torch.from_numpy(np.ascontiguousarray(a)))
+        return t.numpy()
+
+    yp, yi, yv = (pinned(a, dt) for a, dt in zip(wl["tim"], (torch.int32, torch.int32, torch.float32)))
+    tolh = pinned(np.full(B, tol, np.float32), torch.float32)
     X = torch.empty((wl["n"], (B + 3) // 4 * 4), dtype=torch.float32, device="cuda")
     Kh = np.full(B, topk, np.int32)
-    idx = np.empty((B, topk), np.int32)
-    sc = np.empty((B, topk), np.float32)
+    idx = pinned((B, topk), torch.int32)
+    sc = pinned((B, topk), torch.float32)
     times = []
     for k in range(K + 1):
         torch.cuda.synchronize()
