@@ -761,13 +761,22 @@ __global__ void __launch_bounds__(1024) k_colsq(const float* __restrict__ V, int
     int col, g;
     const bool work = red_thread(n, ld, rch, nullptr, r0, r1, col, g);
     KSum acc[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+    // four rows' loads issued before their (row-ordered) compensated adds: one
+    // load in flight per thread left this single-array pass at half the HBM rate
     if (work)
-        for (int64_t row = r0; row < r1; row += RG) {
-            const float4 v = ld4v(V + row * ld + col);
-            ksum_add(acc[0], v.x * v.x);
-            ksum_add(acc[1], v.y * v.y);
-            ksum_add(acc[2], v.z * v.z);
-            ksum_add(acc[3], v.w * v.w);
+        for (int64_t row = r0; row < r1; row += 4 * RG) {
+            float4 v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                v[u] = row + u * RG < r1 ? ld4v(V + (row + u * RG) * ld + col) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (row + u * RG >= r1) break;
+                ksum_add(acc[0], v[u].x * v[u].x);
+                ksum_add(acc[1], v[u].y * v[u].y);
+                ksum_add(acc[2], v[u].z * v[u].z);
+                ksum_add(acc[3], v[u].w * v[u].w);
+            }
         }
     red_finish(part, ld, work, col, g, acc);
 }
