@@ -178,18 +178,19 @@ __global__ void k_sort_out(const uint64_t* cand, const SelState* st, int32_t Kma
 constexpr int TK_SAMPLE = 4096;
 constexpr int TK_CAP = 16384;
 
+// Each thread takes compare-exchange pairs directly (pair q: t = the q-th index
+// with bit `stride` clear, u = t + stride), so no thread idles in a stage.
 __device__ __forceinline__ void bitonic_desc_u64(uint64_t* a, int P) {
     for (int size = 2; size <= P; size <<= 1)
         for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int t = threadIdx.x; t < P; t += blockDim.x) {
-                const int u = t ^ stride;
-                if (u > t) {
-                    const bool desc = (t & size) == 0;
-                    const uint64_t x = a[t], y = a[u];
-                    if (desc ? (x < y) : (x > y)) {
-                        a[t] = y;
-                        a[u] = x;
-                    }
+            for (int q = threadIdx.x; q < P / 2; q += blockDim.x) {
+                const int t = ((q & ~(stride - 1)) << 1) | (q & (stride - 1));
+                const int u = t + stride;
+                const bool desc = (t & size) == 0;
+                const uint64_t x = a[t], y = a[u];
+                if (desc ? (x < y) : (x > y)) {
+                    a[t] = y;
+                    a[u] = x;
                 }
             }
             __syncthreads();
