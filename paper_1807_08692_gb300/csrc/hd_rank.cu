@@ -177,6 +177,9 @@ __global__ void k_sort_out(const uint64_t* cand, const SelState* st, int32_t Kma
 // otherwise that column is ranked again by the radix select.
 constexpr int TK_SAMPLE = 4096;
 constexpr int TK_CAP = 16384;
+constexpr int TK_TOP = 2048;  // K <= Kmax <= 2048
+// dynamic shared memory of k_topk_sort: candidates, the top K, histogram, scalars
+constexpr size_t TK_SORT_SMEM = (size_t)(TK_CAP + TK_TOP) * 8 + 256 * 4 + 2 * 8 + 16;
 
 // Each thread takes compare-exchange pairs directly (pair q: t = the q-th index
 // with bit `stride` clear, u = t + stride), so no thread idles in a stage.
@@ -195,6 +198,61 @@ __device__ __forceinline__ void bitonic_desc_u64(uint64_t* a, int P) {
             }
             __syncthreads();
         }
+}
+
+// The k-th largest (1-based, counting repeats) of a[0 .. cnt) in shared
+// memory, by a most-significant-digit radix select over the low `nbits` bits
+// (8 per round): a 256-bin histogram of the elements that match the digits
+// chosen so far, then one warp finds the bin that holds the k-th (each lane sums
+// 8 bins, a shuffle scan over the lanes).  All threads of the block call it.
+__device__ uint64_t block_kth_desc(const uint64_t* a, int cnt, int k, int nbits, uint32_t* hist, uint64_t* sh) {
+    uint64_t prefix = 0;
+    int krem = k;
+    for (int shift = nbits - 8; shift >= 0; shift -= 8) {
+        for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
+        __syncthreads();
+        const uint64_t hi = shift + 8 >= 64 ? 0ull : (~0ull << (shift + 8));
+        for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+            const uint64_t v = a[i];
+            if ((v & hi) == prefix) atomicAdd(&hist[(v >> shift) & 255u], 1u);
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            const int lane = threadIdx.x;
+            int h[8], sum = 0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                h[q] = (int)hist[255 - 8 * lane - q];  // lane 0 holds the highest bins
+                sum += h[q];
+            }
+            int incl = sum;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            const int excl = incl - sum;
+            const unsigned m = __ballot_sync(0xffffffffu, excl < krem && krem <= incl);
+            if (m && lane == __ffs(m) - 1) {
+                int cum = excl, d = 255 - 8 * lane - 7;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    if (cum + h[q] >= krem) {
+                        d = 255 - 8 * lane - q;
+                        break;
+                    }
+                    cum += h[q];
+                }
+                sh[0] = prefix | ((uint64_t)d << shift);
+                sh[1] = (uint64_t)(krem - cum);
+            }
+        }
+        __syncthreads();
+        prefix = sh[0];
+        krem = (int)sh[1];
+        __syncthreads();
+    }
+    return prefix;
 }
 
 __global__ void __launch_bounds__(1024) k_topk_sample(const float* X, int64_t n, int32_t ld, const int32_t* Kd,
@@ -219,11 +277,14 @@ __global__ void __launch_bounds__(1024) k_topk_sample(const float* X, int64_t n,
         sk[t] = v;
     }
     __syncthreads();
-    bitonic_desc_u64(sk, TK_SAMPLE);
+    // the threshold is the (kp + 1)-th largest sample (a radix select, not a sort)
+    __shared__ uint32_t hist[256];
+    __shared__ uint64_t sh[2];
+    int64_t kp = (4 * K * s + n - 1) / n + 8;
+    if (kp > s - 1) kp = s - 1;
+    const uint64_t t = block_kth_desc(sk, TK_SAMPLE, (int)kp + 1, 32, hist, sh);
     if (threadIdx.x == 0) {
-        int64_t kp = (4 * K * s + n - 1) / n + 8;
-        if (kp > s - 1) kp = s - 1;
-        tau[j] = (uint32_t)sk[kp];
+        tau[j] = (uint32_t)t;
         cnt[j] = 0;
     }
 }
@@ -274,16 +335,28 @@ __global__ void __launch_bounds__(1024) k_topk_sort(const uint64_t* cand, const 
         return;
     }
     if (threadIdx.x == 0) fail[j] = 0;
+    // candidates' keys (score key, ~id) are distinct: exactly K lie at or above
+    // the K-th largest, which a radix select finds; only those K are sorted
+    uint64_t* top = sk + TK_CAP;  // [TK_TOP]
+    uint32_t* hist = reinterpret_cast<uint32_t*>(top + TK_TOP);
+    uint64_t* sh = reinterpret_cast<uint64_t*>(hist + 256);
+    int* fill = reinterpret_cast<int*>(sh + 2);
     int P = 1;
-    while (P < c) P <<= 1;
+    while (P < K) P <<= 1;
     if (K > 0) {
-        for (int t = threadIdx.x; t < P; t += blockDim.x) sk[t] = t < c ? cand[(int64_t)j * TK_CAP + t] : 0ull;
+        for (int t = threadIdx.x; t < c; t += blockDim.x) sk[t] = cand[(int64_t)j * TK_CAP + t];
+        if (threadIdx.x == 0) *fill = 0;
         __syncthreads();
-        bitonic_desc_u64(sk, P);
+        const uint64_t T = block_kth_desc(sk, c, K, 64, hist, sh);
+        for (int t = threadIdx.x; t < c; t += blockDim.x)
+            if (sk[t] >= T) top[atomicAdd(fill, 1)] = sk[t];
+        for (int t = K + threadIdx.x; t < P; t += blockDim.x) top[t] = 0ull;
+        __syncthreads();
+        bitonic_desc_u64(top, P);
     }
     for (int t = threadIdx.x; t < Kmax; t += blockDim.x) {
         if (t < K) {
-            const uint64_t v = sk[t];
+            const uint64_t v = top[t];
             idx_out[(int64_t)j * Kmax + t] = (int32_t)(~(uint32_t)(v & 0xFFFFFFFFu));
             score_out[(int64_t)j * Kmax + t] = key_float((uint32_t)(v >> 32));
         } else {
@@ -326,14 +399,14 @@ int hd_rank_impl(hd_ctx* ctx, const float* Xd, int64_t n, int32_t B, int32_t ldx
     HD_CUDA(ctx, cudaMemcpyAsync(Kd, K_h, B * 4, cudaMemcpyHostToDevice, ctx->stream));
     static uint64_t attr = 0;
     if (hd_first_on_device(attr, ctx->device)) {
-        HD_CUDA(ctx, cudaFuncSetAttribute(k_topk_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, TK_CAP * 8));
+        HD_CUDA(ctx, cudaFuncSetAttribute(k_topk_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, TK_SORT_SMEM));
     }
     k_topk_sample<<<B, 1024, 0, ctx->stream>>>(src, m, ld, Kd, tau, cnt);
     HD_CHECK_LAUNCH(ctx);
     const int gc = std::max(1, std::min<int>(ceil_div(m * B, 256 * 8), ctx->num_sms * 8));
     k_topk_filter<<<gc, 256, 0, ctx->stream>>>(src, m, B, ld, Kd, tau, cnt, cand);
     HD_CHECK_LAUNCH(ctx);
-    k_topk_sort<<<B, 1024, TK_CAP * 8, ctx->stream>>>(cand, cnt, Kd, m, Kmax, idx_d, score_d, fail);
+    k_topk_sort<<<B, 1024, TK_SORT_SMEM, ctx->stream>>>(cand, cnt, Kd, m, Kmax, idx_d, score_d, fail);
     HD_CHECK_LAUNCH(ctx);
     std::vector<int> hf(B);
     HD_CUDA(ctx, cudaMemcpyAsync(hf.data(), fail, B * 4, cudaMemcpyDeviceToHost, ctx->stream));
