@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=2000,
                     help="requests per rate after warm-up (the serving protocol asks for 10000)")
     ap.add_argument("--serve-slots", type=int, default=128)
+    ap.add_argument("--serve-saturated", type=int, default=0,
+                    help="requests queued at once for a saturated-server step profile (0: skip)")
     ap.add_argument("--sweep", type=int, default=1, help="run the storage / rank / batch sweep")
     ap.add_argument("--sweep-batches", default="1,16,256")
     ap.add_argument("--shortlist", type=int, default=75000, help="Temporal† shortlist size (0: skip the leg)")
@@ -710,6 +712,61 @@ def serve_leg(ctx, wl, eig, args, rates, alpha):
     return {"rates": out, "batch_same_mix": batch_same_mix(ctx, wl, eig, args, yp, yi, yv, tols, Ks, alpha)}
 
 
+def serve_saturated(ctx, wl, eig, args, alpha, nreq):
+    """Where a saturated server's time goes: nreq requests of the serving mix
+    queued at once, one CG iteration per step until all are done; wall time in
+    step() and in completed() + poll(), and the per-family kernel time per step
+    (a second pass with CUDA-event profiling on)."""
+    import torch
+    import paper_1807_08692_gb300 as hd
+    import synth
+    c = wl["cfg"]
+    Qv = synth.queries(c.seed + 5000, nreq, wl["d"], c.ncl, c.kappa_lo, c.kappa_hi, c.sizes, c.zipf_s)
+    yp, yi, yv = hd.observe(ctx, wl["Xt"], torch.from_numpy(Qv).to(wl["Xt"].dtype).cuda(), c.k_y, c.gamma)
+    tols, Ks = synth.request_draws(c.seed, nreq)
+    out = {"requests": nreq, "slots": args.serve_slots}
+    for prof in (False, True):
+        srv = hd.Server(ctx, wl["g"], eig, "pcg" if eig is not None else "paper", alpha, max_slots=args.serve_slots,
+                        max_iter=2000, Kmax=1000)
+        for j in range(min(16, nreq)):
+            srv.submit(yi[yp[j]:yp[j + 1]], yv[yp[j]:yp[j + 1]], 1e-4, 10)
+        while srv.step(1):
+            pass
+        for t in srv.completed():
+            srv.poll(t, 10)
+        tick = {srv.submit(yi[yp[j]:yp[j + 1]], yv[yp[j]:yp[j + 1]], float(tols[j]), int(Ks[j])): int(Ks[j])
+                for j in range(nreq)}
+        if prof:
+            ctx.profile(True)
+            for f in FAMILIES:
+                ctx.profile_read(f)
+        t_step = t_poll = 0.0
+        steps = done = 0
+        t0 = time.perf_counter()
+        while done < nreq:
+            a = time.perf_counter()
+            srv.step(1)
+            b = time.perf_counter()
+            fin = srv.completed()
+            for t in fin:
+                srv.poll(t, tick[t])
+            done += len(fin)
+            t_poll += time.perf_counter() - b
+            t_step += b - a
+            steps += 1
+        wall = time.perf_counter() - t0
+        if not prof:
+            out.update({"qps": round(nreq / wall, 1), "steps": steps, "ms_per_step": round(wall / steps * 1e3, 3),
+                        "step_ms": round(t_step / steps * 1e3, 3), "completed_poll_ms": round(t_poll / steps * 1e3, 3),
+                        "retirements_per_step": round(nreq / steps, 1)})
+        else:
+            out["families_ms_per_step"] = {f: round(ms / steps, 3) for f in FAMILIES
+                                           for (cnt, ms) in [ctx.profile_read(f)] if cnt}
+            ctx.profile(False)
+        srv.close()
+    return out
+
+
 def batch_same_mix(ctx, wl, eig, args, yp, yi, yv, tols, Ks, alpha):
     """The batch solver on the serving leg's request mix: batches of
     serve_slots requests with their own tolerances and K (hd_query_batch +
@@ -859,6 +916,8 @@ def main():
     rates = [float(x) for x in args.serve_rates.split(",") if x.strip()] if not wl["pool"] else []
     if rates:
         serving = serve_leg(ctx, wl, eig, args, rates, alpha)
+    if args.serve_saturated > 0 and not wl["pool"]:
+        serving = dict(serving or {}, saturated=serve_saturated(ctx, wl, eig, args, alpha, args.serve_saturated))
     # ---- roofline of the dominant kernel
     ab = algorithmic_bytes(wl, B, eig)
     fam = hprof["fam"]
