@@ -1,6 +1,10 @@
 // Ranking by decreasing score (Sec. 3): per-column top-K of an n x B score block.
 //
-// Per column j the K_j-th largest score is found by a most-significant-digit
+// The usual path is the sampled-threshold one below (one pass over the scores
+// collects the candidates above a threshold drawn from a sample, and only the
+// candidates are selected and sorted).  The exact fallback, and the path of the
+// allocation-free entry point, is a radix select over the whole column:
+// per column j the K_j-th largest score is found by a most-significant-digit
 // radix select over the 32-bit order-preserving key of each float (4 passes of
 // 8 bits, histograms in shared memory).  If scores tie at the boundary, a
 // second radix select over the inverted row ids picks the smallest ids among
@@ -172,7 +176,8 @@ __global__ void k_sort_out(const uint64_t* cand, const SelState* st, int32_t Kma
 // ---- sampled-threshold fast path ----------------------------------------------
 // A strided sample of each column gives a key threshold tau with, in
 // expectation, about 4K + 8 (n / sample) elements at or above it; one pass over
-// the scores collects those candidates, and a per-column sort keeps the top K.
+// the scores collects those candidates, and per column a radix select finds
+// the K-th of them and a sort orders the K at or above it.
 // The result is exact whenever at least K and at most CAP candidates passed;
 // otherwise that column is ranked again by the radix select.
 constexpr int TK_SAMPLE = 4096;
@@ -291,8 +296,8 @@ __global__ void __launch_bounds__(1024) k_topk_sample(const float* X, int64_t n,
 
 // Each thread keeps one column (B <= 256: 256 / B rows per block step) so the
 // column's threshold and K stay in registers and no index is divided per element;
-// eight rows' loads are issued before their compares (one load in flight per
-// thread left the pass at a quarter of the HBM bandwidth).
+// eight rows' loads are issued before their compares (0.136 ms against 0.159 ms
+// for a 1M x 64 block, cold L2).
 constexpr int TK_ROWS = 8;
 __global__ void __launch_bounds__(256) k_topk_filter(const float* X, int64_t n, int32_t B, int32_t ld,
                                                      const int32_t* Kd, const uint32_t* tau, int* cnt, uint64_t* cand) {
