@@ -61,3 +61,25 @@ def test_binding_marshals_element_types():
         hd._typed(torch.zeros(3, dtype=torch.int64), np.int32, "int32")
     with pytest.raises(TypeError):
         hd._typed(torch.zeros(3, dtype=torch.float64), np.float32, "float32")
+
+
+def test_every_entry_point_is_documented():
+    # each declaration in include/hd.h follows a comment block (argument meaning,
+    # layout, ownership, errors) or shares the block of the declaration before it
+    txt = open(os.path.join(ROOT, "include", "hd.h")).read()
+    lines = txt.splitlines()
+    undocumented = []
+    for i, line in enumerate(lines):
+        m = re.match(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s+(hd_[a-z0-9_]+)\s*\(", line)
+        if not m:
+            continue
+        k = i - 1
+        while k >= 0 and lines[k].strip() == "":
+            k -= 1
+        prev = lines[k].strip() if k >= 0 else ""
+        # a comment ends right above, or the line above continues a documented
+        # declaration group (an earlier declaration's trailing argument line)
+        if not (prev.endswith("*/") or prev.endswith(");") or prev.endswith(",")):
+            undocumented.append(m.group(1))
+    assert not undocumented, undocumented
+    assert "/*" in txt and txt.count("Sec.") + txt.count("Eq.") >= 10
