@@ -354,7 +354,10 @@ __global__ void __launch_bounds__(1024) k_topk_sort(const uint64_t* cand, const 
         __syncthreads();
         const uint64_t T = block_kth_desc(sk, c, K, 64, hist, sh);
         for (int t = threadIdx.x; t < c; t += blockDim.x)
-            if (sk[t] >= T) top[atomicAdd(fill, 1)] = sk[t];
+            if (sk[t] >= T) {
+                const int p = atomicAdd(fill, 1);  // exactly K reach here; the bound only guards the array
+                if (p < TK_TOP) top[p] = sk[t];
+            }
         for (int t = K + threadIdx.x; t < P; t += blockDim.x) top[t] = 0ull;
         __syncthreads();
         bitonic_desc_u64(top, P);
