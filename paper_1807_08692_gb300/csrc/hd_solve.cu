@@ -233,10 +233,10 @@ __global__ void __launch_bounds__(256, 8) k_spmm(const int32_t* rp, const int32_
 // lanes per row, lane e summing entries b + e, b + e + 4, ... in order (four
 // loads in flight), the four sums meeting as (v0 + v2) + (v1 + v3).  The
 // row's index / weight reads are coalesced and eight rows gather per warp:
-// 0.24 ms on the 1M-node benchmark graph against 0.38 ms for k_spmm<4> (a
-// thread per row) and 0.32 ms for a warp per row.  Its sums run in another
-// order than k_spmm's, so the server, whose results must not depend on the
-// lane width, keeps k_spmm.
+// 0.24 ms on the 1M-node benchmark graph against 0.28 ms for k_spmm<4> (two
+// lanes per row), 0.38 ms for a thread per row and 0.32 ms for a warp per row.
+// Its sums run in another order than k_spmm's, so the server, whose results
+// must not depend on the lane width, keeps k_spmm.
 constexpr int N4_ROWS = 64;  // rows per 256-thread block
 __global__ void __launch_bounds__(256, 8) k_spmm_n4(const int32_t* rp, const int32_t* ci, const float* wv,
                                                     const float* P, float* Q, int64_t n, float c1, float c2,
